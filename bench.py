@@ -1,0 +1,422 @@
+"""Benchmark: bulk N(0,1) generation on GB300 (one JSON line on stdout).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+A step is one pass of the hot path over the bulk workload: the original
+128-level ziggurat (binary64 output) over 2^20 streams x 1,024 variates with
+seeds 0x5EED + s, once for each generator (java.util.Random LCG48, SplitMix64,
+L64X128Mix): 3 x 2^30 variates, 24 GiB written.  Inputs are resident in HBM
+before the timed region; each launch writes 8 GiB, far more than the 129 MB L2,
+so no L2 flush is needed between launches.
+
+Under torchrun (N > 1) each rank generates its own 2^20 streams (seeds offset by
+rank * 2^20): weak scaling with no collective on the data path; timing is the
+max over ranks.  ``--impl reference`` times the oracle (plain serial C, all host
+cores) on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "N(0,1) variates/s & % HBM-write roofline, plain vs batched/FP32; p50/p99 ms"
+UNIT = "variates/s"
+PRNGS = ["lcg48", "splitmix64", "l64x128mix"]
+N_STREAMS = 1 << 20
+PER_STREAM = 1024
+BYTES_F64 = 8
+WORKLOAD = ("bulk FP64: 2^20 streams x 1,024 variates (seeds 0x5EED+s), 128-level "
+            "ziggurat over lcg48, splitmix64 and l64x128mix (3 x 2^30 variates per step)")
+CONFIG = {
+    "workload": WORKLOAD,
+    "streams_per_gpu": N_STREAMS,
+    "variates_per_stream": PER_STREAM,
+    "algorithm": "zig128 (GSL form)",
+    "prngs": PRNGS,
+    "output": "binary64, stream-major packed, 8 GiB per launch",
+    "l2": "no flush: every launch writes 8 GiB >> 129 MB L2",
+    "parallelism": "streams sharded across ranks, no collective",
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        smi = shutil.which("nvidia-smi")
+        if not smi:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.fh = open(self.path, "w")
+        self.proc = subprocess.Popen(
+            [smi, "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+             "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on host cores
+# ---------------------------------------------------------------------------
+def oracle_rate(n_streams: int, threads: int, seed_base: int = 0x5EED):
+    """Oracle variates/s for the step's three generators over n_streams x 1,024, in threads."""
+    import oracle as O
+    from paper_2405_19493_gb300 import workloads as W
+    O.load()
+    seeds = W.seeds(n_streams, base=seed_base)
+    parts = np.array_split(np.arange(n_streams), threads)
+
+    def run(idx, prng):
+        O.generate(prng, "zig128", seeds[idx], uniform_len=PER_STREAM)
+
+    t0 = time.perf_counter()
+    for prng in PRNGS:
+        ths = [threading.Thread(target=run, args=(idx, prng)) for idx in parts if len(idx)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+    dt = time.perf_counter() - t0
+    return 3 * n_streams * PER_STREAM / dt, dt
+
+
+def cpu_baseline():
+    cores = os.cpu_count() or 1
+    n_all = 1 << 14       # 2^24 variates per generator across all cores
+    rate_all, dt_all = oracle_rate(n_all, cores)
+    n_one = 1 << 11       # 2^21 variates per generator on one core
+    rate_one, dt_one = oracle_rate(n_one, 1)
+    return {"value": rate_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{n_all} streams x 1,024 per generator (1/64 of the workload) on "
+                       f"{cores} threads in {dt_all:.2f} s; single thread {rate_one:.3e} "
+                       f"variates/s on {n_one} streams x 1,024 per generator")}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    n = 1 << 12
+    for _ in range(args.warmup):
+        oracle_rate(n, cores)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_rate(n, cores)
+        times.append(dt)
+    total = sum(times)
+    value = 3 * n * PER_STREAM * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": CONFIG,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} streams x 1,024 per generator per step (1/256 of the "
+                                   f"workload), {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def load_traffic_record():
+    """Per-launch DRAM traffic of the dominant kernel from the committed ncu summary,
+    valid only while the kernel sources are unchanged."""
+    import hashlib
+    rec = os.path.join(ROOT, "profiles", "zig128_f64_bulk_traffic.json")
+    if not os.path.exists(rec):
+        return None
+    with open(rec) as fh:
+        d = json.load(fh)
+    h = hashlib.sha256()
+    for f in ("zig_lib.cu", "zig_device.cuh", "zig_tables.inc"):
+        with open(os.path.join(ROOT, "paper_2405_19493_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if d.get("source_sha256") != h.hexdigest():
+        return None
+    return d
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2405_19493_gb300 as Z
+    from paper_2405_19493_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.cuda.current_device()
+    Z.zig_tables_init(dev)
+    stream = torch.cuda.current_stream()
+
+    seeds_np = W.seeds(N_STREAMS, base=0x5EED + rank * N_STREAMS)
+    seeds = torch.from_numpy(seeds_np.view(np.int64)).cuda()
+    out = torch.empty(N_STREAMS * PER_STREAM, dtype=torch.float64, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(evs=None):
+        for k, prng in enumerate(PRNGS):
+            if evs is not None:
+                evs[k][0].record(stream)
+            Z.zig_generate(prng, "zig128", seeds, out, uniform_len=PER_STREAM, stream=stream)
+            if evs is not None:
+                evs[k][1].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    barrier()
+    events = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in PRNGS]
+              for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    barrier()
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(events[s])
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = t_start.elapsed_time(t_end)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_launch = {p: [events[s][k][0].elapsed_time(events[s][k][1]) for s in range(args.steps)]
+                  for k, p in enumerate(PRNGS)}
+    variates_step = 3 * N_STREAMS * PER_STREAM
+    value = ws * variates_step * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (largest total time)
+    dom = max(PRNGS, key=lambda p: sum(per_launch[p]))
+    dom_ms = statistics.mean(per_launch[dom])
+    alg_bytes = N_STREAMS * PER_STREAM * BYTES_F64 + N_STREAMS * 8
+    peak, peak_src = measured_peaks()
+    achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+    traffic = load_traffic_record()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "kernel": f"gen_kernel<zig128, {dom}, f64>", "peak_source": f"{peak_src} copy bandwidth",
+                "algorithmic_bytes_per_launch": alg_bytes}
+    all_ms = sorted(x for p in PRNGS for x in per_launch[p])
+    line_extra = {
+        "per_prng": {p: {"variates_per_s": N_STREAMS * PER_STREAM / (statistics.mean(per_launch[p]) / 1e3),
+                         "ms_p50": float(np.percentile(per_launch[p], 50)),
+                         "ms_p99": float(np.percentile(per_launch[p], 99))} for p in PRNGS},
+        "launch_ms_p50": float(np.percentile(all_ms, 50)),
+        "launch_ms_p99": float(np.percentile(all_ms, 99)),
+    }
+
+    # write-only bandwidth of a plain fill over the same buffer (context for the roofline)
+    fill_ms = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out.fill_(0.0)
+        b.record(stream)
+        b.synchronize()
+        fill_ms.append(a.elapsed_time(b))
+    line_extra["write_only_fill_gbs"] = out.numel() * 8 / (min(fill_ms[1:]) / 1e3) / 1e9
+
+    # comparisons on the same seeds: other transforms and narrower outputs (rank 0 reports)
+    line_extra["comparisons"] = compare_variants(Z, torch, seeds, stream, args)
+
+    # end to end through the public call: seeds from pinned host memory, result back to host
+    e2e = measure_e2e(Z, torch, seeds_np, stream, args)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded streams; no dataset)", "config": CONFIG,
+        "roofline": roofline, "clocks": clk, "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+    }
+    line.update(line_extra)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        del out
+        torch.cuda.empty_cache()
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def time_launches(torch, stream, fn, reps):
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return ts
+
+
+def compare_variants(Z, torch, seeds, stream, args):
+    res = {}
+    reps = max(3, min(10, args.steps))
+    n = N_STREAMS * PER_STREAM
+    for alg, prng, dt in (("polar", "lcg48", "f64"), ("zig256", "splitmix64", "f64"),
+                          ("zig128", "splitmix64", "f32"), ("zig128", "splitmix64", "bf16"),
+                          ("zig128", "lcg48", "f32")):
+        tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dt]
+        o = torch.empty(n, dtype=tdt, device="cuda")
+        fn = lambda: Z.zig_generate(prng, alg, seeds, o, uniform_len=PER_STREAM, dtype=dt, stream=stream)
+        fn()
+        ts = time_launches(torch, stream, fn, reps)
+        m = statistics.mean(ts)
+        res[f"{alg}/{prng}/{dt}"] = {"variates_per_s": n / (m / 1e3), "ms_mean": m,
+                                     "write_gbs": n * o.element_size() / (m / 1e3) / 1e9}
+        del o
+    # batched: 10,000 streams with log-uniform lengths in [1, 2^20], 2^10 chunks
+    from paper_2405_19493_gb300 import workloads as W
+    L = W.batched_lengths()
+    sd = torch.from_numpy(W.seeds(len(L)).view(np.int64)).cuda()
+    ln = torch.from_numpy(L.view(np.int64)).cuda()
+    total = int(L.sum())
+    for dt in ("f64", "f32"):
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        o = torch.empty(total, dtype=tdt, device="cuda")
+        fn = lambda: Z.zig_generate("splitmix64", "zig128", sd, o, lengths=ln, chunk_log2=10,
+                                    dtype=dt, stream=stream)
+        fn()
+        ts = time_launches(torch, stream, fn, reps)
+        m = statistics.mean(ts)
+        res[f"batched/zig128/splitmix64/{dt}"] = {
+            "variates_per_s": total / (m / 1e3), "ms_mean": m, "variates": total,
+            "write_gbs": total * o.element_size() / (m / 1e3) / 1e9}
+        del o
+    return res
+
+
+def measure_e2e(Z, torch, seeds_np, stream, args):
+    """Seeds H2D from pinned memory, three generations, each 8 GiB result D2H to pinned memory."""
+    n = N_STREAMS * PER_STREAM
+    h_seeds = torch.from_numpy(seeds_np.view(np.int64)).pin_memory()
+    h_out = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    d_seeds = torch.empty_like(h_seeds, device="cuda")
+    d_out = torch.empty(n, dtype=torch.float64, device="cuda")
+    steps = max(2, min(5, args.steps))
+
+    def e2e_step():
+        for prng in PRNGS:
+            d_seeds.copy_(h_seeds, non_blocking=True)
+            Z.zig_generate(prng, "zig128", d_seeds, d_out, uniform_len=PER_STREAM, stream=stream)
+            h_out.copy_(d_out, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        e2e_step()
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    del h_out, d_out
+    return {"value": 3 * n * steps / (ms / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": 3 * seeds_np.nbytes, "d2h_bytes_per_step": 3 * n * 8,
+            "steps": steps}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    ws, _, _ = dist_env()
+    if ws != args.gpus and not (ws == 1 and args.gpus == 1):
+        print(f"warning: --gpus {args.gpus} but WORLD_SIZE={ws}", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

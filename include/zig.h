@@ -1,0 +1,173 @@
+/*
+ * zig.h -- C ABI of libzig_gb300: bulk N(0,1) generation on one GB300 (sm_103a).
+ *
+ * The paper (Cicirello, "Fast Gaussian Distributed Pseudorandom Number
+ * Generation in Java via the Ziggurat Algorithm") times one call,
+ * `nextGaussian`, that draws one standard normal variate from a caller-owned
+ * PRNG object which persists between calls (Sec. 2, Listing 2), for three
+ * generators (Sec. 2, first list) and three transforms: the original ziggurat
+ * in its GSL form, the polar method and McFarland's modified ziggurat (Sec. 2,
+ * bullets; Table 3).  This library is the bulk form of that call:
+ *
+ *     stream s's outputs are exactly the values that repeated nextGaussian
+ *     calls return on a generator seeded with seeds[s].
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are device pointers in the current CUDA context's
+ *    device memory; pointers named *_host are host pointers.  The caller owns
+ *    every buffer it passes; the library keeps no pointer after a call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it asynchronously; the call returns once the
+ *    launch is queued.
+ *  - Argument errors are detected on the host and returned synchronously, with
+ *    nothing enqueued.  Launch failures return ZIG_ERR_CUDA.  Conditions only the
+ *    GPU can see (a chunk overrunning its 2^32-draw budget, a bounded wait that
+ *    gave up) are latched in a per-device error word: read it with
+ *    zig_device_status().
+ *  - There is no CPU fallback: every step runs in this library's kernels.
+ *  - All entry points are thread-safe with respect to distinct streams.
+ */
+#ifndef ZIG_GB300_H
+#define ZIG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ZIG_OK = 0,
+    ZIG_ERR_INVALID_ARG = 1,     /* a bad enum, size, pointer or alignment */
+    ZIG_ERR_NOT_INITIALIZED = 2, /* zig_tables_init was not called on this device */
+    ZIG_ERR_CUDA = 3,            /* a CUDA runtime call or launch failed */
+    ZIG_ERR_BUDGET = 4,          /* a request exceeds the admission budget */
+    ZIG_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
+    ZIG_ERR_CHUNK_OVERFLOW = 6,  /* a chunk consumed more than 2^32 raw draws */
+    ZIG_ERR_UNSUPPORTED = 7      /* the device is not sm_103 or the combination is not built */
+} zig_status;
+
+/* Uniform generators (Sec. 2, first list; Sec. 3 for LXM). */
+typedef enum {
+    ZIG_LCG48 = 0,       /* java.util.Random: s <- (0x5DEECE66D s + 0xB) mod 2^48,
+                            seeded (seed ^ 0x5DEECE66D) mod 2^48; nextInt = s >> 16 */
+    ZIG_SPLITMIX64 = 1,  /* SplittableRandom / ThreadLocalRandom: s += 0x9E3779B97F4A7C15;
+                            nextInt = mix32(s), nextLong = mix64(s) */
+    ZIG_L64X128MIX = 2   /* LXM: 64-bit LCG (M = 0xD1342543DE82EF95) + xoroshiro128
+                            (24, 16, 37) + Lea's mix; seeded from 4 SplitMix64 outputs */
+} zig_prng;
+
+/* Gaussian transforms (Sec. 2, second list). */
+typedef enum {
+    ZIG_ZIG128 = 0,  /* original ziggurat, GSL form: 128 layers, 32-bit draw =
+                        layer (7 b) + sign (1 b) + 24-bit abscissa */
+    ZIG_POLAR = 1,   /* Marsaglia's polar method with the second variate cached */
+    ZIG_ZIG256 = 2   /* modified ziggurat after McFarland: 256 slots, 64-bit draws */
+} zig_alg;
+
+typedef enum {
+    ZIG_F64 = 0,  /* binary64 output (8 B per variate) */
+    ZIG_F32 = 1,  /* binary32 output (4 B per variate) */
+    ZIG_BF16 = 2  /* bfloat16 output (2 B per variate) */
+} zig_dtype;
+
+/*
+ * zig_tables_init -- prepare `device` for the generation calls.
+ * Checks that the device is compute capability 10.3 (GB300), loads the
+ * library's kernels there and resolves its table and error-word symbols.  The
+ * tables themselves are immutable device constants compiled into the library
+ * (the geometry of Sec. 2's two ziggurats, computed at 80 digits).  Idempotent
+ * and cheap after the first call; it makes `device` current.
+ * Returns ZIG_ERR_UNSUPPORTED on a non-sm_103 device, ZIG_ERR_CUDA on a CUDA error.
+ */
+zig_status zig_tables_init(int device);
+
+/*
+ * zig_tables_get_zig128 -- copy the 128-level tables to host memory (for
+ * comparison with an independent construction).  k_host: 128 uint32, w_host
+ * and y_host: 128 double, w32_host: 128 float, R_host: 1 double.  Any pointer
+ * may be NULL to skip that table.  Needs no device.
+ */
+zig_status zig_tables_get_zig128(uint32_t *k_host, double *w_host, double *y_host,
+                                 float *w32_host, double *R_host);
+
+/*
+ * zig_generate -- bulk N(0,1) variates, stream-major and packed.
+ *
+ * prng, alg, dtype   enums above.
+ * seeds_dev          n_streams uint64 seeds (device).
+ * lengths_dev        n_streams uint64 lengths (device), or NULL for every stream
+ *                    having uniform_len outputs.
+ * n_streams          number of streams (0 is a no-op).
+ * chunk_log2         0: each stream is one sequential generator (the paper's
+ *                    semantics).  c in [6, 20]: output t of stream s belongs to
+ *                    chunk q = t >> c, generated from the seeded state advanced
+ *                    by q * 2^32 raw generator steps (closed-form jump), so
+ *                    long streams split across threads.  Outputs of chunk 0
+ *                    equal the sequential ones.
+ * out_dev            device buffer of sum(lengths) elements of `dtype`; stream s
+ *                    occupies [off_s, off_s + L_s) with off_s the exclusive
+ *                    prefix sum of the lengths.  Must be aligned to the element size.
+ * workspace_dev,     scratch for the variable-length path (lengths_dev != NULL):
+ * workspace_bytes    at least zig_generate_workspace_bytes(n_streams) bytes,
+ *                    16-byte aligned, owned by the caller and not used by any
+ *                    other call in flight.  NULL/0 with lengths_dev != NULL makes
+ *                    the library use its own per-device workspace (allocated, or
+ *                    grown, with cudaMalloc on first use).  Ignored when
+ *                    lengths_dev is NULL.
+ * stream             cudaStream_t.
+ *
+ * The sum of all lengths must be < 2^40.  Errors: ZIG_ERR_INVALID_ARG for bad
+ * enums, NULL pointers, chunk_log2 out of range, misaligned buffers or too small
+ * a workspace; ZIG_ERR_NOT_INITIALIZED if zig_tables_init(device) was not
+ * called for the current device.
+ */
+zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t *seeds_dev,
+                        const uint64_t *lengths_dev, uint64_t uniform_len, uint64_t n_streams,
+                        uint32_t chunk_log2, zig_dtype dtype, void *out_dev,
+                        void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/* Bytes of workspace zig_generate needs for n_streams variable-length streams. */
+size_t zig_generate_workspace_bytes(uint64_t n_streams);
+
+/*
+ * zig_mutate -- Gaussian mutation x += sigma * N(0,1) in place (the paper's
+ * motivating workload, Sec. 1: Gaussian mutation in an evolutionary algorithm).
+ * x_dev: P x L binary32 row-major population (device).  Row p draws its L
+ * variates from stream p of the 128-level ziggurat with binary32 output, seeded
+ * seed + p, so row p's increments equal zig_generate(prng, ZIG_ZIG128, seeds =
+ * {seed + p}, L, ZIG_F32) and x[p][l] = fmaf(sigma, z[p][l], x[p][l]).
+ * P * L must be < 2^40; sigma must be finite.
+ */
+zig_status zig_mutate(float *x_dev, float sigma, uint64_t P, uint64_t L, uint64_t seed,
+                      zig_prng prng, void *stream);
+
+/*
+ * zig_prng_fill -- raw uniform draws, for bit-exact checks of the generators.
+ * out_dev: n_streams x n uint64 (device), stream-major.  kind 0 = nextInt
+ * (32-bit, zero-extended), 1 = nextLong, 2 = the 53-bit integer behind
+ * nextDouble.  Each stream is first advanced by `skip` raw steps with the
+ * closed-form jump.
+ */
+zig_status zig_prng_fill(zig_prng prng, const uint64_t *seeds_dev, uint64_t n_streams,
+                         uint64_t n, uint64_t skip, int kind, uint64_t *out_dev, void *stream);
+
+/*
+ * zig_device_status -- read (and, if clear != 0, reset) the device's latched
+ * error word.  Synchronizes the device.  Returns ZIG_OK, ZIG_ERR_TIMEOUT or
+ * ZIG_ERR_CHUNK_OVERFLOW (the first latched condition), or ZIG_ERR_CUDA.
+ */
+zig_status zig_device_status(int device, int clear);
+
+/* Human-readable name of a status code (static storage). */
+const char *zig_status_string(zig_status status);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int zig_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZIG_GB300_H */

@@ -463,6 +463,7 @@ double orc_zig256_next(orc_prng *g, const orc_zig256_tab *t, orc_stats *st, doub
             double x = -log(U1) / t->x0;
             double y = -log(U2);
             st->tail_tries++;
+            if (x > 0) note_margin(st, y + y, x * x, vm);
             if (y + y > x * x) {
                 st->tail++;
                 return sign * (t->x0 + x);

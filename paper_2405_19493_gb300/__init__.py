@@ -1,0 +1,21 @@
+"""GB300-native bulk N(0,1) generation: the original 128-level ziggurat (GSL
+form) over per-stream java.util.Random / SplitMix64 / L64X128Mix generators, with
+the polar method and a 256-slot modified ziggurat as comparison transforms.
+
+The compute lives in libzig_gb300.so (CUDA, sm_103a) behind the C ABI in
+include/zig.h; this package only builds and binds it (``_binding``), plus the
+seeded synthetic workloads (``workloads``) and the request loop for Gaussian
+mutation (``serving``).
+"""
+
+from ._binding import (  # noqa: F401
+    ZigError, generate, load, zig_device_status, zig_generate, zig_generate_workspace_bytes,
+    zig_mutate, zig_prng_fill, zig_status_string, zig_tables_get_zig128, zig_tables_init,
+    zig_version,
+)
+
+__all__ = [
+    "ZigError", "generate", "load", "zig_device_status", "zig_generate",
+    "zig_generate_workspace_bytes", "zig_mutate", "zig_prng_fill", "zig_status_string",
+    "zig_tables_get_zig128", "zig_tables_init", "zig_version",
+]

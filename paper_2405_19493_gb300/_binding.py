@@ -1,0 +1,172 @@
+"""ctypes binding of libzig_gb300 (include/zig.h): argument marshalling only.
+
+Every function named ``zig_*`` here is the C entry point of the same name;
+tensors are passed as data pointers and the current torch CUDA stream as the
+``cudaStream_t``.  Every step of generation runs in the library's kernels; if
+the library cannot be loaded, these calls raise -- there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+ZIG_OK = 0
+STATUS_NAMES = {
+    0: "ZIG_OK", 1: "ZIG_ERR_INVALID_ARG", 2: "ZIG_ERR_NOT_INITIALIZED", 3: "ZIG_ERR_CUDA",
+    4: "ZIG_ERR_BUDGET", 5: "ZIG_ERR_TIMEOUT", 6: "ZIG_ERR_CHUNK_OVERFLOW",
+    7: "ZIG_ERR_UNSUPPORTED",
+}
+PRNG = {"lcg48": 0, "splitmix64": 1, "l64x128mix": 2}
+ALG = {"zig128": 0, "polar": 1, "zig256": 2}
+DTYPE = {"f64": 0, "f32": 1, "bf16": 2}
+ESIZE = {"f64": 8, "f32": 4, "bf16": 2}
+FILL_KIND = {"u32": 0, "u64": 1, "m53": 2}
+
+# every symbol include/zig.h declares
+EXPORTS = (
+    "zig_tables_init", "zig_tables_get_zig128", "zig_generate", "zig_generate_workspace_bytes",
+    "zig_mutate", "zig_prng_fill", "zig_device_status", "zig_status_string", "zig_version",
+)
+
+
+class ZigError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load(build_if_missing: bool = True):
+    """Load libzig_gb300 (building it first when missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.lib_path()
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"libzig_gb300 is not built ({path}); run "
+                              "python -m paper_2405_19493_gb300.build")
+        lib = C.CDLL(path)
+        u64, vp, i32 = C.c_uint64, C.c_void_p, C.c_int
+        lib.zig_tables_init.argtypes = [i32]
+        lib.zig_tables_get_zig128.argtypes = [vp, vp, vp, vp, vp]
+        lib.zig_generate.argtypes = [i32, i32, vp, vp, u64, u64, C.c_uint32, i32, vp, vp,
+                                     C.c_size_t, vp]
+        lib.zig_generate_workspace_bytes.argtypes = [u64]
+        lib.zig_generate_workspace_bytes.restype = C.c_size_t
+        lib.zig_mutate.argtypes = [vp, C.c_float, u64, u64, u64, i32, vp]
+        lib.zig_prng_fill.argtypes = [i32, vp, u64, u64, u64, i32, vp, vp]
+        lib.zig_device_status.argtypes = [i32, i32]
+        lib.zig_status_string.argtypes = [i32]
+        lib.zig_status_string.restype = C.c_char_p
+        for name in ("zig_tables_init", "zig_tables_get_zig128", "zig_generate", "zig_mutate",
+                     "zig_prng_fill", "zig_device_status"):
+            getattr(lib, name).restype = i32
+        lib.zig_version.restype = i32
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != ZIG_OK:
+        raise ZigError(status, where)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+# ---- the C entry points --------------------------------------------------------
+
+def zig_tables_init(device: int = 0) -> None:
+    _check(load().zig_tables_init(device), "zig_tables_init")
+
+
+def zig_tables_get_zig128():
+    import numpy as np
+    k = np.empty(128, np.uint32)
+    w = np.empty(128, np.float64)
+    y = np.empty(128, np.float64)
+    w32 = np.empty(128, np.float32)
+    R = np.empty(1, np.float64)
+    _check(load().zig_tables_get_zig128(k.ctypes.data, w.ctypes.data, y.ctypes.data,
+                                        w32.ctypes.data, R.ctypes.data), "zig_tables_get_zig128")
+    return {"k": k, "w": w, "y": y, "w32": w32, "R": float(R[0])}
+
+
+def zig_generate_workspace_bytes(n_streams: int) -> int:
+    return int(load().zig_generate_workspace_bytes(n_streams))
+
+
+def zig_generate(prng: str, alg: str, seeds, out, lengths=None, uniform_len: int = 0,
+                 chunk_log2: int = 0, dtype: str = "f64", workspace=None, stream=None) -> None:
+    """Fill ``out`` (a CUDA tensor of sum(lengths) elements of ``dtype``)."""
+    n = int(seeds.numel())
+    ws_ptr, ws_bytes = (0, 0)
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    st = load().zig_generate(PRNG[prng], ALG[alg], seeds.data_ptr(),
+                             lengths.data_ptr() if lengths is not None else None,
+                             int(uniform_len), n, int(chunk_log2), DTYPE[dtype], out.data_ptr(),
+                             ws_ptr or None, ws_bytes, _stream_ptr(stream))
+    _check(st, "zig_generate")
+
+
+def zig_mutate(x, sigma: float, P: int, L: int, seed: int, prng: str = "splitmix64",
+               stream=None) -> None:
+    st = load().zig_mutate(x.data_ptr(), float(sigma), int(P), int(L),
+                           int(seed) & (2 ** 64 - 1), PRNG[prng], _stream_ptr(stream))
+    _check(st, "zig_mutate")
+
+
+def zig_prng_fill(prng: str, seeds, n: int, out, skip: int = 0, kind: str = "u32",
+                  stream=None) -> None:
+    st = load().zig_prng_fill(PRNG[prng], seeds.data_ptr(), int(seeds.numel()), int(n),
+                              int(skip), FILL_KIND[kind], out.data_ptr(), _stream_ptr(stream))
+    _check(st, "zig_prng_fill")
+
+
+def zig_device_status(device: int = 0, clear: bool = False) -> int:
+    return int(load().zig_device_status(device, 1 if clear else 0))
+
+
+def zig_status_string(status: int) -> str:
+    return load().zig_status_string(status).decode()
+
+
+def zig_version() -> int:
+    return int(load().zig_version())
+
+
+# ---- tensor-level convenience (allocation through torch, compute in the library) ----
+
+def generate(prng: str, alg: str, seeds, lengths=None, uniform_len: int = 0, chunk_log2: int = 0,
+             dtype: str = "f64", out=None, stream=None):
+    """Allocate (if needed) and fill the packed stream-major output tensor."""
+    import torch
+    torch_dt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    if lengths is not None:
+        total = int(lengths.sum().item()) if out is None else out.numel()
+    else:
+        total = int(seeds.numel()) * int(uniform_len)
+    if out is None:
+        out = torch.empty(total, dtype=torch_dt, device=seeds.device)
+    zig_generate(prng, alg, seeds, out, lengths=lengths, uniform_len=uniform_len,
+                 chunk_log2=chunk_log2, dtype=dtype, stream=stream)
+    return out

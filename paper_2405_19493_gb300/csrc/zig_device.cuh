@@ -1,0 +1,248 @@
+// Device-side building blocks of libzig_gb300: uniform generators with state in
+// registers, the exact binary64 product j * w[i] in integer arithmetic, and the
+// warp-cooperative staging that turns per-thread streams into coalesced stores.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace zig {
+
+constexpr uint64_t kMask48 = (1ull << 48) - 1;
+constexpr uint64_t kLcgA = 0x5DEECE66Dull;           // java.util.Random multiplier
+constexpr uint64_t kLcgC = 0xBull;                   // java.util.Random increment
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;   // SplitMix64 golden gamma
+constexpr uint64_t kLxmM = 0xD1342543DE82EF95ull;    // L64X128Mix LCG multiplier
+constexpr uint64_t kLeaM = 0xDABA0B6EB09322E3ull;    // Lea's 64-bit mix constant
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Error bits latched in the per-device error word.
+constexpr unsigned kErrChunkOverflow = 1u;
+constexpr unsigned kErrTimeout = 2u;
+
+// Jump-ahead tables for 2^b raw steps, b = 0..63 (filled on the host at init).
+struct JumpTab {
+    uint64_t lcg48_A[64], lcg48_C[64];   // s -> (A s + C) mod 2^48
+    uint64_t lxm_A[64], lxm_G[64];       // LXM LCG: s -> A s + a G (mod 2^64)
+    uint64_t xoro[64][256];              // xoroshiro128 T^(2^b): column c at [2c], [2c+1]
+};
+
+// ---------------------------------------------------------------------------
+// mixers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint32_t mix32(uint64_t z) {
+    z = (z ^ (z >> 33)) * 0x62A9D9ED799705F5ull;
+    return (uint32_t)(((z ^ (z >> 28)) * 0xCB24D0A5C88C35B3ull) >> 32);
+}
+
+__device__ __forceinline__ uint64_t mix_lea64(uint64_t z) {
+    z = (z ^ (z >> 32)) * kLeaM;
+    z = (z ^ (z >> 32)) * kLeaM;
+    return z ^ (z >> 32);
+}
+
+__device__ __forceinline__ uint64_t rotl64(uint64_t x, int k) {
+    return (x << k) | (x >> (64 - k));
+}
+
+// ---------------------------------------------------------------------------
+// generators: one per thread, state in registers
+//   next_u32 = nextInt, next_u64 = nextLong, next_m53 = the 53-bit integer of nextDouble
+// ---------------------------------------------------------------------------
+
+struct GenLcg48 {
+    uint64_t s;
+    __device__ __forceinline__ void seed(uint64_t x) { s = (x ^ kLcgA) & kMask48; }
+    __device__ __forceinline__ uint32_t step(int bits) {
+        s = (s * kLcgA + kLcgC) & kMask48;
+        return (uint32_t)(s >> (48 - bits));
+    }
+    __device__ __forceinline__ uint32_t next_u32() { return step(32); }
+    __device__ __forceinline__ uint64_t next_u64() {
+        uint64_t hi = step(32);
+        int32_t lo = (int32_t)step(32);
+        return (hi << 32) + (uint64_t)(int64_t)lo;
+    }
+    __device__ __forceinline__ uint64_t next_m53() {
+        uint64_t hi = step(26);
+        uint64_t lo = step(27);
+        return (hi << 27) + lo;
+    }
+    __device__ __forceinline__ void jump(uint64_t n, const JumpTab* jt) {
+        while (n) {
+            int b = __ffsll((long long)n) - 1;
+            s = (jt->lcg48_A[b] * s + jt->lcg48_C[b]) & kMask48;
+            n &= n - 1;
+        }
+    }
+};
+
+struct GenSplitMix64 {
+    uint64_t s;
+    __device__ __forceinline__ void seed(uint64_t x) { s = x; }
+    __device__ __forceinline__ uint32_t next_u32() { s += kGamma; return mix32(s); }
+    __device__ __forceinline__ uint64_t next_u64() { s += kGamma; return mix64(s); }
+    __device__ __forceinline__ uint64_t next_m53() { s += kGamma; return mix64(s) >> 11; }
+    __device__ __forceinline__ void jump(uint64_t n, const JumpTab*) { s += n * kGamma; }
+};
+
+struct GenL64X128Mix {
+    uint64_t a, s, x0, x1;
+    __device__ __forceinline__ void seed(uint64_t x) {
+        // four consecutive SplitMix64 outputs of a generator seeded with x
+        uint64_t t = x;
+        t += kGamma; a = mix64(t) | 1;
+        t += kGamma; s = mix64(t);
+        t += kGamma; x0 = mix64(t);
+        t += kGamma; x1 = mix64(t);
+        if ((x0 | x1) == 0) x1 = kGamma;
+    }
+    __device__ __forceinline__ uint64_t next_u64() {
+        uint64_t result = mix_lea64(s + x0);
+        s = kLxmM * s + a;
+        uint64_t q1 = x1 ^ x0;
+        x0 = rotl64(x0, 24) ^ q1 ^ (q1 << 16);
+        x1 = rotl64(q1, 37);
+        return result;
+    }
+    __device__ __forceinline__ uint32_t next_u32() { return (uint32_t)(next_u64() >> 32); }
+    __device__ __forceinline__ uint64_t next_m53() { return next_u64() >> 11; }
+    __device__ void jump(uint64_t n, const JumpTab* jt) {
+        while (n) {
+            int b = __ffsll((long long)n) - 1;
+            s = jt->lxm_A[b] * s + a * jt->lxm_G[b];
+            const uint64_t* m = jt->xoro[b];
+            uint64_t r0 = 0, r1 = 0;
+#pragma unroll 8
+            for (int c = 0; c < 64; ++c) {
+                uint64_t mask = 0ull - ((x0 >> c) & 1ull);
+                r0 ^= m[2 * c] & mask;
+                r1 ^= m[2 * c + 1] & mask;
+            }
+#pragma unroll 8
+            for (int c = 0; c < 64; ++c) {
+                uint64_t mask = 0ull - ((x1 >> c) & 1ull);
+                r0 ^= m[128 + 2 * c] & mask;
+                r1 ^= m[128 + 2 * c + 1] & mask;
+            }
+            x0 = r0;
+            x1 = r1;
+            n &= n - 1;
+        }
+    }
+};
+
+template <int PRNG> struct GenOf;
+template <> struct GenOf<0> { using T = GenLcg48; };
+template <> struct GenOf<1> { using T = GenSplitMix64; };
+template <> struct GenOf<2> { using T = GenL64X128Mix; };
+
+__device__ __forceinline__ double m53_to_double(uint64_t m) {
+    return (double)m * 0x1p-53;   // exact: m < 2^53
+}
+
+// ---------------------------------------------------------------------------
+// exact binary64 product RN(j * w) with w = M * 2^(E - 1075), M in [2^52, 2^53)
+// ---------------------------------------------------------------------------
+// j < 2^24.  Normalise j to jn = j << lz (bit 31 set); the 85-bit product
+// P' = jn * M = T * 2^32 + lo has T in [2^51, 2^53).  Keep the top 53 bits q,
+// round to nearest even on the remaining bits, and assemble the exponent by
+// hand: the result is q * 2^(32 - s - lz + E - 1075), s = 1 when T < 2^52.
+// Adding q (hidden bit included) to (exponent - 1) << 52 carries correctly when
+// rounding produces q = 2^53.  Bit-identical to IEEE RN-even j * w.
+__device__ __forceinline__ uint64_t mul_j_w_bits(uint32_t j, uint64_t M, int E) {
+    if (j == 0) return 0ull;
+    int lz = __clz((int)j);
+    uint32_t jn = j << lz;
+    uint64_t A = (uint64_t)jn * (uint32_t)M;
+    uint64_t B = (uint64_t)jn * (uint32_t)(M >> 32);
+    uint64_t T = B + (A >> 32);
+    uint32_t lo = (uint32_t)A;
+    uint32_t s = (uint32_t)(T >> 52) ^ 1u;
+    uint64_t q = (T << s) | ((uint64_t)lo >> (32 - s));
+    uint32_t rem = lo << s;
+    uint32_t up = (uint32_t)(rem > 0x80000000u) | ((uint32_t)(rem == 0x80000000u) & (uint32_t)q);
+    q += up;
+    return ((uint64_t)(E + 31 - (int)s - lz) << 52) + q;
+}
+
+// RN-even binary64 -> bfloat16 bits (finite, normal-range inputs).
+__device__ __forceinline__ uint16_t f64_to_bf16_bits(double x) {
+    uint64_t b = (uint64_t)__double_as_longlong(x);
+    uint64_t sign = b >> 63;
+    uint64_t mag = b & 0x7FFFFFFFFFFFFFFFull;
+    if (mag == 0) return (uint16_t)(sign << 15);
+    uint64_t q = mag >> 45;
+    uint64_t rem = mag & ((1ull << 45) - 1);
+    const uint64_t half = 1ull << 44;
+    q += (rem > half) | ((rem == half) & (q & 1));
+    uint64_t e = (q >> 7) - 1023 + 127;
+    return (uint16_t)((sign << 15) | (e << 7) | (q & 0x7F));
+}
+
+// RN-even binary32 -> bfloat16 bits (finite inputs).
+__device__ __forceinline__ uint16_t f32_to_bf16_bits(float x) {
+    uint32_t b = __float_as_uint(x);
+    uint32_t lsb = (b >> 16) & 1u;
+    b += 0x7FFFu + lsb;
+    return (uint16_t)(b >> 16);
+}
+
+// ---------------------------------------------------------------------------
+// warp staging: 32 rows (one per lane's unit) x 16 columns, swizzled so that
+// both the per-lane column writes and the per-row reads are bank-conflict free
+// ---------------------------------------------------------------------------
+
+template <typename T> struct Stage;
+template <> struct Stage<double> {
+    static __device__ __forceinline__ int sw(int row) { return row & 15; }
+};
+template <> struct Stage<float> {
+    static __device__ __forceinline__ int sw(int row) { return (row >> 1) & 15; }
+};
+template <> struct Stage<uint16_t> {
+    static __device__ __forceinline__ int sw(int row) { return ((row >> 2) & 7) << 1; }
+};
+
+constexpr int kStageCols = 16;
+
+template <typename T>
+__device__ __forceinline__ int stage_idx(int row, int col) {
+    return row * kStageCols + (col ^ Stage<T>::sw(row));
+}
+
+// Write the warp's staged rows: row r has cnt_r valid columns going to dst_r.
+// Two rows per step (16 lanes each).  All 32 lanes must call this.
+template <typename T>
+__device__ __forceinline__ void stage_flush(const T* stage, T* my_dst, int my_cnt, int lane) {
+    const int half = lane >> 4, c = lane & 15;
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+        int row = 2 * k + half;
+        T* dst = (T*)__shfl_sync(kFull, (unsigned long long)my_dst, row);
+        int cnt = __shfl_sync(kFull, my_cnt, row);
+        if (c < cnt) dst[c] = stage[stage_idx<T>(row, c)];
+    }
+}
+
+// Read-modify-write variant for in-place mutation: dst[c] = fmaf(sigma, z, dst[c]).
+__device__ __forceinline__ void stage_flush_fma(const float* stage, float* my_dst, int my_cnt,
+                                                int lane, float sigma) {
+    const int half = lane >> 4, c = lane & 15;
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+        int row = 2 * k + half;
+        float* dst = (float*)__shfl_sync(kFull, (unsigned long long)my_dst, row);
+        int cnt = __shfl_sync(kFull, my_cnt, row);
+        if (c < cnt) dst[c] = fmaf(sigma, stage[stage_idx<float>(row, c)], dst[c]);
+    }
+}
+
+}  // namespace zig

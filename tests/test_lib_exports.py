@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every symbol include/zig.h declares (CPU only).
+
+No compute call is made here (there is no GPU): only host-side entry points,
+argument validation that returns before touching a device, and the tables.
+"""
+
+import os
+import re
+
+import numpy as np
+
+import oracle as O
+import paper_2405_19493_gb300 as Z
+from paper_2405_19493_gb300 import _binding as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "zig.h")
+
+
+def declared():
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return sorted(set(re.findall(r"\b(zig_\w+)\s*\(", txt)))
+
+
+def test_exports_match_header():
+    lib = Z.load()
+    names = declared()
+    assert names == sorted(B.EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert os.path.dirname(os.path.abspath(B.library_path())).startswith(
+        os.path.dirname(os.path.abspath(Z.__file__)))
+
+
+def test_enums_match_header():
+    txt = open(HEADER).read()
+    for name, val in re.findall(r"\b(ZIG_\w+)\s*=\s*(\d+)", txt):
+        key = name[4:].lower()
+        if key in B.PRNG:
+            assert B.PRNG[key] == int(val)
+        elif key in B.ALG:
+            assert B.ALG[key] == int(val)
+        elif key in B.DTYPE:
+            assert B.DTYPE[key] == int(val)
+        elif name.startswith("ZIG_ERR") or name == "ZIG_OK":
+            assert B.STATUS_NAMES[int(val)] == name
+
+
+def test_tables_via_abi_equal_oracle():
+    t = Z.zig_tables_get_zig128()
+    o = O.read_zig128()
+    assert list(t["k"]) == o["k"]
+    assert list(t["w"]) == o["w"]
+    assert list(t["y"]) == o["y"]
+    assert t["R"] == o["R"]
+    assert np.all(np.abs(t["w32"].astype(np.float64) - t["w"]) <=
+                  np.spacing(t["w32"]).astype(np.float64) / 2)
+
+
+def test_status_strings_and_version():
+    for code, name in B.STATUS_NAMES.items():
+        assert Z.zig_status_string(code) == name
+    assert Z.zig_version() >= 100
+
+
+def test_host_side_argument_errors():
+    lib = Z.load()
+    # bad enum / chunk size are rejected before any device is touched
+    assert lib.zig_generate(9, 0, 8, None, 16, 4, 0, 0, 8, None, 0, None) == 1
+    assert lib.zig_generate(0, 0, 8, None, 16, 4, 25, 0, 8, None, 0, None) == 1
+    assert lib.zig_generate(0, 0, 8, None, 16, 0, 0, 0, 8, None, 0, None) == 0   # no streams: no-op
+    assert lib.zig_mutate(None, 1.0, 0, 5, 1, 0, None) == 0                      # empty population
+    assert lib.zig_mutate(8, float("nan"), 2, 5, 1, 0, None) == 1
+    assert lib.zig_prng_fill(0, 8, 4, 4, 0, 5, 8, None) == 1
+    assert Z.zig_generate_workspace_bytes(1000) >= 16 * 1000
