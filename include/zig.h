@@ -101,7 +101,7 @@ zig_status zig_tables_get_zig128(uint32_t *k_host, double *w_host, double *y_hos
  *                    having uniform_len outputs.
  * n_streams          number of streams (0 is a no-op).
  * chunk_log2         0: each stream is one sequential generator (the paper's
- *                    semantics).  c in [6, 20]: output t of stream s belongs to
+ *                    semantics).  c in [4, 24]: output t of stream s belongs to
  *                    chunk q = t >> c, generated from the seeded state advanced
  *                    by q * 2^32 raw generator steps (closed-form jump), so
  *                    long streams split across threads.  Outputs of chunk 0
@@ -109,6 +109,9 @@ zig_status zig_tables_get_zig128(uint32_t *k_host, double *w_host, double *y_hos
  * out_dev            device buffer of sum(lengths) elements of `dtype`; stream s
  *                    occupies [off_s, off_s + L_s) with off_s the exclusive
  *                    prefix sum of the lengths.  Must be aligned to the element size.
+ *                    May be NULL with lengths_dev when every length is zero; if
+ *                    they sum above zero, nothing is written and the device's
+ *                    error word latches ZIG_ERR_INVALID_ARG.
  * workspace_dev,     scratch for the variable-length path (lengths_dev != NULL):
  * workspace_bytes    at least zig_generate_workspace_bytes(n_streams) bytes,
  *                    16-byte aligned, owned by the caller and not used by any
@@ -136,8 +139,9 @@ size_t zig_generate_workspace_bytes(uint64_t n_streams);
  * motivating workload, Sec. 1: Gaussian mutation in an evolutionary algorithm).
  * x_dev: P x L binary32 row-major population (device).  Row p draws its L
  * variates from stream p of the 128-level ziggurat with binary32 output, seeded
- * seed + p, so row p's increments equal zig_generate(prng, ZIG_ZIG128, seeds =
- * {seed + p}, L, ZIG_F32) and x[p][l] = fmaf(sigma, z[p][l], x[p][l]).
+ * seed + p and split into 2^10-variate chunks, so row p's increments equal
+ * zig_generate(prng, ZIG_ZIG128, seeds = {seed + p}, uniform_len = L,
+ * chunk_log2 = 10, ZIG_F32) and x[p][l] = fmaf(sigma, z[p][l], x[p][l]).
  * P * L must be < 2^40; sigma must be finite.
  */
 zig_status zig_mutate(float *x_dev, float sigma, uint64_t P, uint64_t L, uint64_t seed,
@@ -155,8 +159,9 @@ zig_status zig_prng_fill(zig_prng prng, const uint64_t *seeds_dev, uint64_t n_st
 
 /*
  * zig_device_status -- read (and, if clear != 0, reset) the device's latched
- * error word.  Synchronizes the device.  Returns ZIG_OK, ZIG_ERR_TIMEOUT or
- * ZIG_ERR_CHUNK_OVERFLOW (the first latched condition), or ZIG_ERR_CUDA.
+ * error word.  Synchronizes the device.  Returns ZIG_OK, or the latched
+ * condition (ZIG_ERR_INVALID_ARG for a NULL output with nonzero lengths, then
+ * ZIG_ERR_TIMEOUT, then ZIG_ERR_CHUNK_OVERFLOW), or ZIG_ERR_CUDA.
  */
 zig_status zig_device_status(int device, int clear);
 

@@ -19,6 +19,7 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // Error bits latched in the per-device error word.
 constexpr unsigned kErrChunkOverflow = 1u;
 constexpr unsigned kErrTimeout = 2u;
+constexpr unsigned kErrNullOutput = 4u;   // variable lengths summed > 0 with out == NULL
 
 // Jump-ahead tables for 2^b raw steps, b = 0..63 (filled on the host at init).
 struct JumpTab {

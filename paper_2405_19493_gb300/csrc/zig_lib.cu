@@ -311,6 +311,11 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
 
     const int lane = threadIdx.x & 31;
     OutT* stage = stage_all[threadIdx.x >> 5];
+    if (a.out == nullptr) {   // only legal when every length is zero
+        if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0)
+            atomicOr(&d_err, kErrNullOutput);
+        return;
+    }
     const uint64_t n_units = units_total(a);
     const uint64_t n_groups = (n_units + 31) >> 5;
     const uint64_t warp_id = (uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -667,7 +672,9 @@ zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
     if ((unsigned)prng > 2u || (unsigned)alg > 2u || (unsigned)dtype > 2u) return ZIG_ERR_INVALID_ARG;
     if (chunk_log2 != 0 && (chunk_log2 < 4 || chunk_log2 > 24)) return ZIG_ERR_INVALID_ARG;
     if (n_streams == 0) return ZIG_OK;
-    if (!seeds_dev || !out_dev) return ZIG_ERR_INVALID_ARG;
+    // out_dev may be NULL only with lengths_dev (an all-zero batch); the kernel
+    // latches ZIG_ERR_INVALID_ARG in the error word if the lengths sum above zero
+    if (!seeds_dev || (!out_dev && !lengths_dev)) return ZIG_ERR_INVALID_ARG;
     const size_t esz = dtype == ZIG_F64 ? 8 : dtype == ZIG_F32 ? 4 : 2;
     if (((uintptr_t)out_dev) % esz || ((uintptr_t)seeds_dev) % 8) return ZIG_ERR_INVALID_ARG;
     if (lengths_dev == nullptr) {
@@ -777,6 +784,7 @@ zig_status zig_device_status(int device, int clear) {
         unsigned zero = 0;
         if (cudaMemcpyToSymbol(d_err, &zero, sizeof(zero)) != cudaSuccess) return ZIG_ERR_CUDA;
     }
+    if (w & kErrNullOutput) return ZIG_ERR_INVALID_ARG;
     if (w & kErrTimeout) return ZIG_ERR_TIMEOUT;
     if (w & kErrChunkOverflow) return ZIG_ERR_CHUNK_OVERFLOW;
     return ZIG_OK;

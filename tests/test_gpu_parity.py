@@ -134,6 +134,13 @@ def test_ragged_uniform(Z, n, L):
 def test_degenerate_lengths(Z):
     L = np.zeros(50, dtype=np.uint64)
     assert gen(Z, "lcg48", "zig128", W.seeds(50), lengths=L).size == 0
+    assert Z.zig_device_status(0) == 0
+    # NULL output with lengths that sum above zero: nothing written, error latched
+    lib = Z.load()
+    s, ln = dev_u64(W.seeds(2)), dev_u64(np.array([0, 3], dtype=np.uint64))
+    assert lib.zig_generate(0, 0, s.data_ptr(), ln.data_ptr(), 0, 2, 0, 0, None, None, 0, None) == 0
+    assert Z.zig_device_status(0, clear=True) == 1
+    assert Z.zig_device_status(0) == 0
     L[[0, 49]] = [3, 5]
     check(Z, "lcg48", "zig128", W.seeds(50), lengths=L)
     L = np.array([0, 0, 1], dtype=np.uint64)
