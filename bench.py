@@ -222,7 +222,8 @@ def run_gpu(args):
     Z.zig_tables_init(dev)
     stream = torch.cuda.current_stream()
 
-    seeds_np = W.seeds(N_STREAMS, base=0x5EED + rank * N_STREAMS)
+    from paper_2405_19493_gb300 import sharding
+    seeds_np = sharding.rank_seeds(rank, ws, N_STREAMS)
     seeds = torch.from_numpy(seeds_np.view(np.int64)).cuda()
     out = torch.empty(N_STREAMS * PER_STREAM, dtype=torch.float64, device="cuda")
 
@@ -255,11 +256,8 @@ def run_gpu(args):
     t_end.record(stream)
     barrier()
     clk = clocks.stop()
-    ms = t_start.elapsed_time(t_end)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = sharding.max_over_ranks(t_start.elapsed_time(t_end), dist if ws > 1 else None,
+                                 device="cuda")
     per_launch = {p: [events[s][k][0].elapsed_time(events[s][k][1]) for s in range(args.steps)]
                   for k, p in enumerate(PRNGS)}
     variates_step = 3 * N_STREAMS * PER_STREAM
