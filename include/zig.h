@@ -45,7 +45,8 @@ typedef enum {
     ZIG_ERR_BUDGET = 4,          /* a request exceeds the admission budget */
     ZIG_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
     ZIG_ERR_CHUNK_OVERFLOW = 6,  /* a chunk consumed more than 2^32 raw draws */
-    ZIG_ERR_UNSUPPORTED = 7      /* the device is not sm_103 or the combination is not built */
+    ZIG_ERR_UNSUPPORTED = 7,     /* the device is not sm_103 or the combination is not built */
+    ZIG_ERR_TOO_LARGE = 8        /* more streams than zig_generate_noalloc's fixed scratch holds */
 } zig_status;
 
 /* Uniform generators (Sec. 2, first list; Sec. 3 for LXM). */
@@ -133,6 +134,40 @@ zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t *seeds_dev,
 
 /* Bytes of workspace zig_generate needs for n_streams variable-length streams. */
 size_t zig_generate_workspace_bytes(uint64_t n_streams);
+
+/*
+ * zig_generate_noalloc -- zig_generate for a variable-length batch, with no
+ * allocation of any kind.  The paper has no counterpart: this is an
+ * integration entry point for callers that cannot allocate device memory at
+ * call time, e.g. a service that has carved all of HBM into its own pools
+ * before serving, a latency-bound loop that cannot absorb cudaMalloc's implicit
+ * device synchronization, or a host that forbids allocations outside its
+ * start-up phase.  It computes exactly what zig_generate computes for the same
+ * arguments with lengths_dev != NULL (uniform batches need no scratch: use
+ * zig_generate with lengths_dev = NULL).
+ *
+ * Its scratch (the per-stream output offsets and unit starts, 16 B per stream)
+ * is a fixed array of ZIG_NOALLOC_MAX_STREAMS entries compiled into the
+ * library: 1 MiB + 16 B of device memory that every GPU which loads the
+ * library holds until the process exits.  The caller still owns and passes
+ * seeds_dev, lengths_dev and out_dev, with the meanings and layout of
+ * zig_generate.
+ *  - n_streams > ZIG_NOALLOC_MAX_STREAMS returns ZIG_ERR_TOO_LARGE with nothing
+ *    enqueued; split the batch or use zig_generate.
+ *  - The first call on a device resolves the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.  zig_tables_init(device) must come first.
+ *  - Every call shares the one array and leaves its contents behind; each call
+ *    rewrites all of it that it reads, so nothing needs clearing.  Calls that
+ *    overlap on the GPU (e.g. on two streams at once) race on the array and
+ *    must be serialized by the caller.
+ * Other errors as zig_generate.
+ */
+#define ZIG_NOALLOC_MAX_STREAMS 65536u
+zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uint64_t *seeds_dev,
+                                const uint64_t *lengths_dev, uint64_t n_streams,
+                                uint32_t chunk_log2, zig_dtype dtype, void *out_dev,
+                                void *stream);
 
 /*
  * zig_mutate -- Gaussian mutation x += sigma * N(0,1) in place (the paper's

@@ -18,8 +18,10 @@ ZIG_OK = 0
 STATUS_NAMES = {
     0: "ZIG_OK", 1: "ZIG_ERR_INVALID_ARG", 2: "ZIG_ERR_NOT_INITIALIZED", 3: "ZIG_ERR_CUDA",
     4: "ZIG_ERR_BUDGET", 5: "ZIG_ERR_TIMEOUT", 6: "ZIG_ERR_CHUNK_OVERFLOW",
-    7: "ZIG_ERR_UNSUPPORTED",
+    7: "ZIG_ERR_UNSUPPORTED", 8: "ZIG_ERR_TOO_LARGE",
 }
+# fixed scratch capacity of zig_generate_noalloc (ZIG_NOALLOC_MAX_STREAMS in include/zig.h)
+NOALLOC_MAX_STREAMS = 65536
 PRNG = {"lcg48": 0, "splitmix64": 1, "l64x128mix": 2}
 ALG = {"zig128": 0, "polar": 1, "zig256": 2}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2}
@@ -30,6 +32,7 @@ FILL_KIND = {"u32": 0, "u64": 1, "m53": 2}
 EXPORTS = (
     "zig_tables_init", "zig_tables_get_zig128", "zig_generate", "zig_generate_workspace_bytes",
     "zig_mutate", "zig_prng_fill", "zig_device_status", "zig_status_string", "zig_version",
+    "zig_generate_noalloc",
 )
 
 
@@ -68,6 +71,8 @@ def load(build_if_missing: bool = True):
         lib.zig_generate_workspace_bytes.argtypes = [u64]
         lib.zig_generate_workspace_bytes.restype = C.c_size_t
         lib.zig_mutate.argtypes = [vp, C.c_float, u64, u64, u64, i32, vp]
+        lib.zig_generate_noalloc.argtypes = [i32, i32, vp, vp, u64, C.c_uint32, i32, vp, vp]
+        lib.zig_generate_noalloc.restype = i32
         lib.zig_prng_fill.argtypes = [i32, vp, u64, u64, u64, i32, vp, vp]
         lib.zig_device_status.argtypes = [i32, i32]
         lib.zig_status_string.argtypes = [i32]
@@ -126,6 +131,19 @@ def zig_generate(prng: str, alg: str, seeds, out, lengths=None, uniform_len: int
                              int(uniform_len), n, int(chunk_log2), DTYPE[dtype], out.data_ptr(),
                              ws_ptr or None, ws_bytes, _stream_ptr(stream))
     _check(st, "zig_generate")
+
+
+def zig_generate_noalloc(prng: str, alg: str, seeds, lengths, out, chunk_log2: int = 0,
+                         dtype: str = "f64", stream=None) -> None:
+    """Variable-length generation that allocates nothing, for callers that cannot
+    allocate device memory at call time (a service that pre-carved HBM into its
+    own pools, a latency-bound loop that cannot take cudaMalloc's device sync).
+    At most NOALLOC_MAX_STREAMS streams per call; calls must not overlap on the GPU.
+    """
+    st = load().zig_generate_noalloc(PRNG[prng], ALG[alg], seeds.data_ptr(), lengths.data_ptr(),
+                                     int(seeds.numel()), int(chunk_log2), DTYPE[dtype],
+                                     out.data_ptr() or None, _stream_ptr(stream))
+    _check(st, "zig_generate_noalloc")
 
 
 def zig_mutate(x, sigma: float, P: int, L: int, seed: int, prng: str = "splitmix64",

@@ -800,6 +800,7 @@ const char* zig_status_string(zig_status status) {
     case ZIG_ERR_TIMEOUT: return "ZIG_ERR_TIMEOUT";
     case ZIG_ERR_CHUNK_OVERFLOW: return "ZIG_ERR_CHUNK_OVERFLOW";
     case ZIG_ERR_UNSUPPORTED: return "ZIG_ERR_UNSUPPORTED";
+    case ZIG_ERR_TOO_LARGE: return "ZIG_ERR_TOO_LARGE";
     default: return "ZIG_ERR_UNKNOWN";
     }
 }
@@ -807,3 +808,65 @@ const char* zig_status_string(zig_status status) {
 int zig_version(void) { return 100; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// zig_generate_noalloc: the variable-length path with its scratch in a fixed
+// array compiled into the library, for callers that cannot allocate device
+// memory at call time (see include/zig.h).
+// ---------------------------------------------------------------------------
+namespace zig {
+// offsets[MAX] | unit starts[MAX] | totals[2]: 1 MiB + 16 B on every device
+// that loads the library, held until the process exits.
+static __device__ __align__(256) uint64_t g_noalloc_scratch[2 * ZIG_NOALLOC_MAX_STREAMS + 2];
+namespace host {
+// The array's device address, per device.  In host code the symbol name is
+// only a host-side stand-in; the address comes from cudaGetSymbolAddress.
+static uint64_t* g_noalloc_ptr[kMaxDevices];
+}  // namespace host
+}  // namespace zig
+
+extern "C" zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
+                                           const uint64_t* lengths_dev, uint64_t n_streams,
+                                           uint32_t chunk_log2, zig_dtype dtype, void* out_dev,
+                                           void* stream) {
+    if ((unsigned)prng > 2u || (unsigned)alg > 2u || (unsigned)dtype > 2u) return ZIG_ERR_INVALID_ARG;
+    if (chunk_log2 != 0 && (chunk_log2 < 4 || chunk_log2 > 24)) return ZIG_ERR_INVALID_ARG;
+    if (n_streams == 0) return ZIG_OK;
+    if (n_streams > ZIG_NOALLOC_MAX_STREAMS) return ZIG_ERR_TOO_LARGE;
+    if (!seeds_dev || !lengths_dev) return ZIG_ERR_INVALID_ARG;
+    const size_t esz = dtype == ZIG_F64 ? 8 : dtype == ZIG_F32 ? 4 : 2;
+    if (((uintptr_t)out_dev) % esz || ((uintptr_t)seeds_dev) % 8 || ((uintptr_t)lengths_dev) % 8)
+        return ZIG_ERR_INVALID_ARG;
+    int dev;
+    zig_status st = host::current_device(dev);
+    if (st != ZIG_OK) return st;
+    uint64_t* scratch;
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lk(host::g_mu);
+        if (!host::g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ZIG_ERR_CUDA;
+            host::g_noalloc_ptr[dev] = (uint64_t*)p;
+        }
+        scratch = host::g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    GenArgs a{};
+    a.seeds = seeds_dev;
+    a.lengths = lengths_dev;
+    a.n_streams = n_streams;
+    a.chunk_log2 = chunk_log2;
+    a.out = out_dev;
+    a.offsets = scratch;
+    a.ustart = scratch + ZIG_NOALLOC_MAX_STREAMS;
+    a.totals = scratch + 2 * ZIG_NOALLOC_MAX_STREAMS;
+    // the scan rewrites every offset, unit start and total this call reads
+    scan_kernel<<<1, 1024, 0, s>>>(lengths_dev, n_streams, chunk_log2, (uint64_t*)a.offsets,
+                                   (uint64_t*)a.ustart, (uint64_t*)a.totals);
+    if (cudaGetLastError() != cudaSuccess) return ZIG_ERR_CUDA;
+    host::GenFn fn = host::pick(alg, prng, dtype);
+    int grid = host::grid_for((const void*)fn, dev, ~0ull >> 8);
+    fn<<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
+}
