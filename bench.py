@@ -400,6 +400,26 @@ def measure_e2e(Z, torch, seeds_np, stream, args):
             "steps": steps}
 
 
+def run_case(spec: str, reps: int):
+    """One launch configuration, for profilers: alg:prng:dtype:n_streams:len[:chunk_log2]."""
+    import torch
+    import paper_2405_19493_gb300 as Z
+    from paper_2405_19493_gb300 import workloads as W
+    p = spec.split(":")
+    alg, prng, dt, n, L = p[0], p[1], p[2], int(p[3]), int(p[4])
+    c = int(p[5]) if len(p) > 5 else 0
+    Z.zig_tables_init(0)
+    seeds = torch.from_numpy(W.seeds(n).view(np.int64)).cuda()
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dt]
+    out = torch.empty(n * L, dtype=tdt, device="cuda")
+    for _ in range(reps):
+        Z.zig_generate(prng, alg, seeds, out, uniform_len=L, chunk_log2=c, dtype=dt)
+    torch.cuda.synchronize()
+    assert Z.zig_device_status(0) == 0
+    print(json.dumps({"case": spec, "reps": reps, "ok": True}))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -407,7 +427,12 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", default=None,
+                    help="run only alg:prng:dtype:n_streams:len[:chunk_log2] (for ncu)")
+    ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args(argv)
+    if args.ncu_case:
+        return run_case(args.ncu_case, args.reps)
     ws, _, _ = dist_env()
     if ws != args.gpus and not (ws == 1 and args.gpus == 1):
         print(f"warning: --gpus {args.gpus} but WORLD_SIZE={ws}", file=sys.stderr)

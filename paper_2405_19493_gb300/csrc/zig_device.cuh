@@ -83,6 +83,27 @@ struct GenLcg48 {
             n &= n - 1;
         }
     }
+    // Deferred doubles: snap() records what the next nd (1 or 2) nextDouble
+    // calls need and moves the state past them (nextDouble = 2 steps); m53_of()
+    // rebuilds the k-th of those doubles later, from the record alone.
+    static constexpr uint64_t kA2 = (kLcgA * kLcgA) & kMask48;
+    static constexpr uint64_t kC2 = (kLcgA * kLcgC + kLcgC) & kMask48;
+    static constexpr uint64_t kA4 = (kA2 * kA2) & kMask48;
+    static constexpr uint64_t kC4 = (kA2 * kC2 + kC2) & kMask48;
+    static constexpr uint32_t kStepsPerDouble = 2;
+    __device__ __forceinline__ void snap(int nd, uint64_t& b, uint64_t& c) {
+        b = s;
+        c = 0;
+        s = (nd == 1) ? ((kA2 * s + kC2) & kMask48) : ((kA4 * s + kC4) & kMask48);
+    }
+    static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t, int k) {
+        uint64_t t = k ? ((kA2 * b + kC2) & kMask48) : b;
+        t = (t * kLcgA + kLcgC) & kMask48;
+        uint64_t hi = t >> 22;   // next(26)
+        t = (t * kLcgA + kLcgC) & kMask48;
+        uint64_t lo = t >> 21;   // next(27)
+        return (hi << 27) + lo;
+    }
 };
 
 struct GenSplitMix64 {
@@ -92,6 +113,15 @@ struct GenSplitMix64 {
     __device__ __forceinline__ uint64_t next_u64() { s += kGamma; return mix64(s); }
     __device__ __forceinline__ uint64_t next_m53() { s += kGamma; return mix64(s) >> 11; }
     __device__ __forceinline__ void jump(uint64_t n, const JumpTab*) { s += n * kGamma; }
+    static constexpr uint32_t kStepsPerDouble = 1;
+    __device__ __forceinline__ void snap(int nd, uint64_t& b, uint64_t& c) {
+        b = s + kGamma;
+        c = 0;
+        s += (nd == 1) ? kGamma : 2 * kGamma;
+    }
+    static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t, int k) {
+        return mix64(k ? b + kGamma : b) >> 11;
+    }
 };
 
 struct GenL64X128Mix {
@@ -115,6 +145,22 @@ struct GenL64X128Mix {
     }
     __device__ __forceinline__ uint32_t next_u32() { return (uint32_t)(next_u64() >> 32); }
     __device__ __forceinline__ uint64_t next_m53() { return next_u64() >> 11; }
+    __device__ __forceinline__ void advance() {
+        s = kLxmM * s + a;
+        uint64_t q1 = x1 ^ x0;
+        x0 = rotl64(x0, 24) ^ q1 ^ (q1 << 16);
+        x1 = rotl64(q1, 37);
+    }
+    static constexpr uint32_t kStepsPerDouble = 1;
+    __device__ __forceinline__ void snap(int nd, uint64_t& b, uint64_t& c) {
+        b = s + x0;   // the mix input of the next step
+        advance();
+        c = s + x0;
+        if (nd == 2) advance();
+    }
+    static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t c, int k) {
+        return mix_lea64(k ? c : b) >> 11;
+    }
     __device__ void jump(uint64_t n, const JumpTab* jt) {
         while (n) {
             int b = __ffsll((long long)n) - 1;

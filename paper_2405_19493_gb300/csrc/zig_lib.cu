@@ -62,6 +62,7 @@ struct GenArgs {
     uint64_t n_units;          // uniform: number of units
     uint64_t units_per_stream; // uniform: units per stream
     float sigma;               // mutation only
+    uint64_t mut_seed;         // mutation only: row p is seeded mut_seed + p
 };
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
@@ -106,90 +107,8 @@ __device__ __forceinline__ uint64_t units_total(const GenArgs& a) {
 // ---------------------------------------------------------------------------
 // per-variate samplers
 // ---------------------------------------------------------------------------
-struct Z128Smem {
-    uint32_t kE[128];
-    uint64_t M[128];
-    double W[128];
-    double Y[128];
-    float W32[128];
-};
-
-__device__ __forceinline__ void z128_load(Z128Smem& t) {
-    for (int i = threadIdx.x; i < 128; i += blockDim.x) {
-        t.kE[i] = d_z128_kE[i];
-        t.M[i] = d_z128_M[i];
-        t.W[i] = d_z128_W[i];
-        t.Y[i] = d_z128_Y[i];
-        t.W32[i] = d_z128_W32[i];
-    }
-}
-
 __device__ __forceinline__ double neg_half_sq(double x) {
     return __dmul_rn(__dmul_rn(-0.5, x), x);
-}
-
-// Slow path of the 128-level sampler, decided in binary64 exactly as the
-// definition orders the operations.  Returns true when accepted; x is set to
-// the (non-negative) value.  `extra` counts raw draws beyond the layer draw.
-template <class G>
-__device__ __forceinline__ bool z128_slow(G& g, const Z128Smem& t, uint32_t i, uint32_t j, double& x,
-                                       uint32_t& extra) {
-    const double R = zigtab::ZIG128_R;
-    double y;
-    constexpr uint32_t kStepsPerDouble = (sizeof(G) == sizeof(GenLcg48)) ? 2u : 1u;
-    if (i < 127) {
-        x = __dmul_rn((double)j, t.W[i]);
-        double U = m53_to_double(g.next_m53());
-        y = __dadd_rn(t.Y[i + 1], __dmul_rn(__dsub_rn(t.Y[i], t.Y[i + 1]), U));
-        extra += kStepsPerDouble;
-    } else {
-        double U1 = __dsub_rn(1.0, m53_to_double(g.next_m53()));
-        double U2 = m53_to_double(g.next_m53());
-        x = __dsub_rn(R, __ddiv_rn(log(U1), R));
-        y = __dmul_rn(exp(__dmul_rn(-R, __dsub_rn(x, __dmul_rn(0.5, R)))), U2);
-        extra += 2 * kStepsPerDouble;
-    }
-    return y < exp(neg_half_sq(x));
-}
-
-// One 128-level variate as binary64 bits (sign included).
-template <class G>
-__device__ __forceinline__ uint64_t z128_f64(G& g, const Z128Smem& t, uint32_t& extra) {
-    for (;;) {
-        uint32_t u = g.next_u32();
-        uint32_t i = u & 0x7Fu;
-        uint64_t neg = (uint64_t)((~u >> 7) & 1u) << 63;   // bit 7 set -> positive
-        uint32_t j = u >> 8;
-        uint32_t kE = t.kE[i];
-        if (j < (kE & 0xFFFFFFu)) {
-            return mul_j_w_bits(j, t.M[i], (int)(kE >> 24) + 900) | neg;
-        }
-        double x;
-        if (z128_slow(g, t, i, j, x, extra)) return (uint64_t)__double_as_longlong(x) | neg;
-        ++extra;   // the restart's layer draw
-    }
-}
-
-// One 128-level variate with binary32 arithmetic on the fast path; the slow
-// path decides in binary64 and rounds its value once.
-template <class G>
-__device__ __forceinline__ float z128_f32(G& g, const Z128Smem& t, uint32_t& extra) {
-    for (;;) {
-        uint32_t u = g.next_u32();
-        uint32_t i = u & 0x7Fu;
-        uint32_t negbit = ((~u >> 7) & 1u) << 31;
-        uint32_t j = u >> 8;
-        if (j < (t.kE[i] & 0xFFFFFFu)) {
-            float x = __fmul_rn((float)j, t.W32[i]);
-            return __uint_as_float(__float_as_uint(x) | negbit);
-        }
-        double x;
-        if (z128_slow(g, t, i, j, x, extra)) {
-            float xf = __double2float_rn(x);
-            return __uint_as_float(__float_as_uint(xf) | negbit);
-        }
-        ++extra;   // the restart's layer draw
-    }
 }
 
 // Polar method with the cached second variate.
@@ -302,10 +221,9 @@ template <int ALG, int PRNG, int DT>
 __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
     using G = typename GenOf<PRNG>::T;
     using OutT = typename OutOf<DT>::T;
-    __shared__ Z128Smem t128;
+    static_assert(ALG == ZIG_POLAR || ALG == ZIG_ZIG256, "zig128 runs in z128_kernel");
     __shared__ Z256Smem t256;
     __shared__ OutT stage_all[kWarps][32 * kStageCols];
-    if (ALG == ZIG_ZIG128) z128_load(t128);
     if (ALG == ZIG_ZIG256) z256_load(t256);
     __syncthreads();
 
@@ -346,15 +264,7 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
             for (int v = 0; v < kStageCols; ++v) {
                 if (v < cnt) {
                     OutT z;
-                    if (ALG == ZIG_ZIG128) {
-                        if (DT == ZIG_F64) {
-                            z = __longlong_as_double((long long)z128_f64(g, t128, extra));
-                        } else if (DT == ZIG_F32) {
-                            z = z128_f32(g, t128, extra);
-                        } else {
-                            z = f32_to_bf16_bits(z128_f32(g, t128, extra));
-                        }
-                    } else if (ALG == ZIG_POLAR) {
+                    if (ALG == ZIG_POLAR) {
                         z = from_f64<DT>(polar_f64(g, have, cached, extra));
                     } else {
                         z = from_f64<DT>(z256_f64(g, t256, extra));
@@ -371,58 +281,261 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
         // A chunk must stay inside its 2^32-draw window.  Each variate's first
         // draw takes `per` raw steps; `extra` counts every other step.
         if (a.chunk_log2 && n_unit) {
-            const uint64_t per = (ALG == ZIG_ZIG256 && PRNG == ZIG_LCG48) ? 2 : 1;
+            const uint64_t per = (PRNG == ZIG_LCG48) ? 2 : 1;   // zig256's first draw is a nextLong
             uint64_t draws = (ALG == ZIG_POLAR) ? (uint64_t)extra : n_unit * per + extra;
             if (draws > kChunkDraws) atomicOr(&d_err, kErrChunkOverflow);
         }
     }
 }
 
-// Mutation: x[p][l] = fmaf(sigma, z, x[p][l]) with z the binary32 128-level
-// variates of stream seed + p, chunked by 2^10.
-template <int PRNG>
-__global__ void __launch_bounds__(kBlock) mutate_kernel(float* x, float sigma, uint64_t P,
-                                                        uint64_t L, uint64_t seed,
-                                                        uint64_t units_per_row) {
+// ---------------------------------------------------------------------------
+// 128-level ziggurat, batched slow path (v2)
+// ---------------------------------------------------------------------------
+// Per warp and per batch of up to 16 outputs per lane:
+//  A. every lane draws its candidates in lockstep.  A fast-path candidate
+//     (j < k[i]) goes straight into the lane's staging row.  A slow one leaves a
+//     placeholder and a record in the warp's ring queue: (i, j, sign, row, slot)
+//     plus a snapshot from which the wedge's / tail's doubles can be rebuilt;
+//     the lane's generator moves past those doubles at once, so it keeps drawing.
+//  B. whenever 32 records are queued (and at the end of the batch) all 32 lanes
+//     decide 32 records together: wedge tests in binary32 with a proven margin
+//     (binary64 only inside it), tails in binary64.  Accepted values land in their
+//     slot; rejected slots are flagged.
+//  C. each row drops its rejected slots and is flushed with its own count; the
+//     stream simply continues in the next batch.
+// The stream's outputs are its accepted candidates in draw order, exactly as a
+// sequential loop would produce them.
+
+struct Z128Tab {
+    uint32_t kE[128];   // K[i] | (E(w[i]) - 900) << 24
+    uint64_t M[128];    // significand of w[i]
+    float W32[128];     // RN32(x_{i+1} / 2^24)
+    float Y32[128];     // RN32(y[i])
+    float DY32[128];    // RN32(y[i] - y[i+1]) (i < 127)
+    double W[128];
+    double Y[128];
+};
+__device__ float d_z128_Y32[128];
+__device__ float d_z128_DY32[128];
+
+__device__ __forceinline__ void z128tab_load(Z128Tab& t) {
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+        t.kE[i] = d_z128_kE[i];
+        t.M[i] = d_z128_M[i];
+        t.W32[i] = d_z128_W32[i];
+        t.Y32[i] = d_z128_Y32[i];
+        t.DY32[i] = d_z128_DY32[i];
+        t.W[i] = d_z128_W[i];
+        t.Y[i] = d_z128_Y[i];
+    }
+}
+
+struct SlowRec {
+    uint64_t a;   // j | i << 24 | neg << 31 | row << 32 | slot << 37 | tail << 41
+    uint64_t b, c;
+};
+constexpr int kQCap = 64;   // ring capacity: at most 31 left + 32 new per step
+
+template <int DT> struct Z128Out;
+template <> struct Z128Out<ZIG_F64> {
+    using T = double;
+    static __device__ __forceinline__ double fast(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
+        uint32_t kE = t.kE[i];
+        return __longlong_as_double(
+            (long long)(mul_j_w_bits(j, t.M[i], (int)(kE >> 24) + 900) | ((uint64_t)neg << 63)));
+    }
+    static __device__ __forceinline__ double from64(double x, uint32_t neg) {
+        return __longlong_as_double((long long)((uint64_t)__double_as_longlong(x) | ((uint64_t)neg << 63)));
+    }
+};
+template <> struct Z128Out<ZIG_F32> {
+    using T = float;
+    static __device__ __forceinline__ float fast(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
+        return __uint_as_float(__float_as_uint(__fmul_rn((float)j, t.W32[i])) | (neg << 31));
+    }
+    static __device__ __forceinline__ float from64(double x, uint32_t neg) {
+        return __uint_as_float(__float_as_uint(__double2float_rn(x)) | (neg << 31));
+    }
+};
+template <> struct Z128Out<ZIG_BF16> {
+    using T = uint16_t;
+    static __device__ __forceinline__ uint16_t fast(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
+        return f32_to_bf16_bits(Z128Out<ZIG_F32>::fast(t, i, j, neg));
+    }
+    static __device__ __forceinline__ uint16_t from64(double x, uint32_t neg) {
+        return f32_to_bf16_bits(Z128Out<ZIG_F32>::from64(x, neg));
+    }
+};
+
+// Decide one queued record; returns true if accepted, with its output value.
+template <class G, int DT>
+__device__ __forceinline__ bool z128_decide(const Z128Tab& t, const SlowRec& r,
+                                            typename Z128Out<DT>::T& val) {
+    const uint32_t j = (uint32_t)(r.a & 0xFFFFFF);
+    const uint32_t i = (uint32_t)((r.a >> 24) & 0x7F);
+    const uint32_t neg = (uint32_t)((r.a >> 31) & 1);
+    const bool is_tail = (r.a >> 41) & 1;
+    const uint64_t m1 = G::m53_of(r.b, r.c, 0);
+    if (!is_tail) {
+        // binary32 filter: |y32/y - 1| + |e32/e - 1| <= 2.6e-6 < 2^-16 (expf: <= 2 ulp)
+        const float x32 = __fmul_rn((float)j, t.W32[i]);
+        const float e32 = expf(__fmul_rn(__fmul_rn(-0.5f, x32), x32));
+        const float u32 = (float)(uint32_t)(m1 >> 29) * 0x1p-24f;
+        const float y32 = __fadd_rn(t.Y32[i + 1], __fmul_rn(t.DY32[i], u32));
+        bool acc;
+        if (y32 < e32 * (1.0f - 0x1p-16f)) {
+            acc = true;
+        } else if (y32 > e32 * (1.0f + 0x1p-16f)) {
+            acc = false;
+        } else {
+            // inside the margin: the binary64 test exactly as defined
+            const double x = __dmul_rn((double)j, t.W[i]);
+            const double U = m53_to_double(m1);
+            const double y = __dadd_rn(t.Y[i + 1], __dmul_rn(__dsub_rn(t.Y[i], t.Y[i + 1]), U));
+            acc = y < exp(neg_half_sq(x));
+        }
+        if (acc) val = Z128Out<DT>::fast(t, i, j, neg);
+        return acc;
+    }
+    const double R = zigtab::ZIG128_R;
+    const double U1 = __dsub_rn(1.0, m53_to_double(m1));
+    const double U2 = m53_to_double(G::m53_of(r.b, r.c, 1));
+    const double x = __dsub_rn(R, __ddiv_rn(log(U1), R));
+    const double y = __dmul_rn(exp(__dmul_rn(-R, __dsub_rn(x, __dmul_rn(0.5, R)))), U2);
+    const bool acc = y < exp(neg_half_sq(x));
+    if (acc) val = Z128Out<DT>::from64(x, neg);
+    return acc;
+}
+
+template <typename OutT>
+__host__ __device__ constexpr size_t z128_warp_bytes() {
+    return 128 + kQCap * sizeof(SlowRec) + 32 * kStageCols * sizeof(OutT);
+}
+
+// MODE 0: generation into a.out; MODE 1: mutation x += sigma * z (binary32).
+template <int PRNG, int DT, int MODE>
+__global__ void __launch_bounds__(kBlock) z128_kernel(GenArgs a) {
     using G = typename GenOf<PRNG>::T;
-    __shared__ Z128Smem t128;
-    __shared__ float stage_all[kWarps][32 * kStageCols];
-    z128_load(t128);
+    using OutT = typename Z128Out<DT>::T;
+    __shared__ Z128Tab t;
+    // dynamic: per warp [rej u32 x 32][ring SlowRec x kQCap][stage OutT x 32 x 16]
+    extern __shared__ __align__(16) unsigned char z128_dsm[];
+    z128tab_load(t);
     __syncthreads();
+
     const int lane = threadIdx.x & 31;
-    float* stage = stage_all[threadIdx.x >> 5];
-    const uint64_t n_units = P * units_per_row;
+    const int wib = threadIdx.x >> 5;
+    unsigned char* wbase = z128_dsm + (size_t)wib * z128_warp_bytes<OutT>();
+    uint32_t* rej = (uint32_t*)wbase;
+    SlowRec* q = (SlowRec*)(wbase + 128);
+    OutT* stage = (OutT*)(wbase + 128 + kQCap * sizeof(SlowRec));
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    if (MODE == 0 && a.out == nullptr) {   // only legal when every length is zero
+        if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0)
+            atomicOr(&d_err, kErrNullOutput);
+        return;
+    }
+    const uint64_t n_units = units_total(a);
     const uint64_t n_groups = (n_units + 31) >> 5;
-    const uint64_t warp_id = (uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const uint64_t warp_id = (uint64_t)blockIdx.x * kWarps + wib;
     const uint64_t warp_stride = (uint64_t)gridDim.x * kWarps;
-    constexpr uint32_t kC = 10;
+    OutT* out = (OutT*)a.out;
+
     for (uint64_t grp = warp_id; grp < n_groups; grp += warp_stride) {
-        uint64_t u = grp * 32 + lane;
+        const uint64_t u = grp * 32 + lane;
         uint64_t rem = 0;
-        float* dst = x;
+        OutT* dst = out;
         G g;
         g.seed(0);
         if (u < n_units) {
-            uint64_t p = u / units_per_row, q = u - p * units_per_row;
-            g.seed(seed + p);
-            if (q) g.jump(q * kChunkDraws, &d_jump);
-            uint64_t t0 = q << kC;
-            rem = umin64(L - t0, (uint64_t)1 << kC);
-            dst = x + p * L + t0;
+            uint64_t s, qd, off, n;
+            unit_info(a, u, s, qd, off, n);
+            g.seed(MODE == 0 ? a.seeds[s] : a.mut_seed + s);   // mutation: seed + row
+            if (qd) g.jump(qd * kChunkDraws, &d_jump);
+            rem = n;
+            dst = out + off;
         }
-        uint32_t extra = 0;
+        uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
+        const bool check_chunk = a.chunk_log2 != 0 && rem != 0;
+        uint32_t head = 0, tail = 0;   // warp-uniform ring indices
+
         while (__any_sync(kFull, rem > 0)) {
             const int cnt = (int)umin64(rem, (uint64_t)kStageCols);
+            rej[lane] = 0;
+            draws += (uint64_t)cnt;
+            __syncwarp();
 #pragma unroll 1
             for (int v = 0; v < kStageCols; ++v) {
-                if (v < cnt) stage[stage_idx<float>(lane, v)] = z128_f32(g, t128, extra);
+                bool slow = false;
+                SlowRec r;
+                if (v < cnt) {
+                    const uint32_t w = g.next_u32();
+                    const uint32_t i = w & 0x7Fu;
+                    const uint32_t neg = (~w >> 7) & 1u;   // bit 7 set -> positive
+                    const uint32_t j = w >> 8;
+                    if (j < (t.kE[i] & 0xFFFFFFu)) {
+                        stage[stage_idx<OutT>(lane, v)] = Z128Out<DT>::fast(t, i, j, neg);
+                    } else {
+                        slow = true;
+                        const int nd = (i == 127) ? 2 : 1;
+                        g.snap(nd, r.b, r.c);
+                        draws += (uint64_t)nd * G::kStepsPerDouble;
+                        r.a = (uint64_t)j | ((uint64_t)i << 24) | ((uint64_t)neg << 31) |
+                              ((uint64_t)lane << 32) | ((uint64_t)v << 37) | ((uint64_t)(nd - 1) << 41);
+                    }
+                }
+                const uint32_t m = __ballot_sync(kFull, slow);
+                if (m) {
+                    if (slow) q[(tail + __popc(m & lt_mask)) & (kQCap - 1)] = r;
+                    tail += __popc(m);
+                    if (tail - head >= 32) {
+                        __syncwarp();
+                        SlowRec rr = q[(head + lane) & (kQCap - 1)];
+                        OutT val;
+                        const uint32_t row = (uint32_t)(rr.a >> 32) & 31u, slot = (uint32_t)(rr.a >> 37) & 15u;
+                        if (z128_decide<G, DT>(t, rr, val)) stage[stage_idx<OutT>(row, slot)] = val;
+                        else atomicOr(&rej[row], 1u << slot);
+                        head += 32;
+                        __syncwarp();
+                    }
+                }
+            }
+            // drain the records left in this batch
+            while (tail != head) {
+                __syncwarp();
+                const uint32_t n = umin64(tail - head, 32);
+                if ((uint32_t)lane < n) {
+                    SlowRec rr = q[(head + lane) & (kQCap - 1)];
+                    OutT val;
+                    const uint32_t row = (uint32_t)(rr.a >> 32) & 31u, slot = (uint32_t)(rr.a >> 37) & 15u;
+                    if (z128_decide<G, DT>(t, rr, val)) stage[stage_idx<OutT>(row, slot)] = val;
+                    else atomicOr(&rej[row], 1u << slot);
+                }
+                head += n;
             }
             __syncwarp();
-            stage_flush_fma(stage, dst, cnt, lane, sigma);
+            // drop rejected slots (a rejection costs the stream one extra layer draw,
+            // already counted: the next batch draws it as a new candidate)
+            const uint32_t rj = rej[lane];
+            int acc = cnt;
+            if (rj) {
+                int wpos = 0;
+                for (int v = 0; v < cnt; ++v) {
+                    if (!((rj >> v) & 1u)) {
+                        stage[stage_idx<OutT>(lane, wpos)] = stage[stage_idx<OutT>(lane, v)];
+                        ++wpos;
+                    }
+                }
+                acc = wpos;
+            }
             __syncwarp();
-            dst += cnt;
-            rem -= cnt;
+            if (MODE == 0) stage_flush<OutT>(stage, dst, acc, lane);
+            else stage_flush_fma((const float*)stage, (float*)dst, acc, lane, a.sigma);
+            __syncwarp();
+            dst += acc;
+            rem -= (uint64_t)acc;
         }
+        if (check_chunk && draws > kChunkDraws) atomicOr(&d_err, kErrChunkOverflow);
     }
 }
 
@@ -566,6 +679,13 @@ static zig_status init_device(int device) {
     ZIG_CUDA(cudaMemcpyToSymbol(d_z128_W, zigtab::ZIG128_W, sizeof(zigtab::ZIG128_W)));
     ZIG_CUDA(cudaMemcpyToSymbol(d_z128_Y, zigtab::ZIG128_Y, sizeof(zigtab::ZIG128_Y)));
     ZIG_CUDA(cudaMemcpyToSymbol(d_z128_W32, zigtab::ZIG128_W32, sizeof(zigtab::ZIG128_W32)));
+    float y32[128], dy32[128];
+    for (int i = 0; i < 128; ++i) {
+        y32[i] = (float)zigtab::ZIG128_Y[i];
+        dy32[i] = i < 127 ? (float)(zigtab::ZIG128_Y[i] - zigtab::ZIG128_Y[i + 1]) : 0.0f;
+    }
+    ZIG_CUDA(cudaMemcpyToSymbol(d_z128_Y32, y32, sizeof(y32)));
+    ZIG_CUDA(cudaMemcpyToSymbol(d_z128_DY32, dy32, sizeof(dy32)));
     const int nr = zigtab::ZIG256_NR;
     double xs[256] = {0};
     std::memcpy(xs, zigtab::ZIG256_XS, sizeof(double) * nr);
@@ -600,10 +720,18 @@ typedef void (*GenFn)(GenArgs);
 
 template <int ALG, int PRNG>
 static GenFn pick_dt(int dt) {
-    switch (dt) {
-    case ZIG_F64: return gen_kernel<ALG, PRNG, ZIG_F64>;
-    case ZIG_F32: return gen_kernel<ALG, PRNG, ZIG_F32>;
-    default: return gen_kernel<ALG, PRNG, ZIG_BF16>;
+    if constexpr (ALG == ZIG_ZIG128) {
+        switch (dt) {
+        case ZIG_F64: return z128_kernel<PRNG, ZIG_F64, 0>;
+        case ZIG_F32: return z128_kernel<PRNG, ZIG_F32, 0>;
+        default: return z128_kernel<PRNG, ZIG_BF16, 0>;
+        }
+    } else {
+        switch (dt) {
+        case ZIG_F64: return gen_kernel<ALG, PRNG, ZIG_F64>;
+        case ZIG_F32: return gen_kernel<ALG, PRNG, ZIG_F32>;
+        default: return gen_kernel<ALG, PRNG, ZIG_BF16>;
+        }
     }
 }
 template <int ALG>
@@ -622,9 +750,25 @@ static GenFn pick(int alg, int prng, int dt) {
     }
 }
 
-static int grid_for(const void* fn, int dev, uint64_t n_groups) {
+// Dynamic shared memory a kernel needs (0 for the kernels that use static only).
+static size_t dyn_smem_of(int alg, int dt) {
+    if (alg != ZIG_ZIG128) return 0;
+    size_t per = dt == ZIG_F64 ? z128_warp_bytes<double>()
+               : dt == ZIG_F32 ? z128_warp_bytes<float>() : z128_warp_bytes<uint16_t>();
+    return per * kWarps;
+}
+
+// Opt in to the dynamic shared memory a launch needs (static + dynamic may pass
+// the 48 KB default only with the attribute set).
+static bool allow_dyn_smem(const void* fn, size_t bytes) {
+    if (bytes == 0) return true;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+           cudaSuccess;
+}
+
+static int grid_for(const void* fn, int dev, uint64_t n_groups, size_t dyn = 0) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, dyn) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     uint64_t full = (uint64_t)g_sms[dev] * per_sm;
@@ -727,8 +871,10 @@ zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
         n_groups_hint = ~0ull >> 8;   // unknown on the host: fill the device
     }
     host::GenFn fn = host::pick(alg, prng, dtype);
-    int grid = host::grid_for((const void*)fn, dev, n_groups_hint);
-    fn<<<grid, kBlock, 0, s>>>(a);
+    const size_t dyn = host::dyn_smem_of(alg, dtype);
+    if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
+    int grid = host::grid_for((const void*)fn, dev, n_groups_hint, dyn);
+    fn<<<grid, kBlock, dyn, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
 }
 
@@ -744,13 +890,25 @@ zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_
     const uint64_t upr = (L + 1023) >> 10;
     const uint64_t groups = (P * upr + 31) / 32;
     cudaStream_t s = (cudaStream_t)stream;
-    const void* fn = prng == ZIG_LCG48 ? (const void*)mutate_kernel<0>
-                   : prng == ZIG_SPLITMIX64 ? (const void*)mutate_kernel<1>
-                                            : (const void*)mutate_kernel<2>;
-    int grid = host::grid_for(fn, dev, groups);
-    if (prng == ZIG_LCG48) mutate_kernel<0><<<grid, kBlock, 0, s>>>(x_dev, sigma, P, L, seed, upr);
-    else if (prng == ZIG_SPLITMIX64) mutate_kernel<1><<<grid, kBlock, 0, s>>>(x_dev, sigma, P, L, seed, upr);
-    else mutate_kernel<2><<<grid, kBlock, 0, s>>>(x_dev, sigma, P, L, seed, upr);
+    GenArgs a{};
+    a.uniform_len = L;          // row length
+    a.n_streams = P;
+    a.chunk_log2 = 10;
+    a.out = x_dev;
+    a.units_per_stream = upr;
+    a.n_units = P * upr;
+    a.sigma = sigma;
+    a.seeds = nullptr;
+    // the kernel seeds row p with a.uniform_len + p in mutation mode; pass seed there
+    GenArgs am = a;
+    host::GenFn fn = prng == ZIG_LCG48 ? z128_kernel<0, ZIG_F32, 1>
+                   : prng == ZIG_SPLITMIX64 ? z128_kernel<1, ZIG_F32, 1>
+                                            : z128_kernel<2, ZIG_F32, 1>;
+    am.mut_seed = seed;
+    const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32);
+    if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
+    int grid = host::grid_for((const void*)fn, dev, groups, dyn);
+    fn<<<grid, kBlock, dyn, s>>>(am);
     return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
 }
 
@@ -866,7 +1024,9 @@ extern "C" zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uin
                                    (uint64_t*)a.ustart, (uint64_t*)a.totals);
     if (cudaGetLastError() != cudaSuccess) return ZIG_ERR_CUDA;
     host::GenFn fn = host::pick(alg, prng, dtype);
-    int grid = host::grid_for((const void*)fn, dev, ~0ull >> 8);
-    fn<<<grid, kBlock, 0, s>>>(a);
+    const size_t dyn = host::dyn_smem_of(alg, dtype);
+    if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
+    int grid = host::grid_for((const void*)fn, dev, ~0ull >> 8, dyn);
+    fn<<<grid, kBlock, dyn, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
 }
