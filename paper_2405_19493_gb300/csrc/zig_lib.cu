@@ -289,29 +289,36 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// 128-level ziggurat, batched slow path (v2)
+// 128-level ziggurat (GSL form): one launch per bulk request
 // ---------------------------------------------------------------------------
-// Per warp and per batch of up to 16 outputs per lane:
-//  A. every lane draws its candidates in lockstep.  A fast-path candidate
-//     (j < k[i]) goes straight into the lane's staging row.  A slow one leaves a
-//     placeholder and a record in the warp's ring queue: (i, j, sign, row, slot)
-//     plus a snapshot from which the wedge's / tail's doubles can be rebuilt;
-//     the lane's generator moves past those doubles at once, so it keeps drawing.
-//  B. whenever 32 records are queued (and at the end of the batch) all 32 lanes
-//     decide 32 records together: wedge tests in binary32 with a proven margin
-//     (binary64 only inside it), tails in binary64.  Accepted values land in their
-//     slot; rejected slots are flagged.
-//  C. each row drops its rejected slots and is flushed with its own count; the
-//     stream simply continues in the next batch.
-// The stream's outputs are its accepted candidates in draw order, exactly as a
-// sequential loop would produce them.
+// Each lane owns one unit (stream or chunk) with its generator in registers.
+// A warp works in batches of up to 16 outputs per lane:
+//  A. the lanes draw candidates in lockstep, two per step.  A fast-path
+//     candidate (j < k[i]) is finished on the spot: x = RN(j * w[i]) is built
+//     exactly with integer arithmetic (binary64) or as fl32(j * w32[i])
+//     (binary32/bfloat16).  A slow candidate (wedge or tail) keeps a
+//     placeholder slot and pushes a 16-byte record into the warp's ring: the
+//     layer, j, sign, (row, slot) and either a snapshot of the generator from
+//     which its uniform double is rebuilt (wedge) or the two uniforms (tail).
+//     The lane's generator moves past those doubles at once and keeps drawing.
+//  B. whenever 32 records wait (and at the end of a batch) all 32 lanes decide
+//     32 records together: the wedge test in binary32 with a proven margin,
+//     binary64 only inside it; the tail in binary64.
+//  C. each row drops its rejected slots and is flushed, two rows per warp store,
+//     with its own count; the stream continues in the next batch.
+// The outputs of a unit are its accepted candidates in draw order: exactly the
+// sequence a one-variate-at-a-time loop produces.
+
+constexpr int kZBlock = 1024;               // one block per SM
+constexpr int kZWarps = kZBlock / 32;
+constexpr int kQCap = 64;                   // ring: <= 31 waiting + 32 new per step
 
 struct Z128Tab {
-    uint32_t kE[128];   // K[i] | (E(w[i]) - 900) << 24
-    uint64_t M[128];    // significand of w[i]
-    float W32[128];     // RN32(x_{i+1} / 2^24)
-    float Y32[128];     // RN32(y[i])
-    float DY32[128];    // RN32(y[i] - y[i+1]) (i < 127)
+    uint32_t kE[128][32];   // K[i] | (E(w[i]) - 900) << 24, one copy per lane
+    uint2 M[128][16];       // significand of w[i] as (low 32, high 21 bits), 16 copies
+    float W32[128];         // RN32(x_{i+1} / 2^24)
+    float Y32[128];         // RN32(y[i])
+    float DY32[128];        // RN32(y[i] - y[i+1])
     double W[128];
     double Y[128];
 };
@@ -319,9 +326,15 @@ __device__ float d_z128_Y32[128];
 __device__ float d_z128_DY32[128];
 
 __device__ __forceinline__ void z128tab_load(Z128Tab& t) {
+    for (int k = threadIdx.x; k < 128 * 32; k += blockDim.x) {
+        const int i = k >> 5, c = k & 31;
+        t.kE[i][c] = d_z128_kE[i];
+        if (c < 16) {
+            const uint64_t m = d_z128_M[i];
+            t.M[i][c] = make_uint2((uint32_t)m, (uint32_t)(m >> 32));
+        }
+    }
     for (int i = threadIdx.x; i < 128; i += blockDim.x) {
-        t.kE[i] = d_z128_kE[i];
-        t.M[i] = d_z128_M[i];
         t.W32[i] = d_z128_W32[i];
         t.Y32[i] = d_z128_Y32[i];
         t.DY32[i] = d_z128_DY32[i];
@@ -330,95 +343,207 @@ __device__ __forceinline__ void z128tab_load(Z128Tab& t) {
     }
 }
 
+// RN(j * w) as binary64 bits, w = (mh:ml) * 2^(E - 1075), j < 2^24, with
+// eb = E - 900 from the table word.  Same arithmetic as mul_j_w_bits, written
+// on 32-bit words and selects so that it has no branch; j = 0 gives +0.
+__device__ __forceinline__ uint64_t mul_j_w_bits32(uint32_t j, uint32_t ml, uint32_t mh, uint32_t eb) {
+    const uint32_t lz = __clz((int)j);                 // 8..31; 32 for j = 0
+    const uint32_t jn = j << (lz & 31);
+    const uint64_t A = (uint64_t)jn * ml;
+    const uint64_t B = (uint64_t)jn * mh;
+    const uint64_t T = B + (A >> 32);
+    const uint32_t lo = (uint32_t)A;
+    const uint32_t Tl = (uint32_t)T, Th = (uint32_t)(T >> 32);
+    const bool s = Th < (1u << 20);                    // T < 2^52: shift one more bit in
+    const uint32_t qh = s ? __funnelshift_l(Tl, Th, 1) : Th;
+    const uint32_t ql = s ? __funnelshift_l(lo, Tl, 1) : Tl;
+    const uint32_t rem = s ? (lo << 1) : lo;
+    const uint32_t up = (uint32_t)(rem > 0x80000000u) | ((uint32_t)(rem == 0x80000000u) & ql);
+    const uint64_t q = (((uint64_t)qh << 32) | ql) + (up & 1u);
+    const uint32_t ex = eb + 931u - (uint32_t)s - lz;  // biased exponent - 1
+    const uint64_t bits = ((uint64_t)ex << 52) + q;
+    return j ? bits : 0ull;
+}
+
+// Slow-candidate record (16 bytes).
+//   a: bits 53..57 row, 58..61 slot, 62 negative, 63 tail;
+//      wedge: bits 0..23 j, 24..30 layer i;  tail: bits 0..52 the first uniform (m53)
+//   b: wedge: the generator snapshot for its uniform;  tail: the second uniform (m53)
 struct SlowRec {
-    uint64_t a;   // j | i << 24 | neg << 31 | row << 32 | slot << 37 | tail << 41
-    uint64_t b, c;
+    uint64_t a, b;
 };
-constexpr int kQCap = 64;   // ring capacity: at most 31 left + 32 new per step
 
 template <int DT> struct Z128Out;
 template <> struct Z128Out<ZIG_F64> {
     using T = double;
-    static __device__ __forceinline__ double fast(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
-        uint32_t kE = t.kE[i];
+    using Pair = double2;
+    static __device__ __forceinline__ double fast(const Z128Tab& t, uint32_t i, uint32_t j,
+                                                  uint32_t negbit, int lane, uint32_t kE) {
+        const uint2 m = t.M[i][lane & 15];
         return __longlong_as_double(
-            (long long)(mul_j_w_bits(j, t.M[i], (int)(kE >> 24) + 900) | ((uint64_t)neg << 63)));
+            (long long)(mul_j_w_bits32(j, m.x, m.y, kE >> 24) | ((uint64_t)negbit << 63)));
     }
     static __device__ __forceinline__ double from64(double x, uint32_t neg) {
         return __longlong_as_double((long long)((uint64_t)__double_as_longlong(x) | ((uint64_t)neg << 63)));
     }
+    static __device__ __forceinline__ double fast32(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
+        const uint32_t kE = t.kE[i][0];
+        const uint2 m = t.M[i][0];
+        return __longlong_as_double(
+            (long long)(mul_j_w_bits32(j, m.x, m.y, kE >> 24) | ((uint64_t)neg << 63)));
+    }
 };
 template <> struct Z128Out<ZIG_F32> {
     using T = float;
-    static __device__ __forceinline__ float fast(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
-        return __uint_as_float(__float_as_uint(__fmul_rn((float)j, t.W32[i])) | (neg << 31));
+    using Pair = float2;
+    static __device__ __forceinline__ float fast(const Z128Tab& t, uint32_t i, uint32_t j,
+                                                 uint32_t negbit, int, uint32_t) {
+        return __uint_as_float(__float_as_uint(__fmul_rn((float)j, t.W32[i])) | (negbit << 31));
     }
     static __device__ __forceinline__ float from64(double x, uint32_t neg) {
         return __uint_as_float(__float_as_uint(__double2float_rn(x)) | (neg << 31));
     }
+    static __device__ __forceinline__ float fast32(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
+        return fast(t, i, j, neg, 0, 0);
+    }
 };
 template <> struct Z128Out<ZIG_BF16> {
     using T = uint16_t;
-    static __device__ __forceinline__ uint16_t fast(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
-        return f32_to_bf16_bits(Z128Out<ZIG_F32>::fast(t, i, j, neg));
+    using Pair = uint32_t;
+    static __device__ __forceinline__ uint16_t fast(const Z128Tab& t, uint32_t i, uint32_t j,
+                                                    uint32_t negbit, int, uint32_t) {
+        return f32_to_bf16_bits(Z128Out<ZIG_F32>::fast(t, i, j, negbit, 0, 0));
     }
     static __device__ __forceinline__ uint16_t from64(double x, uint32_t neg) {
         return f32_to_bf16_bits(Z128Out<ZIG_F32>::from64(x, neg));
     }
+    static __device__ __forceinline__ uint16_t fast32(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
+        return fast(t, i, j, neg, 0, 0);
+    }
 };
 
-// Decide one queued record; returns true if accepted, with its output value.
+// Staging: per warp, 32 rows x 16 elements, row-major, with the pair index
+// (two elements) XOR-swizzled by the row so that the per-lane pair stores and
+// the per-row element reads are both bank-conflict free.
+template <typename T> struct ZSw;
+template <> struct ZSw<double> { static __device__ __forceinline__ int f(int r) { return r & 7; } };
+template <> struct ZSw<float> { static __device__ __forceinline__ int f(int r) { return (r >> 1) & 7; } };
+template <> struct ZSw<uint16_t> { static __device__ __forceinline__ int f(int r) { return (r >> 2) & 7; } };
+
+template <typename T>
+__device__ __forceinline__ int zelt(int row, int col) {   // element index of (row, col)
+    return row * 16 + ((((col >> 1) ^ ZSw<T>::f(row)) << 1) | (col & 1));
+}
+
+// binary32 value of m * 2^-53 for m < 2^53 (relative error < 2^-23).
+__device__ __forceinline__ float m53_to_float(uint64_t m) {
+    const uint32_t hi = (uint32_t)(m >> 29);
+    return hi ? (float)hi * 0x1p-24f : (float)(uint32_t)m * 0x1p-53f;
+}
+
+// Decide one queued record.  Wedge: the slot already holds RN(j * w[i]) from
+// Phase A, so only the decision is made.  Tail: decision, and on acceptance
+// the value x = R - ln(U1)/R goes into its slot.
 template <class G, int DT>
-__device__ __forceinline__ bool z128_decide(const Z128Tab& t, const SlowRec& r,
+__device__ __forceinline__ bool z128_decide(const Z128Tab& t, const SlowRec& r, bool& has_val,
                                             typename Z128Out<DT>::T& val) {
-    const uint32_t j = (uint32_t)(r.a & 0xFFFFFF);
-    const uint32_t i = (uint32_t)((r.a >> 24) & 0x7F);
-    const uint32_t neg = (uint32_t)((r.a >> 31) & 1);
-    const bool is_tail = (r.a >> 41) & 1;
-    const uint64_t m1 = G::m53_of(r.b, r.c, 0);
-    if (!is_tail) {
-        // binary32 filter: |y32/y - 1| + |e32/e - 1| <= 2.6e-6 < 2^-16 (expf: <= 2 ulp)
+    const uint32_t neg = (uint32_t)(r.a >> 62) & 1u;
+    has_val = false;
+    if (!(r.a >> 63)) {
+        const uint32_t j = (uint32_t)r.a & 0xFFFFFFu;
+        const uint32_t i = (uint32_t)(r.a >> 24) & 0x7Fu;
+        const uint64_t m1 = G::m53_of(r.b, 0, 0);
+        // binary32 filter: |y32/y - 1| + |e32/e - 1| <= 2.6e-6 < 2^-16 (expf <= 2 ulp)
         const float x32 = __fmul_rn((float)j, t.W32[i]);
         const float e32 = expf(__fmul_rn(__fmul_rn(-0.5f, x32), x32));
         const float u32 = (float)(uint32_t)(m1 >> 29) * 0x1p-24f;
         const float y32 = __fadd_rn(t.Y32[i + 1], __fmul_rn(t.DY32[i], u32));
-        bool acc;
-        if (y32 < e32 * (1.0f - 0x1p-16f)) {
-            acc = true;
-        } else if (y32 > e32 * (1.0f + 0x1p-16f)) {
-            acc = false;
-        } else {
-            // inside the margin: the binary64 test exactly as defined
-            const double x = __dmul_rn((double)j, t.W[i]);
-            const double U = m53_to_double(m1);
-            const double y = __dadd_rn(t.Y[i + 1], __dmul_rn(__dsub_rn(t.Y[i], t.Y[i + 1]), U));
+        if (y32 < e32 * (1.0f - 0x1p-16f)) return true;
+        if (y32 > e32 * (1.0f + 0x1p-16f)) return false;
+        // inside the margin: the binary64 test exactly as defined
+        const double x = __dmul_rn((double)j, t.W[i]);
+        const double U = m53_to_double(m1);
+        const double y = __dadd_rn(t.Y[i + 1], __dmul_rn(__dsub_rn(t.Y[i], t.Y[i + 1]), U));
+        return y < exp(neg_half_sq(x));
+    }
+    // Tail: y = exp(-R (x - R/2)) U2 < exp(-x^2/2) with x = R + s, s = -ln(U1)/R, is
+    // ln U2 < -s^2/2 in exact arithmetic.  Decide that in binary32 when it clears a
+    // margin of 2^-14 (1 + s^2/2 + |ln U2|), far above the binary32 errors (< 1e-5
+    // relative); otherwise evaluate the definition in binary64.
+    const double R = zigtab::ZIG128_R;
+    const uint64_t m1 = r.a & ((1ull << 53) - 1);
+    const uint64_t n1 = (1ull << 53) - m1;           // U1 = n1 * 2^-53 in (0, 1]
+    const float s32 = -logf(m53_to_float(n1)) * (float)(1.0 / zigtab::ZIG128_R);
+    const float h32 = 0.5f * s32 * s32;
+    bool acc;
+    if (r.b == 0) {
+        acc = true;                                   // U2 = 0: y = 0 < exp(-x^2/2)
+    } else {
+        const float l32 = logf(m53_to_float(r.b));
+        const float marg = 0x1p-14f * (1.0f + h32 - l32);
+        if (l32 < -h32 - marg) acc = true;
+        else if (l32 > -h32 + marg) acc = false;
+        else {
+            const double U1 = __dsub_rn(1.0, m53_to_double(m1));
+            const double U2 = m53_to_double(r.b);
+            const double x = __dsub_rn(R, __ddiv_rn(log(U1), R));
+            const double y = __dmul_rn(exp(__dmul_rn(-R, __dsub_rn(x, __dmul_rn(0.5, R)))), U2);
             acc = y < exp(neg_half_sq(x));
         }
-        if (acc) val = Z128Out<DT>::fast(t, i, j, neg);
-        return acc;
     }
-    const double R = zigtab::ZIG128_R;
-    const double U1 = __dsub_rn(1.0, m53_to_double(m1));
-    const double U2 = m53_to_double(G::m53_of(r.b, r.c, 1));
-    const double x = __dsub_rn(R, __ddiv_rn(log(U1), R));
-    const double y = __dmul_rn(exp(__dmul_rn(-R, __dsub_rn(x, __dmul_rn(0.5, R)))), U2);
-    const bool acc = y < exp(neg_half_sq(x));
-    if (acc) val = Z128Out<DT>::from64(x, neg);
+    if (acc) {
+        const double U1 = __dsub_rn(1.0, m53_to_double(m1));
+        const double x = __dsub_rn(R, __ddiv_rn(log(U1), R));
+        val = Z128Out<DT>::from64(x, neg);
+        has_val = true;
+    }
     return acc;
 }
 
 template <typename OutT>
 __host__ __device__ constexpr size_t z128_warp_bytes() {
-    return 128 + kQCap * sizeof(SlowRec) + 32 * kStageCols * sizeof(OutT);
+    // [rej u32 x 32][row info 16 B x 32][ring SlowRec x kQCap][stage OutT x 32 x 16]
+    return 128 + 512 + kQCap * sizeof(SlowRec) + 32 * 16 * sizeof(OutT);
+}
+
+struct RowInfo {
+    unsigned long long dst;
+    int cnt;
+    int pad;
+};
+
+// One candidate of Phase A.  Returns true (and fills rec) for a slow candidate.
+template <class G, int DT>
+__device__ __forceinline__ bool z128_candidate(G& g, const Z128Tab& t, int lane, int v,
+                                               typename Z128Out<DT>::T& val, SlowRec& rec,
+                                               uint64_t& draws) {
+    const uint32_t w = g.next_u32();
+    const uint32_t i = w & 0x7Fu;
+    const uint32_t neg = (~w >> 7) & 1u;   // bit 7 set -> positive
+    const uint32_t j = w >> 8;
+    const uint32_t kE = t.kE[i][lane];
+    val = Z128Out<DT>::fast(t, i, j, neg, lane, kE);
+    if (j < (kE & 0xFFFFFFu)) return false;
+    const uint64_t meta = ((uint64_t)lane << 53) | ((uint64_t)v << 58) | ((uint64_t)neg << 62);
+    if (i < 127) {
+        g.snap(1, rec.b, rec.a);
+        rec.a = meta | (uint64_t)j | ((uint64_t)i << 24);
+        draws += G::kStepsPerDouble;
+    } else {
+        rec.a = meta | (1ull << 63) | g.next_m53();
+        rec.b = g.next_m53();
+        draws += 2 * G::kStepsPerDouble;
+    }
+    return true;
 }
 
 // MODE 0: generation into a.out; MODE 1: mutation x += sigma * z (binary32).
 template <int PRNG, int DT, int MODE>
-__global__ void __launch_bounds__(kBlock) z128_kernel(GenArgs a) {
+__global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
     using G = typename GenOf<PRNG>::T;
     using OutT = typename Z128Out<DT>::T;
+    using Pair = typename Z128Out<DT>::Pair;
     __shared__ Z128Tab t;
-    // dynamic: per warp [rej u32 x 32][ring SlowRec x kQCap][stage OutT x 32 x 16]
     extern __shared__ __align__(16) unsigned char z128_dsm[];
     z128tab_load(t);
     __syncthreads();
@@ -427,8 +552,9 @@ __global__ void __launch_bounds__(kBlock) z128_kernel(GenArgs a) {
     const int wib = threadIdx.x >> 5;
     unsigned char* wbase = z128_dsm + (size_t)wib * z128_warp_bytes<OutT>();
     uint32_t* rej = (uint32_t*)wbase;
-    SlowRec* q = (SlowRec*)(wbase + 128);
-    OutT* stage = (OutT*)(wbase + 128 + kQCap * sizeof(SlowRec));
+    RowInfo* rowinfo = (RowInfo*)(wbase + 128);
+    SlowRec* q = (SlowRec*)(wbase + 640);
+    OutT* stage = (OutT*)(wbase + 640 + kQCap * sizeof(SlowRec));
     const uint32_t lt_mask = (1u << lane) - 1u;
     if (MODE == 0 && a.out == nullptr) {   // only legal when every length is zero
         if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0)
@@ -437,9 +563,21 @@ __global__ void __launch_bounds__(kBlock) z128_kernel(GenArgs a) {
     }
     const uint64_t n_units = units_total(a);
     const uint64_t n_groups = (n_units + 31) >> 5;
-    const uint64_t warp_id = (uint64_t)blockIdx.x * kWarps + wib;
-    const uint64_t warp_stride = (uint64_t)gridDim.x * kWarps;
+    const uint64_t warp_id = (uint64_t)blockIdx.x * kZWarps + wib;
+    const uint64_t warp_stride = (uint64_t)gridDim.x * kZWarps;
     OutT* out = (OutT*)a.out;
+
+    // decide up to 32 queued records from `head`; results land in stage / rej
+    auto run_pass = [&](uint32_t head, uint32_t n) {
+        if ((uint32_t)lane < n) {
+            const SlowRec rr = q[(head + lane) & (kQCap - 1)];
+            OutT val;
+            bool has_val;
+            const int row = (int)(rr.a >> 53) & 31, slot = (int)(rr.a >> 58) & 15;
+            if (!z128_decide<G, DT>(t, rr, has_val, val)) atomicOr(&rej[row], 1u << slot);
+            else if (has_val) stage[zelt<OutT>(row, slot)] = val;
+        }
+    };
 
     for (uint64_t grp = warp_id; grp < n_groups; grp += warp_stride) {
         const uint64_t u = grp * 32 + lane;
@@ -460,77 +598,69 @@ __global__ void __launch_bounds__(kBlock) z128_kernel(GenArgs a) {
         uint32_t head = 0, tail = 0;   // warp-uniform ring indices
 
         while (__any_sync(kFull, rem > 0)) {
-            const int cnt = (int)umin64(rem, (uint64_t)kStageCols);
+            const int cnt = (int)umin64(rem, 16);
             rej[lane] = 0;
             draws += (uint64_t)cnt;
             __syncwarp();
 #pragma unroll 1
-            for (int v = 0; v < kStageCols; ++v) {
-                bool slow = false;
-                SlowRec r;
-                if (v < cnt) {
-                    const uint32_t w = g.next_u32();
-                    const uint32_t i = w & 0x7Fu;
-                    const uint32_t neg = (~w >> 7) & 1u;   // bit 7 set -> positive
-                    const uint32_t j = w >> 8;
-                    if (j < (t.kE[i] & 0xFFFFFFu)) {
-                        stage[stage_idx<OutT>(lane, v)] = Z128Out<DT>::fast(t, i, j, neg);
-                    } else {
-                        slow = true;
-                        const int nd = (i == 127) ? 2 : 1;
-                        g.snap(nd, r.b, r.c);
-                        draws += (uint64_t)nd * G::kStepsPerDouble;
-                        r.a = (uint64_t)j | ((uint64_t)i << 24) | ((uint64_t)neg << 31) |
-                              ((uint64_t)lane << 32) | ((uint64_t)v << 37) | ((uint64_t)(nd - 1) << 41);
-                    }
-                }
-                const uint32_t m = __ballot_sync(kFull, slow);
-                if (m) {
-                    if (slow) q[(tail + __popc(m & lt_mask)) & (kQCap - 1)] = r;
-                    tail += __popc(m);
+            for (int v = 0; v < 16; v += 2) {
+                OutT v0, v1;
+                SlowRec r0, r1;
+                const bool s0 = (v < cnt) && z128_candidate<G, DT>(g, t, lane, v, v0, r0, draws);
+                const bool s1 = (v + 1 < cnt) && z128_candidate<G, DT>(g, t, lane, v + 1, v1, r1, draws);
+                Pair pr;
+                if constexpr (DT == ZIG_BF16) pr = (uint32_t)v0 | ((uint32_t)v1 << 16);
+                else pr = Pair{v0, v1};
+                *(Pair*)&stage[zelt<OutT>(lane, v)] = pr;
+                const uint32_t m0 = __ballot_sync(kFull, s0);
+                const uint32_t m1 = __ballot_sync(kFull, s1);
+                if (m0 | m1) {
+                    if (s0) q[(tail + __popc(m0 & lt_mask)) & (kQCap - 1)] = r0;
+                    tail += __popc(m0);
+                    if (s1) q[(tail + __popc(m1 & lt_mask)) & (kQCap - 1)] = r1;
+                    tail += __popc(m1);
                     if (tail - head >= 32) {
                         __syncwarp();
-                        SlowRec rr = q[(head + lane) & (kQCap - 1)];
-                        OutT val;
-                        const uint32_t row = (uint32_t)(rr.a >> 32) & 31u, slot = (uint32_t)(rr.a >> 37) & 15u;
-                        if (z128_decide<G, DT>(t, rr, val)) stage[stage_idx<OutT>(row, slot)] = val;
-                        else atomicOr(&rej[row], 1u << slot);
+                        run_pass(head, 32);
                         head += 32;
                         __syncwarp();
                     }
                 }
             }
-            // drain the records left in this batch
+            // drain the rest of this batch's records
             while (tail != head) {
                 __syncwarp();
                 const uint32_t n = umin64(tail - head, 32);
-                if ((uint32_t)lane < n) {
-                    SlowRec rr = q[(head + lane) & (kQCap - 1)];
-                    OutT val;
-                    const uint32_t row = (uint32_t)(rr.a >> 32) & 31u, slot = (uint32_t)(rr.a >> 37) & 15u;
-                    if (z128_decide<G, DT>(t, rr, val)) stage[stage_idx<OutT>(row, slot)] = val;
-                    else atomicOr(&rej[row], 1u << slot);
-                }
+                run_pass(head, n);
                 head += n;
             }
             __syncwarp();
-            // drop rejected slots (a rejection costs the stream one extra layer draw,
-            // already counted: the next batch draws it as a new candidate)
-            const uint32_t rj = rej[lane];
-            int acc = cnt;
-            if (rj) {
-                int wpos = 0;
-                for (int v = 0; v < cnt; ++v) {
-                    if (!((rj >> v) & 1u)) {
-                        stage[stage_idx<OutT>(lane, wpos)] = stage[stage_idx<OutT>(lane, v)];
-                        ++wpos;
+            // rejected slots are skipped (each costs the stream one more layer draw,
+            // which the next batch draws as a new candidate)
+            const int acc = cnt - __popc(rej[lane]);
+            rowinfo[lane].dst = (unsigned long long)dst;
+            rowinfo[lane].cnt = acc;
+            __syncwarp();
+            {
+                const int half = lane >> 4, c = lane & 15;
+#pragma unroll 4
+                for (int k = 0; k < 16; ++k) {
+                    const int row = 2 * k + half;
+                    const int rc = rowinfo[row].cnt;
+                    OutT* rd = (OutT*)rowinfo[row].dst;
+                    if (c < rc) {
+                        // slot of the row's c-th accepted candidate
+                        int src = c;
+                        for (uint32_t m = rej[row]; m; m &= m - 1) {
+                            if (__ffs(m) - 1 <= src) ++src;
+                            else break;
+                        }
+                        const OutT z = stage[zelt<OutT>(row, src)];
+                        if constexpr (MODE == 0) rd[c] = z;
+                        else ((float*)rd)[c] = fmaf(a.sigma, (float)z, ((float*)rd)[c]);
                     }
                 }
-                acc = wpos;
             }
-            __syncwarp();
-            if (MODE == 0) stage_flush<OutT>(stage, dst, acc, lane);
-            else stage_flush_fma((const float*)stage, (float*)dst, acc, lane, a.sigma);
             __syncwarp();
             dst += acc;
             rem -= (uint64_t)acc;
@@ -755,8 +885,10 @@ static size_t dyn_smem_of(int alg, int dt) {
     if (alg != ZIG_ZIG128) return 0;
     size_t per = dt == ZIG_F64 ? z128_warp_bytes<double>()
                : dt == ZIG_F32 ? z128_warp_bytes<float>() : z128_warp_bytes<uint16_t>();
-    return per * kWarps;
+    return per * kZWarps;
 }
+
+static int block_of(int alg) { return alg == ZIG_ZIG128 ? kZBlock : kBlock; }
 
 // Opt in to the dynamic shared memory a launch needs (static + dynamic may pass
 // the 48 KB default only with the attribute set).
@@ -766,13 +898,14 @@ static bool allow_dyn_smem(const void* fn, size_t bytes) {
            cudaSuccess;
 }
 
-static int grid_for(const void* fn, int dev, uint64_t n_groups, size_t dyn = 0) {
+static int grid_for(const void* fn, int dev, uint64_t n_groups, size_t dyn = 0, int block = kBlock) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, dyn) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, dyn) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     uint64_t full = (uint64_t)g_sms[dev] * per_sm;
-    uint64_t need = (n_groups + kWarps - 1) / kWarps;
+    const uint64_t warps = (uint64_t)block / 32;
+    uint64_t need = (n_groups + warps - 1) / warps;
     if (need == 0) need = 1;
     return (int)std::min<uint64_t>(full, need);
 }
@@ -873,8 +1006,9 @@ zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
     host::GenFn fn = host::pick(alg, prng, dtype);
     const size_t dyn = host::dyn_smem_of(alg, dtype);
     if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
-    int grid = host::grid_for((const void*)fn, dev, n_groups_hint, dyn);
-    fn<<<grid, kBlock, dyn, s>>>(a);
+    const int block = host::block_of(alg);
+    int grid = host::grid_for((const void*)fn, dev, n_groups_hint, dyn, block);
+    fn<<<grid, block, dyn, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
 }
 
@@ -907,8 +1041,8 @@ zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_
     am.mut_seed = seed;
     const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32);
     if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
-    int grid = host::grid_for((const void*)fn, dev, groups, dyn);
-    fn<<<grid, kBlock, dyn, s>>>(am);
+    int grid = host::grid_for((const void*)fn, dev, groups, dyn, kZBlock);
+    fn<<<grid, kZBlock, dyn, s>>>(am);
     return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
 }
 
@@ -1026,7 +1160,8 @@ extern "C" zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uin
     host::GenFn fn = host::pick(alg, prng, dtype);
     const size_t dyn = host::dyn_smem_of(alg, dtype);
     if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
-    int grid = host::grid_for((const void*)fn, dev, ~0ull >> 8, dyn);
-    fn<<<grid, kBlock, dyn, s>>>(a);
+    const int block = host::block_of(alg);
+    int grid = host::grid_for((const void*)fn, dev, ~0ull >> 8, dyn, block);
+    fn<<<grid, block, dyn, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
 }
