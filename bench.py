@@ -272,7 +272,7 @@ def run_gpu(args):
     traffic = load_traffic_record()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
-                "kernel": f"gen_kernel<zig128, {dom}, f64>", "peak_source": f"{peak_src} copy bandwidth",
+                "kernel": f"z128_kernel<{dom}, f64>", "peak_source": f"{peak_src} copy bandwidth",
                 "algorithmic_bytes_per_launch": alg_bytes}
     all_ms = sorted(x for p in PRNGS for x in per_launch[p])
     line_extra = {
