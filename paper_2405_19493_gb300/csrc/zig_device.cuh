@@ -96,6 +96,20 @@ struct GenLcg48 {
         c = 0;
         s = (nd == 1) ? ((kA2 * s + kC2) & kMask48) : ((kA4 * s + kC4) & kMask48);
     }
+    // Batch-start state and the snapshot of a uniform d raw steps later (for
+    // deciding a deferred wedge without keeping a per-record snapshot).
+    struct Saved { uint64_t s; };
+    __device__ __forceinline__ Saved save() const { return Saved{s}; }
+    static __device__ __forceinline__ uint64_t snap_at(const Saved& st, uint32_t d, const JumpTab* jt) {
+        uint64_t t = st.s;
+        while (d) {
+            const int b = __ffs(d) - 1;
+            t = (jt->lcg48_A[b] * t + jt->lcg48_C[b]) & kMask48;
+            d &= d - 1;
+        }
+        return t;   // the state before the uniform's two steps
+    }
+    __device__ __forceinline__ void skip_double() { s = (kA2 * s + kC2) & kMask48; }
     static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t, int k) {
         uint64_t t = k ? ((kA2 * b + kC2) & kMask48) : b;
         t = (t * kLcgA + kLcgC) & kMask48;
@@ -122,6 +136,12 @@ struct GenSplitMix64 {
     static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t, int k) {
         return mix64(k ? b + kGamma : b) >> 11;
     }
+    struct Saved { uint64_t s; };
+    __device__ __forceinline__ Saved save() const { return Saved{s}; }
+    static __device__ __forceinline__ uint64_t snap_at(const Saved& st, uint32_t d, const JumpTab*) {
+        return st.s + (uint64_t)(d + 1) * kGamma;   // the state of the uniform's own step
+    }
+    __device__ __forceinline__ void skip_double() { s += kGamma; }
 };
 
 struct GenL64X128Mix {
@@ -161,6 +181,15 @@ struct GenL64X128Mix {
     static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t c, int k) {
         return mix_lea64(k ? c : b) >> 11;
     }
+    struct Saved { uint64_t a, s, x0, x1; };
+    __device__ __forceinline__ Saved save() const { return Saved{a, s, x0, x1}; }
+    static __device__ __forceinline__ uint64_t snap_at(const Saved& st, uint32_t d, const JumpTab*) {
+        GenL64X128Mix t;
+        t.a = st.a; t.s = st.s; t.x0 = st.x0; t.x1 = st.x1;
+        for (uint32_t k = 0; k < d; ++k) t.advance();   // replay d steps
+        return t.s + t.x0;                              // the uniform's mix input
+    }
+    __device__ __forceinline__ void skip_double() { advance(); }
     __device__ void jump(uint64_t n, const JumpTab* jt) {
         while (n) {
             int b = __ffsll((long long)n) - 1;

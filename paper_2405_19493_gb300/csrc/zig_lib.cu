@@ -293,33 +293,34 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
 // ---------------------------------------------------------------------------
 // Each lane owns one unit (stream or chunk) with its generator in registers.
 // A warp works in batches of up to 16 outputs per lane:
-//  A. the lanes draw candidates in lockstep, two per step.  A fast-path
-//     candidate (j < k[i]) is finished on the spot: x = RN(j * w[i]) is built
-//     exactly with integer arithmetic (binary64) or as fl32(j * w32[i])
-//     (binary32/bfloat16).  A slow candidate (wedge or tail) keeps a
-//     placeholder slot and pushes a 16-byte record into the warp's ring: the
-//     layer, j, sign, (row, slot) and either a snapshot of the generator from
-//     which its uniform double is rebuilt (wedge) or the two uniforms (tail).
-//     The lane's generator moves past those doubles at once and keeps drawing.
-//  B. whenever 32 records wait (and at the end of a batch) all 32 lanes decide
-//     32 records together: the wedge test in binary32 with a proven margin,
-//     binary64 only inside it; the tail in binary64.
-//  C. each row drops its rejected slots and is flushed, two rows per warp store,
-//     with its own count; the stream continues in the next batch.
+//  A. the lanes draw candidates in lockstep, two per step.
+//     - fast path (j < k[i]): x = RN(j * w[i]) on the spot.  For binary64 this
+//       is one fused multiply-add, fma(2^52 + j, w, -2^52 w) = RN(j w) exactly
+//       (2^52 + j is built from j's bits; -2^52 w from w's bits), on GB300's
+//       narrow binary64 pipe; every fourth slot uses the same product in
+//       integer arithmetic instead, to balance that pipe against the integer
+//       pipes.  binary32/bfloat16 use fl32(j * w32[i]).
+//     - wedge (i < 127): the slot keeps RN(j w[i]), which is the output if the
+//       wedge test accepts; a 16-byte record (i, j, sign, row, slot, and a
+//       snapshot from which the test's uniform is rebuilt) goes to the warp's
+//       ring and the generator moves past that uniform at once.
+//     - tail (i = 127, j >= k[127]; 0.06 % of draws): decided in the lane.
+//  B. whenever 32 records wait (and at the end of the batch) the 32 lanes test
+//     32 wedges together in binary32 with a proven margin (binary64 only inside
+//     it) and flag the rejected slots.
+//  C. the rows are written two per warp store, skipping rejected slots; the
+//     stream continues in the next batch.
 // The outputs of a unit are its accepted candidates in draw order: exactly the
 // sequence a one-variate-at-a-time loop produces.
 
-constexpr int kZBlock = 1024;               // one block per SM
-constexpr int kZWarps = kZBlock / 32;
-constexpr int kQCap = 64;                   // ring: <= 31 waiting + 32 new per step
 
 struct Z128Tab {
-    uint32_t kE[128][32];   // K[i] | (E(w[i]) - 900) << 24, one copy per lane
-    uint2 M[128][16];       // significand of w[i] as (low 32, high 21 bits), 16 copies
+    uint32_t K[128][32];    // k[i], one copy per lane
+    double W[128][16];      // w[i], 16 copies (a half-warp reads without conflicts)
     float W32[128];         // RN32(x_{i+1} / 2^24)
     float Y32[128];         // RN32(y[i])
     float DY32[128];        // RN32(y[i] - y[i+1])
-    double W[128];
+    double Wd[128];
     double Y[128];
 };
 __device__ float d_z128_Y32[128];
@@ -328,25 +329,24 @@ __device__ float d_z128_DY32[128];
 __device__ __forceinline__ void z128tab_load(Z128Tab& t) {
     for (int k = threadIdx.x; k < 128 * 32; k += blockDim.x) {
         const int i = k >> 5, c = k & 31;
-        t.kE[i][c] = d_z128_kE[i];
-        if (c < 16) {
-            const uint64_t m = d_z128_M[i];
-            t.M[i][c] = make_uint2((uint32_t)m, (uint32_t)(m >> 32));
-        }
+        t.K[i][c] = d_z128_kE[i] & 0xFFFFFFu;
+        if (c < 16) t.W[i][c] = d_z128_W[i];
     }
     for (int i = threadIdx.x; i < 128; i += blockDim.x) {
         t.W32[i] = d_z128_W32[i];
         t.Y32[i] = d_z128_Y32[i];
         t.DY32[i] = d_z128_DY32[i];
-        t.W[i] = d_z128_W[i];
+        t.Wd[i] = d_z128_W[i];
         t.Y[i] = d_z128_Y[i];
     }
 }
 
-// RN(j * w) as binary64 bits, w = (mh:ml) * 2^(E - 1075), j < 2^24, with
-// eb = E - 900 from the table word.  Same arithmetic as mul_j_w_bits, written
-// on 32-bit words and selects so that it has no branch; j = 0 gives +0.
-__device__ __forceinline__ uint64_t mul_j_w_bits32(uint32_t j, uint32_t ml, uint32_t mh, uint32_t eb) {
+// RN(j * w) as binary64 bits, j < 2^24, w a normal binary64 with bits (wh:wl):
+// integer arithmetic, no branch, j = 0 gives +0.  Normalise j (bit 31 set), take
+// the 85-bit product with the 53-bit significand, keep 53 bits, round to nearest
+// even, and assemble the exponent.
+__device__ __forceinline__ uint64_t mul_j_w_int(uint32_t j, uint32_t wh, uint32_t wl) {
+    const uint32_t ml = wl, mh = (wh & 0xFFFFFu) | 0x100000u;
     const uint32_t lz = __clz((int)j);                 // 8..31; 32 for j = 0
     const uint32_t jn = j << (lz & 31);
     const uint64_t A = (uint64_t)jn * ml;
@@ -360,79 +360,18 @@ __device__ __forceinline__ uint64_t mul_j_w_bits32(uint32_t j, uint32_t ml, uint
     const uint32_t rem = s ? (lo << 1) : lo;
     const uint32_t up = (uint32_t)(rem > 0x80000000u) | ((uint32_t)(rem == 0x80000000u) & ql);
     const uint64_t q = (((uint64_t)qh << 32) | ql) + (up & 1u);
-    const uint32_t ex = eb + 931u - (uint32_t)s - lz;  // biased exponent - 1
+    const uint32_t ex = (wh >> 20) + 31u - (uint32_t)s - lz;   // biased exponent - 1
     const uint64_t bits = ((uint64_t)ex << 52) + q;
     return j ? bits : 0ull;
 }
 
-// Slow-candidate record (16 bytes).
-//   a: bits 53..57 row, 58..61 slot, 62 negative, 63 tail;
-//      wedge: bits 0..23 j, 24..30 layer i;  tail: bits 0..52 the first uniform (m53)
-//   b: wedge: the generator snapshot for its uniform;  tail: the second uniform (m53)
-struct SlowRec {
-    uint64_t a, b;
-};
-
-template <int DT> struct Z128Out;
-template <> struct Z128Out<ZIG_F64> {
-    using T = double;
-    using Pair = double2;
-    static __device__ __forceinline__ double fast(const Z128Tab& t, uint32_t i, uint32_t j,
-                                                  uint32_t negbit, int lane, uint32_t kE) {
-        const uint2 m = t.M[i][lane & 15];
-        return __longlong_as_double(
-            (long long)(mul_j_w_bits32(j, m.x, m.y, kE >> 24) | ((uint64_t)negbit << 63)));
-    }
-    static __device__ __forceinline__ double from64(double x, uint32_t neg) {
-        return __longlong_as_double((long long)((uint64_t)__double_as_longlong(x) | ((uint64_t)neg << 63)));
-    }
-    static __device__ __forceinline__ double fast32(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
-        const uint32_t kE = t.kE[i][0];
-        const uint2 m = t.M[i][0];
-        return __longlong_as_double(
-            (long long)(mul_j_w_bits32(j, m.x, m.y, kE >> 24) | ((uint64_t)neg << 63)));
-    }
-};
-template <> struct Z128Out<ZIG_F32> {
-    using T = float;
-    using Pair = float2;
-    static __device__ __forceinline__ float fast(const Z128Tab& t, uint32_t i, uint32_t j,
-                                                 uint32_t negbit, int, uint32_t) {
-        return __uint_as_float(__float_as_uint(__fmul_rn((float)j, t.W32[i])) | (negbit << 31));
-    }
-    static __device__ __forceinline__ float from64(double x, uint32_t neg) {
-        return __uint_as_float(__float_as_uint(__double2float_rn(x)) | (neg << 31));
-    }
-    static __device__ __forceinline__ float fast32(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
-        return fast(t, i, j, neg, 0, 0);
-    }
-};
-template <> struct Z128Out<ZIG_BF16> {
-    using T = uint16_t;
-    using Pair = uint32_t;
-    static __device__ __forceinline__ uint16_t fast(const Z128Tab& t, uint32_t i, uint32_t j,
-                                                    uint32_t negbit, int, uint32_t) {
-        return f32_to_bf16_bits(Z128Out<ZIG_F32>::fast(t, i, j, negbit, 0, 0));
-    }
-    static __device__ __forceinline__ uint16_t from64(double x, uint32_t neg) {
-        return f32_to_bf16_bits(Z128Out<ZIG_F32>::from64(x, neg));
-    }
-    static __device__ __forceinline__ uint16_t fast32(const Z128Tab& t, uint32_t i, uint32_t j, uint32_t neg) {
-        return fast(t, i, j, neg, 0, 0);
-    }
-};
-
-// Staging: per warp, 32 rows x 16 elements, row-major, with the pair index
-// (two elements) XOR-swizzled by the row so that the per-lane pair stores and
-// the per-row element reads are both bank-conflict free.
-template <typename T> struct ZSw;
-template <> struct ZSw<double> { static __device__ __forceinline__ int f(int r) { return r & 7; } };
-template <> struct ZSw<float> { static __device__ __forceinline__ int f(int r) { return (r >> 1) & 7; } };
-template <> struct ZSw<uint16_t> { static __device__ __forceinline__ int f(int r) { return (r >> 2) & 7; } };
-
-template <typename T>
-__device__ __forceinline__ int zelt(int row, int col) {   // element index of (row, col)
-    return row * 16 + ((((col >> 1) ^ ZSw<T>::f(row)) << 1) | (col & 1));
+// RN(j * w) with one binary64 fma: (2^52 + j) * w - 2^52 * w = j * w exactly
+// before the single rounding.  2^52 + j and -2^52 * w are built from bits.
+__device__ __forceinline__ uint64_t mul_j_w_fma(uint32_t j, double w) {
+    const uint32_t wh = (uint32_t)__double2hiint(w), wl = (uint32_t)__double2loint(w);
+    const double d = __hiloint2double(0x43300000, (int)j);
+    const double c = __hiloint2double((int)((wh + (52u << 20)) | 0x80000000u), (int)wl);
+    return (uint64_t)__double_as_longlong(__fma_rn(d, w, c));
 }
 
 // binary32 value of m * 2^-53 for m < 2^53 (relative error < 2^-23).
@@ -441,108 +380,186 @@ __device__ __forceinline__ float m53_to_float(uint64_t m) {
     return hi ? (float)hi * 0x1p-24f : (float)(uint32_t)m * 0x1p-53f;
 }
 
-// Decide one queued record.  Wedge: the slot already holds RN(j * w[i]) from
-// Phase A, so only the decision is made.  Tail: decision, and on acceptance
-// the value x = R - ln(U1)/R goes into its slot.
-template <class G, int DT>
-__device__ __forceinline__ bool z128_decide(const Z128Tab& t, const SlowRec& r, bool& has_val,
-                                            typename Z128Out<DT>::T& val) {
-    const uint32_t neg = (uint32_t)(r.a >> 62) & 1u;
-    has_val = false;
-    if (!(r.a >> 63)) {
-        const uint32_t j = (uint32_t)r.a & 0xFFFFFFu;
-        const uint32_t i = (uint32_t)(r.a >> 24) & 0x7Fu;
-        const uint64_t m1 = G::m53_of(r.b, 0, 0);
-        // binary32 filter: |y32/y - 1| + |e32/e - 1| <= 2.6e-6 < 2^-16 (expf <= 2 ulp)
-        const float x32 = __fmul_rn((float)j, t.W32[i]);
-        const float e32 = expf(__fmul_rn(__fmul_rn(-0.5f, x32), x32));
-        const float u32 = (float)(uint32_t)(m1 >> 29) * 0x1p-24f;
-        const float y32 = __fadd_rn(t.Y32[i + 1], __fmul_rn(t.DY32[i], u32));
-        if (y32 < e32 * (1.0f - 0x1p-16f)) return true;
-        if (y32 > e32 * (1.0f + 0x1p-16f)) return false;
-        // inside the margin: the binary64 test exactly as defined
-        const double x = __dmul_rn((double)j, t.W[i]);
-        const double U = m53_to_double(m1);
-        const double y = __dadd_rn(t.Y[i + 1], __dmul_rn(__dsub_rn(t.Y[i], t.Y[i + 1]), U));
-        return y < exp(neg_half_sq(x));
+template <int DT> struct Z128Out;
+template <> struct Z128Out<ZIG_F64> {
+    using T = double;
+    using Pair = double2;
+    static __device__ __forceinline__ double fast(const Z128Tab& t, uint32_t i, uint32_t j,
+                                                  uint32_t neg, int lane, bool use_int) {
+        const double w = t.W[i][lane & 15];
+        uint64_t b;
+        if (use_int) b = mul_j_w_int(j, (uint32_t)__double2hiint(w), (uint32_t)__double2loint(w));
+        else b = mul_j_w_fma(j, w);
+        return __longlong_as_double((long long)(b | ((uint64_t)neg << 63)));
     }
-    // Tail: y = exp(-R (x - R/2)) U2 < exp(-x^2/2) with x = R + s, s = -ln(U1)/R, is
-    // ln U2 < -s^2/2 in exact arithmetic.  Decide that in binary32 when it clears a
-    // margin of 2^-14 (1 + s^2/2 + |ln U2|), far above the binary32 errors (< 1e-5
-    // relative); otherwise evaluate the definition in binary64.
-    const double R = zigtab::ZIG128_R;
-    const uint64_t m1 = r.a & ((1ull << 53) - 1);
-    const uint64_t n1 = (1ull << 53) - m1;           // U1 = n1 * 2^-53 in (0, 1]
-    const float s32 = -logf(m53_to_float(n1)) * (float)(1.0 / zigtab::ZIG128_R);
-    const float h32 = 0.5f * s32 * s32;
-    bool acc;
-    if (r.b == 0) {
-        acc = true;                                   // U2 = 0: y = 0 < exp(-x^2/2)
-    } else {
-        const float l32 = logf(m53_to_float(r.b));
-        const float marg = 0x1p-14f * (1.0f + h32 - l32);
-        if (l32 < -h32 - marg) acc = true;
-        else if (l32 > -h32 + marg) acc = false;
-        else {
-            const double U1 = __dsub_rn(1.0, m53_to_double(m1));
-            const double U2 = m53_to_double(r.b);
-            const double x = __dsub_rn(R, __ddiv_rn(log(U1), R));
-            const double y = __dmul_rn(exp(__dmul_rn(-R, __dsub_rn(x, __dmul_rn(0.5, R)))), U2);
-            acc = y < exp(neg_half_sq(x));
-        }
+    static __device__ __forceinline__ double from64(double x, uint32_t neg) {
+        return __longlong_as_double((long long)((uint64_t)__double_as_longlong(x) | ((uint64_t)neg << 63)));
     }
-    if (acc) {
-        const double U1 = __dsub_rn(1.0, m53_to_double(m1));
-        const double x = __dsub_rn(R, __ddiv_rn(log(U1), R));
-        val = Z128Out<DT>::from64(x, neg);
-        has_val = true;
+};
+template <> struct Z128Out<ZIG_F32> {
+    using T = float;
+    using Pair = float2;
+    static __device__ __forceinline__ float fast(const Z128Tab& t, uint32_t i, uint32_t j,
+                                                 uint32_t neg, int, bool) {
+        return __uint_as_float(__float_as_uint(__fmul_rn((float)j, t.W32[i])) | (neg << 31));
     }
-    return acc;
+    static __device__ __forceinline__ float from64(double x, uint32_t neg) {
+        return __uint_as_float(__float_as_uint(__double2float_rn(x)) | (neg << 31));
+    }
+};
+// The wedge test for layer i, abscissa j and uniform U = m1 2^-53:
+// y = y[i+1] + (y[i] - y[i+1]) U < exp(-x^2/2) with x = RN(j w[i]).  Decided in
+// binary32 when |y32 - e32| clears 2^-16 e32 (the binary32 errors are
+// |y32/y - 1| + |e32/e - 1| <= 2.6e-6, expf within 2 ulp); inside the margin
+// the binary64 definition decides.
+__device__ __forceinline__ bool z128_wedge_accept(const Z128Tab& t, uint32_t i, uint32_t j, uint64_t m1) {
+    const float x32 = __fmul_rn((float)j, t.W32[i]);
+    const float e32 = expf(__fmul_rn(__fmul_rn(-0.5f, x32), x32));
+    const float u32 = (float)(uint32_t)(m1 >> 29) * 0x1p-24f;
+    const float y32 = __fadd_rn(t.Y32[i + 1], __fmul_rn(t.DY32[i], u32));
+    if (y32 < e32 * (1.0f - 0x1p-16f)) return true;
+    if (y32 > e32 * (1.0f + 0x1p-16f)) return false;
+    const double x = __dmul_rn((double)j, t.Wd[i]);
+    const double U = m53_to_double(m1);
+    const double y = __dadd_rn(t.Y[i + 1], __dmul_rn(__dsub_rn(t.Y[i], t.Y[i + 1]), U));
+    return y < exp(neg_half_sq(x));
 }
 
-template <typename OutT>
-__host__ __device__ constexpr size_t z128_warp_bytes() {
-    // [rej u32 x 32][row info 16 B x 32][ring SlowRec x kQCap][stage OutT x 32 x 16]
-    return 128 + 512 + kQCap * sizeof(SlowRec) + 32 * 16 * sizeof(OutT);
+// The tail test for U1 = 1 - m1 2^-53, U2 = m2 2^-53:
+// y = exp(-R (x - R/2)) U2 < exp(-x^2/2) with x = R + s, s = -ln(U1)/R, which is
+// ln U2 < -s^2/2 in exact arithmetic.  Decided in binary32 when that clears a
+// margin of 2^-14 (1 + s^2/2 + |ln U2|), far above the binary32 errors (< 1e-5
+// relative); otherwise the binary64 definition decides.
+__device__ __forceinline__ bool z128_tail_accept(uint64_t m1, uint64_t m2) {
+    if (m2 == 0) return true;                         // U2 = 0: y = 0 < exp(-x^2/2)
+    const uint64_t n1 = (1ull << 53) - m1;            // U1 = n1 2^-53 in (0, 1]
+    const float s32 = -logf(m53_to_float(n1)) * (float)(1.0 / zigtab::ZIG128_R);
+    const float h32 = 0.5f * s32 * s32;
+    const float l32 = logf(m53_to_float(m2));
+    const float marg = 0x1p-14f * (1.0f + h32 - l32);
+    if (l32 < -h32 - marg) return true;
+    if (l32 > -h32 + marg) return false;
+    const double R = zigtab::ZIG128_R;
+    const double U1 = __dsub_rn(1.0, m53_to_double(m1));
+    const double U2 = m53_to_double(m2);
+    const double x = __dsub_rn(R, __ddiv_rn(log(U1), R));
+    const double y = __dmul_rn(exp(__dmul_rn(-R, __dsub_rn(x, __dmul_rn(0.5, R)))), U2);
+    return y < exp(neg_half_sq(x));
+}
+
+// The tail step, kept out of line so that its binary64 math does not raise the
+// register pressure of the draw loop: the accepted x, or -1 if rejected.
+__device__ __noinline__ double z128_tail(uint64_t m1, uint64_t m2) {
+    if (!z128_tail_accept(m1, m2)) return -1.0;
+    const double R = zigtab::ZIG128_R;
+    const double U1 = __dsub_rn(1.0, m53_to_double(m1));
+    return __dsub_rn(R, __ddiv_rn(log(U1), R));
+}
+
+// Staging word per slot: binary64 bits, or binary32 bits (binary32 and bfloat16
+// outputs; bfloat16 is rounded at the store).  A deferred wedge's slot holds
+// j | i << 24 | negative << 31 until it is decided.
+template <int DT> struct ZStage { using T = uint32_t; };
+template <> struct ZStage<ZIG_F64> { using T = uint64_t; };
+
+
+template <int DT>
+__device__ __forceinline__ typename ZStage<DT>::T z128_value(const Z128Tab& t, uint32_t i, uint32_t j,
+                                                              uint32_t neg, int lane, bool use_int) {
+    if constexpr (DT == ZIG_F64) {
+        return (uint64_t)__double_as_longlong(Z128Out<ZIG_F64>::fast(t, i, j, neg, lane, use_int));
+    } else {
+        return __float_as_uint(Z128Out<ZIG_F32>::fast(t, i, j, neg, lane, false));
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ typename ZStage<DT>::T z128_from64(double x, uint32_t neg) {
+    if constexpr (DT == ZIG_F64) return (uint64_t)__double_as_longlong(Z128Out<ZIG_F64>::from64(x, neg));
+    else return __float_as_uint(Z128Out<ZIG_F32>::from64(x, neg));
 }
 
 struct RowInfo {
     unsigned long long dst;
     int cnt;
-    int pad;
+    uint32_t rej;
 };
 
-// One candidate of Phase A.  Returns true (and fills rec) for a slow candidate.
+// Batch width: 32 slots per lane with 4-byte staging words, 16 with 8-byte words.
+template <int DT> struct ZBatch { static constexpr int B = (DT == ZIG_F64) ? 16 : 32; };
+
 template <class G, int DT>
-__device__ __forceinline__ bool z128_candidate(G& g, const Z128Tab& t, int lane, int v,
-                                               typename Z128Out<DT>::T& val, SlowRec& rec,
-                                               uint64_t& draws) {
-    const uint32_t w = g.next_u32();
-    const uint32_t i = w & 0x7Fu;
-    const uint32_t neg = (~w >> 7) & 1u;   // bit 7 set -> positive
-    const uint32_t j = w >> 8;
-    const uint32_t kE = t.kE[i][lane];
-    val = Z128Out<DT>::fast(t, i, j, neg, lane, kE);
-    if (j < (kE & 0xFFFFFFu)) return false;
-    const uint64_t meta = ((uint64_t)lane << 53) | ((uint64_t)v << 58) | ((uint64_t)neg << 62);
-    if (i < 127) {
-        g.snap(1, rec.b, rec.a);
-        rec.a = meta | (uint64_t)j | ((uint64_t)i << 24);
-        draws += G::kStepsPerDouble;
-    } else {
-        rec.a = meta | (1ull << 63) | g.next_m53();
-        rec.b = g.next_m53();
-        draws += 2 * G::kStepsPerDouble;
+struct ZWarp {
+    static constexpr int B = ZBatch<DT>::B;
+    using S = typename ZStage<DT>::T;
+    S stage[32 * B];
+    uint16_t dd[32][B];                   // raw steps before a deferred wedge's uniform
+    typename G::Saved saved[32];          // each lane's generator at the batch start
+    uint32_t smask[32], rej[32], excl[32];
+    RowInfo rowinfo[32];
+};
+
+template <int B, typename S>
+__device__ __forceinline__ int zslot(int row, int col) {   // bank-conflict-free swizzle
+    if constexpr (B == 32) return row * 32 + (col ^ row);              // 4-byte words
+    else if constexpr (sizeof(S) == 8) return row * 16 + (col ^ (row & 15));
+    else return row * 16 + (col ^ ((row >> 1) & 15));
+}
+
+constexpr int kZBlock = 768;              // 24 warps; one block per SM
+constexpr int kZWarps = kZBlock / 32;
+
+template <class G, int DT>
+__host__ __device__ constexpr size_t z128_warp_bytes() {
+    return (sizeof(ZWarp<G, DT>) + 15) & ~(size_t)15;
+}
+
+// Resolve a slow draw (j >= k[i]) of slot v.  A wedge is deferred to phase B
+// (its slot keeps j | i << 24 | negative << 31 and its step count goes to dd)
+// unless the batch's step count has outgrown 16 bits; a tail is decided here and
+// a rejected tail draws again for the same slot.  Returns the slot's word.
+template <class G, int DT>
+__device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab& t, ZWarp<G, DT>& ws,
+                                                             int lane, int v, uint32_t i, uint32_t j,
+                                                             uint32_t neg, uint32_t& drel, uint32_t& smask) {
+    using S = typename ZStage<DT>::T;
+    for (;;) {
+        if (i < 127) {
+            if (drel <= 0xFFFFu) {
+                ws.dd[lane][v] = (uint16_t)drel;
+                g.skip_double();
+                drel += G::kStepsPerDouble;
+                smask |= 1u << v;
+                return (S)(j | (i << 24) | (neg << 31));
+            }
+            const uint64_t mu = g.next_m53();
+            drel += G::kStepsPerDouble;
+            if (z128_wedge_accept(t, i, j, mu)) return z128_value<DT>(t, i, j, neg, lane, false);
+        } else {
+            const uint64_t m1 = g.next_m53();
+            const uint64_t m2 = g.next_m53();
+            drel += 2 * G::kStepsPerDouble;
+            const double x = z128_tail(m1, m2);
+            if (x >= 0.0) return z128_from64<DT>(x, neg);
+        }
+        // rejected: the next draw is for the same slot
+        const uint32_t w = g.next_u32();
+        ++drel;
+        i = w & 0x7Fu;
+        neg = (~w >> 7) & 1u;
+        j = w >> 8;
+        if (j < t.K[i][lane]) return z128_value<DT>(t, i, j, neg, lane, false);
     }
-    return true;
 }
 
 // MODE 0: generation into a.out; MODE 1: mutation x += sigma * z (binary32).
 template <int PRNG, int DT, int MODE>
 __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
     using G = typename GenOf<PRNG>::T;
-    using OutT = typename Z128Out<DT>::T;
-    using Pair = typename Z128Out<DT>::Pair;
+    using S = typename ZStage<DT>::T;
+    using OutT = typename OutOf<DT>::T;
+    using W = ZWarp<G, DT>;
+    constexpr int B = W::B;
     __shared__ Z128Tab t;
     extern __shared__ __align__(16) unsigned char z128_dsm[];
     z128tab_load(t);
@@ -550,12 +567,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    unsigned char* wbase = z128_dsm + (size_t)wib * z128_warp_bytes<OutT>();
-    uint32_t* rej = (uint32_t*)wbase;
-    RowInfo* rowinfo = (RowInfo*)(wbase + 128);
-    SlowRec* q = (SlowRec*)(wbase + 640);
-    OutT* stage = (OutT*)(wbase + 640 + kQCap * sizeof(SlowRec));
-    const uint32_t lt_mask = (1u << lane) - 1u;
+    W& ws = *(W*)(z128_dsm + (size_t)wib * z128_warp_bytes<G, DT>());
     if (MODE == 0 && a.out == nullptr) {   // only legal when every length is zero
         if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0)
             atomicOr(&d_err, kErrNullOutput);
@@ -566,18 +578,6 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
     const uint64_t warp_id = (uint64_t)blockIdx.x * kZWarps + wib;
     const uint64_t warp_stride = (uint64_t)gridDim.x * kZWarps;
     OutT* out = (OutT*)a.out;
-
-    // decide up to 32 queued records from `head`; results land in stage / rej
-    auto run_pass = [&](uint32_t head, uint32_t n) {
-        if ((uint32_t)lane < n) {
-            const SlowRec rr = q[(head + lane) & (kQCap - 1)];
-            OutT val;
-            bool has_val;
-            const int row = (int)(rr.a >> 53) & 31, slot = (int)(rr.a >> 58) & 15;
-            if (!z128_decide<G, DT>(t, rr, has_val, val)) atomicOr(&rej[row], 1u << slot);
-            else if (has_val) stage[zelt<OutT>(row, slot)] = val;
-        }
-    };
 
     for (uint64_t grp = warp_id; grp < n_groups; grp += warp_stride) {
         const uint64_t u = grp * 32 + lane;
@@ -595,69 +595,120 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
         }
         uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
         const bool check_chunk = a.chunk_log2 != 0 && rem != 0;
-        uint32_t head = 0, tail = 0;   // warp-uniform ring indices
 
         while (__any_sync(kFull, rem > 0)) {
-            const int cnt = (int)umin64(rem, 16);
-            rej[lane] = 0;
-            draws += (uint64_t)cnt;
-            __syncwarp();
+            ws.saved[lane] = g.save();
+            ws.rej[lane] = 0;
+            uint32_t drel = 0, smask = 0;
+            int produced;
+            // ---- A: draw the batch's candidates ----
+            if (__all_sync(kFull, rem >= (uint64_t)B)) {
+                // full batch: B candidates per lane, one warp vote per candidate guarding
+                // the rare slow draws (unrolled by two: deeper unrolling copies the slow
+                // handler into the instruction stream and costs more than it saves)
+#pragma unroll 2
+                for (int v = 0; v < B; ++v) {
+                    const uint32_t w = g.next_u32();
+                    ++drel;
+                    const uint32_t i = w & 0x7Fu;
+                    const uint32_t neg = (~w >> 7) & 1u;   // bit 7 set -> positive
+                    const uint32_t j = w >> 8;
+                    S val = z128_value<DT>(t, i, j, neg, lane, (v & 3) == 3);
+                    const bool slow = j >= t.K[i][lane];
+                    if (__any_sync(kFull, slow)) {
+                        if (slow) val = z128_slow<G, DT>(g, t, ws, lane, v, i, j, neg, drel, smask);
+                    }
+                    ws.stage[zslot<B, S>(lane, v)] = val;
+                }
+                produced = B;
+            } else {
+                // the end of some streams: up to min(rem, B) candidates per lane
+                const int cnt = (int)umin64(rem, (uint64_t)B);
+                produced = 0;
 #pragma unroll 1
-            for (int v = 0; v < 16; v += 2) {
-                OutT v0, v1;
-                SlowRec r0, r1;
-                const bool s0 = (v < cnt) && z128_candidate<G, DT>(g, t, lane, v, v0, r0, draws);
-                const bool s1 = (v + 1 < cnt) && z128_candidate<G, DT>(g, t, lane, v + 1, v1, r1, draws);
-                Pair pr;
-                if constexpr (DT == ZIG_BF16) pr = (uint32_t)v0 | ((uint32_t)v1 << 16);
-                else pr = Pair{v0, v1};
-                *(Pair*)&stage[zelt<OutT>(lane, v)] = pr;
-                const uint32_t m0 = __ballot_sync(kFull, s0);
-                const uint32_t m1 = __ballot_sync(kFull, s1);
-                if (m0 | m1) {
-                    if (s0) q[(tail + __popc(m0 & lt_mask)) & (kQCap - 1)] = r0;
-                    tail += __popc(m0);
-                    if (s1) q[(tail + __popc(m1 & lt_mask)) & (kQCap - 1)] = r1;
-                    tail += __popc(m1);
-                    if (tail - head >= 32) {
-                        __syncwarp();
-                        run_pass(head, 32);
-                        head += 32;
-                        __syncwarp();
+                for (int v = 0; v < B; ++v) {
+                    if (v < cnt && drel < 60000u) {
+                        const uint32_t w = g.next_u32();
+                        ++drel;
+                        const uint32_t i = w & 0x7Fu;
+                        const uint32_t neg = (~w >> 7) & 1u;
+                        const uint32_t j = w >> 8;
+                        S val = z128_value<DT>(t, i, j, neg, lane, false);
+                        if (j >= t.K[i][lane]) val = z128_slow<G, DT>(g, t, ws, lane, v, i, j, neg, drel, smask);
+                        ws.stage[zslot<B, S>(lane, v)] = val;
+                        produced = v + 1;
                     }
                 }
             }
-            // drain the rest of this batch's records
-            while (tail != head) {
+            draws += drel;
+            // ---- B: decide the deferred wedges, 32 at a time ----
+            const int ns = __popc(smask);
+            int incl = ns;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(kFull, incl, 31);
+            if (total) {
+                ws.smask[lane] = smask;
+                ws.excl[lane] = (uint32_t)(incl - ns);
                 __syncwarp();
-                const uint32_t n = umin64(tail - head, 32);
-                run_pass(head, n);
-                head += n;
+                for (int base = 0; base < total; base += 32) {
+                    const int r = base + lane;
+                    if (r < total) {
+                        // the row holding record r: the last o with excl[o] <= r (excl[0] = 0;
+                        // o + step never exceeds 31)
+                        int o = 0;
+#pragma unroll
+                        for (int step = 16; step; step >>= 1)
+                            if (ws.excl[o + step] <= (uint32_t)r) o += step;
+                        uint32_t m = ws.smask[o];
+                        for (int k = r - (int)ws.excl[o]; k > 0; --k) m &= m - 1;
+                        const int slot = __ffs(m) - 1;
+                        const uint32_t meta = (uint32_t)ws.stage[zslot<B, S>(o, slot)];
+                        const uint32_t j = meta & 0xFFFFFFu, i = (meta >> 24) & 0x7Fu, neg = meta >> 31;
+                        const uint64_t b = G::snap_at(ws.saved[o], ws.dd[o][slot], &d_jump);
+                        if (z128_wedge_accept(t, i, j, G::m53_of(b, 0, 0)))
+                            ws.stage[zslot<B, S>(o, slot)] = z128_value<DT>(t, i, j, neg, lane, false);
+                        else
+                            atomicOr(&ws.rej[o], 1u << slot);
+                    }
+                }
             }
             __syncwarp();
-            // rejected slots are skipped (each costs the stream one more layer draw,
-            // which the next batch draws as a new candidate)
-            const int acc = cnt - __popc(rej[lane]);
-            rowinfo[lane].dst = (unsigned long long)dst;
-            rowinfo[lane].cnt = acc;
+            // ---- C: write the rows, skipping rejected slots ----
+            const uint32_t rj = ws.rej[lane];
+            const int acc = produced - __popc(rj);
+            ws.rowinfo[lane].dst = (unsigned long long)dst;
+            ws.rowinfo[lane].cnt = acc;
+            ws.rowinfo[lane].rej = rj;
             __syncwarp();
             {
-                const int half = lane >> 4, c = lane & 15;
+                constexpr int kLanesPerRow = (B == 32) ? 32 : 16;
+                constexpr int kRowsPerStep = 32 / kLanesPerRow;
+                const int sub = lane / kLanesPerRow, c = lane % kLanesPerRow;
 #pragma unroll 4
-                for (int k = 0; k < 16; ++k) {
-                    const int row = 2 * k + half;
-                    const int rc = rowinfo[row].cnt;
-                    OutT* rd = (OutT*)rowinfo[row].dst;
-                    if (c < rc) {
-                        // slot of the row's c-th accepted candidate
-                        int src = c;
-                        for (uint32_t m = rej[row]; m; m &= m - 1) {
+                for (int k = 0; k < 32 / kRowsPerStep; ++k) {
+                    const int row = kRowsPerStep * k + sub;
+                    const RowInfo ri = ws.rowinfo[row];
+                    if (c < ri.cnt) {
+                        int src = c;   // slot of the row's c-th accepted candidate
+                        for (uint32_t m = ri.rej; m; m &= m - 1) {
                             if (__ffs(m) - 1 <= src) ++src;
                             else break;
                         }
-                        const OutT z = stage[zelt<OutT>(row, src)];
-                        if constexpr (MODE == 0) rd[c] = z;
-                        else ((float*)rd)[c] = fmaf(a.sigma, (float)z, ((float*)rd)[c]);
+                        const S z = ws.stage[zslot<B, S>(row, src)];
+                        OutT* rd = (OutT*)ri.dst;
+                        if constexpr (MODE == 1) {
+                            ((float*)rd)[c] = fmaf(a.sigma, __uint_as_float((uint32_t)z), ((float*)rd)[c]);
+                        } else if constexpr (DT == ZIG_F64) {
+                            rd[c] = __longlong_as_double((long long)z);
+                        } else if constexpr (DT == ZIG_F32) {
+                            rd[c] = __uint_as_float((uint32_t)z);
+                        } else {
+                            rd[c] = f32_to_bf16_bits(__uint_as_float((uint32_t)z));
+                        }
                     }
                 }
             }
@@ -881,11 +932,15 @@ static GenFn pick(int alg, int prng, int dt) {
 }
 
 // Dynamic shared memory a kernel needs (0 for the kernels that use static only).
-static size_t dyn_smem_of(int alg, int dt) {
+template <class G>
+static size_t z128_dyn_for(int dt) {
+    return (dt == ZIG_F64 ? z128_warp_bytes<G, ZIG_F64>() : z128_warp_bytes<G, ZIG_F32>()) * kZWarps;
+}
+
+static size_t dyn_smem_of(int alg, int dt, int prng) {
     if (alg != ZIG_ZIG128) return 0;
-    size_t per = dt == ZIG_F64 ? z128_warp_bytes<double>()
-               : dt == ZIG_F32 ? z128_warp_bytes<float>() : z128_warp_bytes<uint16_t>();
-    return per * kZWarps;
+    return prng == ZIG_LCG48 ? z128_dyn_for<GenLcg48>(dt)
+         : prng == ZIG_SPLITMIX64 ? z128_dyn_for<GenSplitMix64>(dt) : z128_dyn_for<GenL64X128Mix>(dt);
 }
 
 static int block_of(int alg) { return alg == ZIG_ZIG128 ? kZBlock : kBlock; }
@@ -1004,7 +1059,7 @@ zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
         n_groups_hint = ~0ull >> 8;   // unknown on the host: fill the device
     }
     host::GenFn fn = host::pick(alg, prng, dtype);
-    const size_t dyn = host::dyn_smem_of(alg, dtype);
+    const size_t dyn = host::dyn_smem_of(alg, dtype, prng);
     if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
     const int block = host::block_of(alg);
     int grid = host::grid_for((const void*)fn, dev, n_groups_hint, dyn, block);
@@ -1039,7 +1094,7 @@ zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_
                    : prng == ZIG_SPLITMIX64 ? z128_kernel<1, ZIG_F32, 1>
                                             : z128_kernel<2, ZIG_F32, 1>;
     am.mut_seed = seed;
-    const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32);
+    const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32, prng);
     if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
     int grid = host::grid_for((const void*)fn, dev, groups, dyn, kZBlock);
     fn<<<grid, kZBlock, dyn, s>>>(am);
@@ -1158,7 +1213,7 @@ extern "C" zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uin
                                    (uint64_t*)a.ustart, (uint64_t*)a.totals);
     if (cudaGetLastError() != cudaSuccess) return ZIG_ERR_CUDA;
     host::GenFn fn = host::pick(alg, prng, dtype);
-    const size_t dyn = host::dyn_smem_of(alg, dtype);
+    const size_t dyn = host::dyn_smem_of(alg, dtype, prng);
     if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
     const int block = host::block_of(alg);
     int grid = host::grid_for((const void*)fn, dev, ~0ull >> 8, dyn, block);
