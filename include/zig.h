@@ -182,6 +182,72 @@ zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uint64_t *seed
 zig_status zig_mutate(float *x_dev, float sigma, uint64_t P, uint64_t L, uint64_t seed,
                       zig_prng prng, void *stream);
 
+/* One request of a mutation batch: x_dev (P x L binary32, device) += sigma * N(0,1),
+ * rows seeded seed + p, exactly as zig_mutate. */
+typedef struct {
+    float *x_dev;
+    uint64_t P, L;
+    float sigma;
+    uint64_t seed;
+} zig_mutation;
+
+/*
+ * zig_mutate_batch -- n_req mutation requests in one launch (continuous
+ * batching of the Gaussian-mutation workload, Sec. 1).  Each request's result is
+ * identical to zig_mutate on it alone; requests must not overlap in memory.
+ * reqs_host: host array (copied before the call returns).  desc_dev: device
+ * scratch of at least zig_mutate_batch_desc_bytes(n_req) bytes, 16-byte aligned,
+ * not used by another call in flight.  All requests use one generator `prng`.
+ */
+size_t zig_mutate_batch_desc_bytes(uint32_t n_req);
+zig_status zig_mutate_batch(const zig_mutation *reqs_host, uint32_t n_req, zig_prng prng,
+                            void *desc_dev, size_t desc_bytes, void *stream);
+
+/*
+ * Continuous-batching service for mutation requests (serving form of Sec. 1's
+ * workload).  A worker thread admits submitted requests in arrival order while
+ * the bytes of the populations in flight stay within budget_bytes, packs up to
+ * max_batch of them into one zig_mutate_batch launch on one of n_slots streams,
+ * and retires a launch when its CUDA event completes; requests that arrive
+ * meanwhile go to the next free slot, so launches overlap on the device.  Each
+ * result equals zig_mutate on that request alone.  Populations are
+ * caller-owned device memory and must not overlap while in flight.
+ * device < 0 runs the scheduler without a GPU (launches complete after a
+ * simulated time), for testing the admission logic.
+ *
+ * zig_server_create  -- start a service (allocates its streams, events and a
+ *                       descriptor buffer per slot).
+ * zig_server_submit  -- enqueue x += sigma * N(0,1) on P x L binary32 x_dev with
+ *                       row seeds seed + p; returns a ticket.  A population larger
+ *                       than the budget is refused with ZIG_ERR_BUDGET.
+ * zig_server_wait    -- block until the ticket completes (timeout_s < 0: no
+ *                       limit; ZIG_ERR_TIMEOUT on expiry); returns its status.
+ * zig_server_query   -- state (0 queued, 1 running, 2 done, 3 failed), latency
+ *                       from submit to completion and queueing time, in us.
+ * zig_server_drain   -- wait until nothing is queued or running.
+ * zig_server_stats   -- counts, p50 / p99 latency, batching and peak memory.
+ * zig_server_destroy -- finish all work and stop.
+ */
+typedef struct zig_server zig_server;
+typedef struct {
+    uint64_t submitted, completed, failed, elements;
+    double latency_p50_us, latency_p99_us, span_us;
+    uint64_t batches;
+    double mean_batch;
+    uint64_t peak_inflight_bytes;
+    uint32_t peak_busy_slots, reserved;
+} zig_serving_stats;
+zig_status zig_server_create(int device, zig_prng prng, uint64_t budget_bytes, uint32_t n_slots,
+                             uint32_t max_batch, zig_server **out);
+zig_status zig_server_submit(zig_server *server, float *x_dev, uint64_t P, uint64_t L, float sigma,
+                             uint64_t seed, uint64_t *ticket);
+zig_status zig_server_wait(zig_server *server, uint64_t ticket, double timeout_s);
+zig_status zig_server_query(zig_server *server, uint64_t ticket, int *state, double *latency_us,
+                            double *queue_us);
+zig_status zig_server_drain(zig_server *server, double timeout_s);
+zig_status zig_server_stats(zig_server *server, zig_serving_stats *out);
+zig_status zig_server_destroy(zig_server *server);
+
 /*
  * zig_prng_fill -- raw uniform draws, for bit-exact checks of the generators.
  * out_dev: n_streams x n uint64 (device), stream-major.  kind 0 = nextInt

@@ -32,8 +32,28 @@ FILL_KIND = {"u32": 0, "u64": 1, "m53": 2}
 EXPORTS = (
     "zig_tables_init", "zig_tables_get_zig128", "zig_generate", "zig_generate_workspace_bytes",
     "zig_mutate", "zig_prng_fill", "zig_device_status", "zig_status_string", "zig_version",
-    "zig_generate_noalloc",
+    "zig_generate_noalloc", "zig_mutate_batch_desc_bytes", "zig_mutate_batch",
+    "zig_server_create", "zig_server_submit", "zig_server_wait", "zig_server_query",
+    "zig_server_drain", "zig_server_stats", "zig_server_destroy",
 )
+
+
+class Mutation(C.Structure):
+    """zig_mutation: one request of a mutation batch."""
+    _fields_ = [("x_dev", C.c_void_p), ("P", C.c_uint64), ("L", C.c_uint64),
+                ("sigma", C.c_float), ("seed", C.c_uint64)]
+
+
+class ServingStats(C.Structure):
+    """zig_serving_stats."""
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("elements", C.c_uint64), ("latency_p50_us", C.c_double),
+                ("latency_p99_us", C.c_double), ("span_us", C.c_double), ("batches", C.c_uint64),
+                ("mean_batch", C.c_double), ("peak_inflight_bytes", C.c_uint64),
+                ("peak_busy_slots", C.c_uint32), ("reserved", C.c_uint32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
 
 
 class ZigError(RuntimeError):
@@ -74,6 +94,21 @@ def load(build_if_missing: bool = True):
         lib.zig_generate_noalloc.argtypes = [i32, i32, vp, vp, u64, C.c_uint32, i32, vp, vp]
         lib.zig_generate_noalloc.restype = i32
         lib.zig_prng_fill.argtypes = [i32, vp, u64, u64, u64, i32, vp, vp]
+        lib.zig_mutate_batch_desc_bytes.argtypes = [C.c_uint32]
+        lib.zig_mutate_batch_desc_bytes.restype = C.c_size_t
+        lib.zig_mutate_batch.argtypes = [C.POINTER(Mutation), C.c_uint32, i32, vp, C.c_size_t, vp]
+        lib.zig_server_create.argtypes = [i32, i32, u64, C.c_uint32, C.c_uint32, C.POINTER(vp)]
+        lib.zig_server_submit.argtypes = [vp, vp, u64, u64, C.c_float, u64, C.POINTER(u64)]
+        lib.zig_server_wait.argtypes = [vp, u64, C.c_double]
+        lib.zig_server_query.argtypes = [vp, u64, C.POINTER(i32), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double)]
+        lib.zig_server_drain.argtypes = [vp, C.c_double]
+        lib.zig_server_stats.argtypes = [vp, C.POINTER(ServingStats)]
+        lib.zig_server_destroy.argtypes = [vp]
+        for name in ("zig_mutate_batch", "zig_server_create", "zig_server_submit", "zig_server_wait",
+                     "zig_server_query", "zig_server_drain", "zig_server_stats",
+                     "zig_server_destroy"):
+            getattr(lib, name).restype = i32
         lib.zig_device_status.argtypes = [i32, i32]
         lib.zig_status_string.argtypes = [i32]
         lib.zig_status_string.restype = C.c_char_p
@@ -151,6 +186,22 @@ def zig_mutate(x, sigma: float, P: int, L: int, seed: int, prng: str = "splitmix
     st = load().zig_mutate(x.data_ptr(), float(sigma), int(P), int(L),
                            int(seed) & (2 ** 64 - 1), PRNG[prng], _stream_ptr(stream))
     _check(st, "zig_mutate")
+
+
+def zig_mutate_batch(requests, prng: str = "splitmix64", desc=None, stream=None) -> None:
+    """requests: list of (x, sigma, seed) with x a P x L float32 CUDA tensor."""
+    import torch
+    n = len(requests)
+    arr = (Mutation * max(n, 1))()
+    for k, (x, sigma, seed) in enumerate(requests):
+        P, L = (x.shape[0], x.shape[1]) if x.dim() == 2 else (1, x.numel())
+        arr[k] = Mutation(x.data_ptr() or None, P, L, float(sigma), int(seed) & (2 ** 64 - 1))
+    need = int(load().zig_mutate_batch_desc_bytes(n))
+    if desc is None:
+        desc = torch.empty(need, dtype=torch.uint8, device="cuda")
+    st = load().zig_mutate_batch(arr, n, PRNG[prng], desc.data_ptr(), desc.numel(),
+                                 _stream_ptr(stream))
+    _check(st, "zig_mutate_batch")
 
 
 def zig_prng_fill(prng: str, seeds, n: int, out, skip: int = 0, kind: str = "u32",

@@ -2,7 +2,8 @@
 
     python -m paper_2405_19493_gb300.build [--force] [-v]
 
-The library is one translation unit (csrc/zig_lib.cu) plus its headers; the
+The library is csrc/zig_lib.cu (kernels and the C ABI) and csrc/zig_server.cpp
+(the mutation service's scheduler), plus their headers; the
 output goes to paper_2405_19493_gb300/_lib/libzig_gb300_<arch>.so (git-ignored),
 named by the host architecture because the x86 build host and the aarch64 GPU
 host share the tree.
@@ -21,8 +22,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB_DIR = os.path.join(HERE, "_lib")
-SOURCES = ["zig_lib.cu"]
-DEPS = ["zig_lib.cu", "zig_device.cuh", "zig_tables.inc"]
+SOURCES = ["zig_lib.cu", "zig_server.cpp"]
+DEPS = ["zig_lib.cu", "zig_server.cpp", "zig_device.cuh", "zig_tables.inc"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -52,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(LIB_DIR, exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
     cmd = [nvcc(), "-O3", "-std=c++17", *ARCH_FLAGS, "-lineinfo", "-shared",
-           "-Xcompiler", "-fPIC", "-cudart", "shared", "-I", INCLUDE,
+           "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-cudart", "shared", "-I", INCLUDE,
            "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

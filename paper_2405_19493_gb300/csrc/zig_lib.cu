@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "../../include/zig.h"
 #include "zig_device.cuh"
@@ -63,6 +64,16 @@ struct GenArgs {
     uint64_t units_per_stream; // uniform: units per stream
     float sigma;               // mutation only
     uint64_t mut_seed;         // mutation only: row p is seeded mut_seed + p
+    const struct MutDesc* reqs;  // batched mutation: request descriptors
+    uint32_t n_req;              // batched mutation: number of requests
+};
+
+// One mutation request of a batch (device copy; ustart = its first unit).
+struct MutDesc {
+    float* x;
+    uint64_t P, L, seed, upr, ustart;
+    float sigma;
+    uint32_t pad;
 };
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
@@ -483,6 +494,8 @@ struct RowInfo {
     unsigned long long dst;
     int cnt;
     uint32_t rej;
+    float sigma;       // mutation
+    uint32_t pad[3];
 };
 
 // Batch width: 32 slots per lane with 4-byte staging words, 16 with 8-byte words.
@@ -493,7 +506,7 @@ struct ZWarp {
     static constexpr int B = ZBatch<DT>::B;
     using S = typename ZStage<DT>::T;
     S stage[32 * B];
-    uint16_t dd[32][B];                   // raw steps before a deferred wedge's uniform
+    uint8_t dd[32][B];                    // raw steps before a deferred wedge's uniform
     typename G::Saved saved[32];          // each lane's generator at the batch start
     uint32_t smask[32], rej[32], excl[32];
     RowInfo rowinfo[32];
@@ -516,8 +529,9 @@ __host__ __device__ constexpr size_t z128_warp_bytes() {
 
 // Resolve a slow draw (j >= k[i]) of slot v.  A wedge is deferred to phase B
 // (its slot keeps j | i << 24 | negative << 31 and its step count goes to dd)
-// unless the batch's step count has outgrown 16 bits; a tail is decided here and
-// a rejected tail draws again for the same slot.  Returns the slot's word.
+// unless the batch's step count has outgrown 8 bits (a batch normally takes
+// about B + 2 steps); a tail is decided here and a rejected tail draws again for
+// the same slot.  Returns the slot's word.
 template <class G, int DT>
 __device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab& t, ZWarp<G, DT>& ws,
                                                              int lane, int v, uint32_t i, uint32_t j,
@@ -525,8 +539,8 @@ __device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab&
     using S = typename ZStage<DT>::T;
     for (;;) {
         if (i < 127) {
-            if (drel <= 0xFFFFu) {
-                ws.dd[lane][v] = (uint16_t)drel;
+            if (drel <= 0xFFu) {
+                ws.dd[lane][v] = (uint8_t)drel;
                 g.skip_double();
                 drel += G::kStepsPerDouble;
                 smask |= 1u << v;
@@ -552,7 +566,8 @@ __device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab&
     }
 }
 
-// MODE 0: generation into a.out; MODE 1: mutation x += sigma * z (binary32).
+// MODE 0: generation into a.out; MODE 1: mutation x += sigma * z (binary32);
+// MODE 2: a batch of mutation requests (a.reqs), each row with its own sigma.
 template <int PRNG, int DT, int MODE>
 __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
     using G = typename GenOf<PRNG>::T;
@@ -585,16 +600,34 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
         OutT* dst = out;
         G g;
         g.seed(0);
+        float sigma = a.sigma;
         if (u < n_units) {
-            uint64_t s, qd, off, n;
-            unit_info(a, u, s, qd, off, n);
-            g.seed(MODE == 0 ? a.seeds[s] : a.mut_seed + s);   // mutation: seed + row
-            if (qd) g.jump(qd * kChunkDraws, &d_jump);
-            rem = n;
-            dst = out + off;
+            if constexpr (MODE == 2) {
+                // batched mutation: the request holding unit u (the last with ustart <= u)
+                uint32_t lo = 0, hi = a.n_req;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (a.reqs[mid].ustart <= u) lo = mid; else hi = mid;
+                }
+                const MutDesc& r = a.reqs[lo];
+                const uint64_t ur = u - r.ustart, p = ur / r.upr, qd = ur - p * r.upr;
+                g.seed(r.seed + p);
+                if (qd) g.jump(qd * kChunkDraws, &d_jump);
+                const uint64_t t0 = qd << 10;
+                rem = umin64(r.L - t0, 1024);
+                dst = (OutT*)(r.x + p * r.L + t0);
+                sigma = r.sigma;
+            } else {
+                uint64_t s, qd, off, n;
+                unit_info(a, u, s, qd, off, n);
+                g.seed(MODE == 0 ? a.seeds[s] : a.mut_seed + s);   // mutation: seed + row
+                if (qd) g.jump(qd * kChunkDraws, &d_jump);
+                rem = n;
+                dst = out + off;
+            }
         }
         uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
-        const bool check_chunk = a.chunk_log2 != 0 && rem != 0;
+        const bool check_chunk = (MODE == 2 || a.chunk_log2 != 0) && rem != 0;
 
         while (__any_sync(kFull, rem > 0)) {
             ws.saved[lane] = g.save();
@@ -627,7 +660,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                 produced = 0;
 #pragma unroll 1
                 for (int v = 0; v < B; ++v) {
-                    if (v < cnt && drel < 60000u) {
+                    if (v < cnt) {
                         const uint32_t w = g.next_u32();
                         ++drel;
                         const uint32_t i = w & 0x7Fu;
@@ -683,6 +716,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             ws.rowinfo[lane].dst = (unsigned long long)dst;
             ws.rowinfo[lane].cnt = acc;
             ws.rowinfo[lane].rej = rj;
+            ws.rowinfo[lane].sigma = sigma;
             __syncwarp();
             {
                 constexpr int kLanesPerRow = (B == 32) ? 32 : 16;
@@ -700,8 +734,8 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                         }
                         const S z = ws.stage[zslot<B, S>(row, src)];
                         OutT* rd = (OutT*)ri.dst;
-                        if constexpr (MODE == 1) {
-                            ((float*)rd)[c] = fmaf(a.sigma, __uint_as_float((uint32_t)z), ((float*)rd)[c]);
+                        if constexpr (MODE != 0) {
+                            ((float*)rd)[c] = fmaf(ri.sigma, __uint_as_float((uint32_t)z), ((float*)rd)[c]);
                         } else if constexpr (DT == ZIG_F64) {
                             rd[c] = __longlong_as_double((long long)z);
                         } else if constexpr (DT == ZIG_F32) {
@@ -932,6 +966,16 @@ static GenFn pick(int alg, int prng, int dt) {
 }
 
 // Dynamic shared memory a kernel needs (0 for the kernels that use static only).
+// Every instantiation must fit one SM's shared memory (227 KB per block).
+template <class G, int DT>
+constexpr bool z128_fits() {
+    return z128_warp_bytes<G, DT>() * kZWarps + sizeof(Z128Tab) <= 227 * 1024;
+}
+static_assert(z128_fits<GenLcg48, ZIG_F64>() && z128_fits<GenLcg48, ZIG_F32>() &&
+                  z128_fits<GenSplitMix64, ZIG_F64>() && z128_fits<GenSplitMix64, ZIG_F32>() &&
+                  z128_fits<GenL64X128Mix, ZIG_F64>() && z128_fits<GenL64X128Mix, ZIG_F32>(),
+              "z128_kernel shared memory exceeds 227 KB per block");
+
 template <class G>
 static size_t z128_dyn_for(int dt) {
     return (dt == ZIG_F64 ? z128_warp_bytes<G, ZIG_F64>() : z128_warp_bytes<G, ZIG_F32>()) * kZWarps;
@@ -1098,6 +1142,57 @@ zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_
     if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
     int grid = host::grid_for((const void*)fn, dev, groups, dyn, kZBlock);
     fn<<<grid, kZBlock, dyn, s>>>(am);
+    return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
+}
+
+size_t zig_mutate_batch_desc_bytes(uint32_t n_req) { return (size_t)n_req * sizeof(MutDesc) + 256; }
+
+zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_prng prng, void* desc_dev,
+                            size_t desc_bytes, void* stream) {
+    if ((unsigned)prng > 2u) return ZIG_ERR_INVALID_ARG;
+    if (n_req == 0) return ZIG_OK;
+    if (!reqs_host || !desc_dev || desc_bytes < zig_mutate_batch_desc_bytes(n_req) ||
+        ((uintptr_t)desc_dev) % 16)
+        return ZIG_ERR_INVALID_ARG;
+    std::vector<MutDesc> d(n_req);
+    uint64_t units = 0;
+    for (uint32_t r = 0; r < n_req; ++r) {
+        const zig_mutation& q = reqs_host[r];
+        if (!std::isfinite(q.sigma) || (q.P && q.L && (!q.x_dev || ((uintptr_t)q.x_dev) % 4)) ||
+            q.L > (1ull << 40) || (q.L && q.P > (1ull << 40) / q.L))
+            return ZIG_ERR_INVALID_ARG;
+        d[r].x = q.x_dev;
+        d[r].P = q.P;
+        d[r].L = q.L;
+        d[r].seed = q.seed;
+        d[r].sigma = q.sigma;
+        d[r].upr = q.L ? (q.L + 1023) >> 10 : 1;
+        d[r].ustart = units;
+        d[r].pad = 0;
+        units += (q.P && q.L) ? q.P * d[r].upr : 0;
+    }
+    if (units == 0) return ZIG_OK;
+    int dev;
+    zig_status st = host::current_device(dev);
+    if (st != ZIG_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // pageable source: the copy is staged before this call returns, so reqs_host
+    // may be reused at once
+    if (cudaMemcpyAsync(desc_dev, d.data(), n_req * sizeof(MutDesc), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return ZIG_ERR_CUDA;
+    GenArgs a{};
+    a.reqs = (const MutDesc*)desc_dev;
+    a.n_req = n_req;
+    a.n_units = units;
+    a.chunk_log2 = 10;
+    host::GenFn fn = prng == ZIG_LCG48 ? z128_kernel<0, ZIG_F32, 2>
+                   : prng == ZIG_SPLITMIX64 ? z128_kernel<1, ZIG_F32, 2>
+                                            : z128_kernel<2, ZIG_F32, 2>;
+    const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32, prng);
+    if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
+    int grid = host::grid_for((const void*)fn, dev, (units + 31) / 32, dyn, kZBlock);
+    fn<<<grid, kZBlock, dyn, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
 }
 

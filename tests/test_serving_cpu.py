@@ -1,0 +1,57 @@
+"""The mutation service's scheduler without a GPU (dry run: simulated launches).
+
+Checks admission in arrival order under the memory budget, refusal of a
+population larger than the budget, batching of requests that queue up, and the
+latency statistics.
+"""
+
+import pytest
+
+from paper_2405_19493_gb300 import _binding as B
+from paper_2405_19493_gb300.serving import MutationServer
+
+FAKE = 1 << 20   # a non-null pointer; dry runs never dereference it
+
+
+def test_dry_run_admission_and_batching():
+    budget = 64 << 20   # 64 MiB
+    with MutationServer(device=-1, budget_bytes=budget, n_slots=2, max_batch=8) as srv:
+        tickets = [srv.submit(None, 0.5, k, P=64, L=32768, x_ptr=FAKE) for k in range(40)]   # 8 MiB each
+        srv.drain(timeout_s=30)
+        st = srv.stats()
+        assert st["completed"] == 40 and st["failed"] == 0
+        assert st["peak_inflight_bytes"] <= budget
+        assert st["batches"] < 40 and st["mean_batch"] > 1          # requests were batched
+        assert st["peak_busy_slots"] <= 2
+        assert 0 < st["latency_p50_us"] <= st["latency_p99_us"]
+        for t in tickets:
+            q = srv.query(t)
+            assert q["state"] == 2 and q["queue_us"] >= 0 and q["latency_us"] >= q["queue_us"]
+
+
+def test_dry_run_budget_refusal_and_invalid():
+    with MutationServer(device=-1, budget_bytes=1 << 20, n_slots=1, max_batch=4) as srv:
+        with pytest.raises(B.ZigError) as e:
+            srv.submit(None, 0.1, 1, P=1024, L=1024, x_ptr=FAKE)       # 4 MiB > 1 MiB
+        assert e.value.status == 4                                      # ZIG_ERR_BUDGET
+        t = srv.submit(None, 0.1, 2, P=16, L=16, x_ptr=FAKE)
+        srv.wait(t, timeout_s=10)
+        assert srv.query(t)["state"] == 2
+        with pytest.raises(B.ZigError):
+            srv.submit(None, float("nan"), 3, P=4, L=4, x_ptr=FAKE)
+        st = srv.stats()
+        assert st["failed"] == 1 and st["completed"] == 1
+
+
+def test_dry_run_fifo_under_memory_pressure():
+    # each request needs the whole budget: they must run one at a time, in order
+    budget = 4 << 20
+    with MutationServer(device=-1, budget_bytes=budget, n_slots=4, max_batch=16) as srv:
+        tickets = [srv.submit(None, 0.3, k, P=1024, L=1024, x_ptr=FAKE) for k in range(6)]
+        srv.drain(timeout_s=30)
+        st = srv.stats()
+        assert st["peak_busy_slots"] == 1 and st["batches"] == 6
+        # one at a time in arrival order: each waits at least as long as the one before
+        q = [srv.query(t)["queue_us"] for t in tickets]
+        assert all(q[k] <= q[k + 1] + 1e-6 for k in range(5))
+        assert all(srv.query(t)["latency_us"] > 0 for t in tickets)
