@@ -299,6 +299,11 @@ def run_gpu(args):
 
     # end to end through the public call: seeds from pinned host memory, result back to host
     e2e = measure_e2e(Z, torch, seeds_np, stream, args)
+    if rank == 0 and not args.no_serving:
+        del out
+        torch.cuda.empty_cache()
+        line_extra["serving"] = measure_serving(Z, torch)
+        out = None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -310,7 +315,7 @@ def run_gpu(args):
     }
     line.update(line_extra)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        del out
+        out = None
         torch.cuda.empty_cache()
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -355,19 +360,81 @@ def compare_variants(Z, torch, seeds, stream, args):
     sd = torch.from_numpy(W.seeds(len(L)).view(np.int64)).cuda()
     ln = torch.from_numpy(L.view(np.int64)).cuda()
     total = int(L.sum())
+    ws = torch.empty(Z.zig_generate_workspace_bytes(len(L)), dtype=torch.uint8, device="cuda")
     for dt in ("f64", "f32"):
         tdt = torch.float64 if dt == "f64" else torch.float32
         o = torch.empty(total, dtype=tdt, device="cuda")
         fn = lambda: Z.zig_generate("splitmix64", "zig128", sd, o, lengths=ln, chunk_log2=10,
-                                    dtype=dt, stream=stream)
+                                    dtype=dt, workspace=ws, stream=stream)
         fn()
         ts = time_launches(torch, stream, fn, reps)
         m = statistics.mean(ts)
-        res[f"batched/zig128/splitmix64/{dt}"] = {
-            "variates_per_s": total / (m / 1e3), "ms_mean": m, "variates": total,
-            "write_gbs": total * o.element_size() / (m / 1e3) / 1e9}
-        del o
+        entry = {"variates_per_s": total / (m / 1e3), "ms_mean": m, "variates": total,
+                 "write_gbs": total * o.element_size() / (m / 1e3) / 1e9}
+        # the same request captured once in a CUDA graph (prefix sums + the persistent
+        # generation launch) and replayed
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            fn_side = lambda: Z.zig_generate("splitmix64", "zig128", sd, o, lengths=ln, chunk_log2=10,
+                                             dtype=dt, workspace=ws, stream=side)
+            fn_side()
+            with torch.cuda.graph(g, stream=side):
+                fn_side()
+        torch.cuda.current_stream().wait_stream(side)
+        g.replay()
+        torch.cuda.synchronize()
+        tg = time_launches(torch, stream, g.replay, reps)
+        mg = statistics.mean(tg)
+        entry["graph_replay"] = {"variates_per_s": total / (mg / 1e3), "ms_mean": mg}
+        res[f"batched/zig128/splitmix64/{dt}"] = entry
+        del o, g
     return res
+
+
+def measure_serving(Z, torch, rates=(1000, 10000, 50000), n_req=1500):
+    """Gaussian-mutation requests, Poisson arrivals, through the native service.
+
+    Populations live in one device arena (48 GB) handed out as a ring; the service
+    admits requests while the bytes in flight stay within 40 GB.  The arena's
+    contents are placeholders: only timing is measured here (results are checked
+    bit for bit in tests/test_gpu_serving.py).
+    """
+    from paper_2405_19493_gb300 import workloads as W
+    from paper_2405_19493_gb300.serving import MutationServer, drive_poisson
+    arena_bytes, budget = 48 << 30, 40 << 30
+    arena = torch.empty(arena_bytes // 4, dtype=torch.float32, device="cuda")
+    base = arena.data_ptr()
+    out = {}
+    for rate in rates:
+        reqs = W.mutation_requests(n_req, rate_hz=rate, seed=11 + rate)
+        offs, pos = [], 0
+        for r in reqs:
+            nb = r["P"] * r["L"] * 4
+            if pos + nb > arena_bytes:
+                pos = 0
+            offs.append(pos)
+            pos += (nb + 255) // 256 * 256
+        with MutationServer(device=torch.cuda.current_device(), prng="splitmix64",
+                            budget_bytes=budget, n_slots=4, max_batch=64) as srv:
+            drive_poisson(srv, reqs, lambda k, r: base + offs[k])
+            srv.drain()
+            st = srv.stats()
+        span_s = st["span_us"] / 1e6
+        out[f"{rate}_req_per_s"] = {
+            "requests": st["completed"], "latency_p50_ms": st["latency_p50_us"] / 1e3,
+            "latency_p99_ms": st["latency_p99_us"] / 1e3,
+            "throughput_req_per_s": st["completed"] / span_s if span_s else None,
+            "elements_per_s": st["elements"] / span_s if span_s else None,
+            "mean_batch": st["mean_batch"], "launches": st["batches"],
+            "peak_inflight_gb": st["peak_inflight_bytes"] / 1e9}
+    del arena
+    torch.cuda.empty_cache()
+    return {"workload": ("x += sigma*N(0,1) on float32 P x L populations, P log-uniform 16..4096, "
+                         "L log-uniform 8..100,000, sigma U[0.01,1], per-request seed, Poisson "
+                         f"arrivals, {n_req} requests per rate, 40 GB admission budget, 4 stream "
+                         "slots, up to 64 requests per launch"), "rates": out}
 
 
 def measure_e2e(Z, torch, seeds_np, stream, args):
@@ -427,6 +494,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--ncu-case", default=None,
                     help="run only alg:prng:dtype:n_streams:len[:chunk_log2] (for ncu)")
     ap.add_argument("--reps", type=int, default=2)

@@ -991,17 +991,45 @@ static int block_of(int alg) { return alg == ZIG_ZIG128 ? kZBlock : kBlock; }
 
 // Opt in to the dynamic shared memory a launch needs (static + dynamic may pass
 // the 48 KB default only with the attribute set).
+// Per-kernel launch facts, resolved once (so a launch inside stream capture only
+// enqueues work): the dynamic shared-memory opt-in and the resident blocks per SM.
+struct LaunchFacts {
+    const void* fn;
+    int dev;
+    size_t dyn;
+    int block;
+    int per_sm;
+};
+std::mutex g_facts_mu;
+std::vector<LaunchFacts> g_facts;
+
 static bool allow_dyn_smem(const void* fn, size_t bytes) {
     if (bytes == 0) return true;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
-           cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_facts_mu);
+    for (const LaunchFacts& f : g_facts)
+        if (f.fn == fn && f.dev == dev && f.dyn == bytes && f.block == -1) return true;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return false;
+    g_facts.push_back(LaunchFacts{fn, dev, bytes, -1, 0});
+    return true;
 }
 
-static int grid_for(const void* fn, int dev, uint64_t n_groups, size_t dyn = 0, int block = kBlock) {
+static int blocks_per_sm(const void* fn, int dev, size_t dyn, int block) {
+    std::lock_guard<std::mutex> lk(g_facts_mu);
+    for (const LaunchFacts& f : g_facts)
+        if (f.fn == fn && f.dev == dev && f.dyn == dyn && f.block == block) return f.per_sm;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, dyn) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
+    g_facts.push_back(LaunchFacts{fn, dev, dyn, block, per_sm});
+    return per_sm;
+}
+
+static int grid_for(const void* fn, int dev, uint64_t n_groups, size_t dyn = 0, int block = kBlock) {
+    const int per_sm = blocks_per_sm(fn, dev, dyn, block);
     uint64_t full = (uint64_t)g_sms[dev] * per_sm;
     const uint64_t warps = (uint64_t)block / 32;
     uint64_t need = (n_groups + warps - 1) / warps;
