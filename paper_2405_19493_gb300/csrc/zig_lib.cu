@@ -158,6 +158,31 @@ __device__ __forceinline__ void z256_load(Z256Smem& t) {
     }
 }
 
+// binary64 value of an integer m < 2^53 (exact), scaled by 2^-k, built with
+// integer operations: GB300's conversion to binary64 runs on the narrow binary64 pipe.
+__device__ __forceinline__ double u53_to_double(uint64_t m, int k = 0) {
+    const int lz = __clzll((long long)m);   // 11..63 (64 for m = 0)
+    const uint64_t frac = ((m << (lz & 63)) >> 11) & ((1ull << 52) - 1);
+    const uint64_t bits = ((uint64_t)(1086 - lz - k) << 52) | frac;
+    return m ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+// binary32 filter for an overhang test y < exp(-x^2/2): x = ox + odx u, y = oy + ody v
+// with u, v in [0, 1).  The binary32 errors are below 3e-6 relative (x < 3.7,
+// expf within 2 ulp), far inside the 2^-16 margin; returns 1 accept, 0 reject,
+// -1 undecided (evaluate in binary64).
+__device__ __forceinline__ int z256_overhang_filter(float ox, float odx, float oy, float ody, uint64_t m1,
+                                                    uint64_t m2) {
+    const float u = (float)(uint32_t)(m1 >> 29) * 0x1p-24f;
+    const float v = (float)(uint32_t)(m2 >> 29) * 0x1p-24f;
+    const float x = __fmaf_rn(odx, u, ox);
+    const float y = __fmaf_rn(ody, v, oy);
+    const float e = expf(-0.5f * x * x);
+    if (y < e * (1.0f - 0x1p-16f)) return 1;
+    if (y > e * (1.0f + 0x1p-16f)) return 0;
+    return -1;
+}
+
 template <class G>
 __device__ __forceinline__ double z256_slow(G& g, const Z256Smem& t, uint32_t& extra) {
     constexpr uint32_t kSteps64 = (sizeof(G) == sizeof(GenLcg48)) ? 2u : 1u;
@@ -190,10 +215,13 @@ __device__ __forceinline__ double z256_slow(G& g, const Z256Smem& t, uint32_t& e
             m1 = two53 - m1;
             m2 = two53 - m2;
         }
-        double x = __dadd_rn(ox, __dmul_rn(odx, m53_to_double(m1)));
+        const double x = __dadd_rn(ox, __dmul_rn(odx, u53_to_double(m1, 53)));
         if (kd > 0 && m1 + m2 <= two53 - qa) return x;
         if (kd < 0 && m1 + m2 < two53) return x;
-        double y = __dadd_rn(oy, __dmul_rn(ody, m53_to_double(m2)));
+        const int f = z256_overhang_filter((float)ox, (float)odx, (float)oy, (float)ody, m1, m2);
+        if (f == 1) return x;
+        if (f == 0) continue;
+        const double y = __dadd_rn(oy, __dmul_rn(ody, u53_to_double(m2, 53)));
         if (y < exp(neg_half_sq(x))) return x;
     }
 }
@@ -205,11 +233,11 @@ __device__ __forceinline__ double z256_f64(G& g, const Z256Smem& t, uint32_t& ex
     bool neg = (U >> 8) & 1;
     double x;
     if (j < (uint32_t)zigtab::ZIG256_NR) {
-        x = __dmul_rn(t.XS[j], (double)(U >> 11));
+        x = __dmul_rn(t.XS[j], u53_to_double(U >> 11));
     } else {
         x = z256_slow(g, t, extra);
     }
-    return neg ? -x : x;
+    return __longlong_as_double(__double_as_longlong(x) | ((long long)neg << 63));   // x >= 0
 }
 
 // ---------------------------------------------------------------------------
@@ -734,14 +762,15 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                         }
                         const S z = ws.stage[zslot<B, S>(row, src)];
                         OutT* rd = (OutT*)ri.dst;
+                        // write-once output: global streaming stores (evict-first)
                         if constexpr (MODE != 0) {
                             ((float*)rd)[c] = fmaf(ri.sigma, __uint_as_float((uint32_t)z), ((float*)rd)[c]);
                         } else if constexpr (DT == ZIG_F64) {
-                            rd[c] = __longlong_as_double((long long)z);
+                            __stcs((unsigned long long*)rd + c, (unsigned long long)z);
                         } else if constexpr (DT == ZIG_F32) {
-                            rd[c] = __uint_as_float((uint32_t)z);
+                            __stcs((unsigned int*)rd + c, (unsigned int)z);
                         } else {
-                            rd[c] = f32_to_bf16_bits(__uint_as_float((uint32_t)z));
+                            __stcs((unsigned short*)rd + c, f32_to_bf16_bits(__uint_as_float((uint32_t)z)));
                         }
                     }
                 }
