@@ -388,8 +388,20 @@ def compare_variants(Z, torch, seeds, stream, args):
         tg = time_launches(torch, stream, g.replay, reps)
         mg = statistics.mean(tg)
         entry["graph_replay"] = {"variates_per_s": total / (mg / 1e3), "ms_mean": mg}
+        del g
+        # the autotuner on this request: every candidate (block size x batch width x
+        # store width) timed through the C ABI, the fastest recorded, then re-timed
+        # as zig_generate runs it
+        cfg, tune_ms = Z.zig_autotune("splitmix64", sd, o, lengths=ln, chunk_log2=10, dtype=dt,
+                                      reps=3, workspace=ws, stream=stream)
+        tt = time_launches(torch, stream, fn, reps)
+        mt = statistics.mean(tt)
+        entry["autotuned"] = {"config": cfg, "candidates": len(Z.zig_autotune_candidates(dt)),
+                              "tuner_ms_per_call": tune_ms, "variates_per_s": total / (mt / 1e3),
+                              "ms_mean": mt}
+        Z.zig_launch_config_set("splitmix64", dt, True, None)
         res[f"batched/zig128/splitmix64/{dt}"] = entry
-        del o, g
+        del o
     return res
 
 

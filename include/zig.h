@@ -170,6 +170,55 @@ zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uint64_t *seed
                                 void *stream);
 
 /*
+ * Launch configuration of the 128-level generation kernel (ZIG_ZIG128).  The
+ * paper's single-threaded Java generator has no counterpart; these knobs only
+ * change how the same work is laid out on the GPU, never the values:
+ *  block        threads per block, a multiple of 32 in [64, 768] (default 768).
+ *  batch        candidates each lane draws per batch before the warp decides its
+ *               deferred wedge tests and writes: 16 (default) or 8 for
+ *               ZIG_F64; 32 (default) or 16 for ZIG_F32 and ZIG_BF16.
+ *  store_bytes  0 (default): one element per store; 16: each output row goes
+ *               out as the aligned 16-byte vectors that cover it (partly covered
+ *               vectors element by element).
+ * One configuration is kept per device, PRNG, dtype and input form
+ * (variable_lengths = 1 for calls with a lengths array, 0 for uniform ones);
+ * zig_generate and zig_generate_noalloc read it at each call.
+ */
+typedef struct {
+    uint32_t block;
+    uint32_t batch;
+    uint32_t store_bytes;
+    uint32_t reserved; /* 0 */
+} zig_launch_config;
+
+/* The recorded configuration (the default if none was set). No CUDA call. */
+zig_status zig_launch_config_get(int device, zig_prng prng, zig_dtype dtype, int variable_lengths,
+                                 zig_launch_config *cfg);
+/* Record cfg (validated as above: ZIG_ERR_INVALID_ARG otherwise); cfg = NULL
+ * restores the default.  No CUDA call. */
+zig_status zig_launch_config_set(int device, zig_prng prng, zig_dtype dtype, int variable_lengths,
+                                 const zig_launch_config *cfg);
+/* The configurations zig_autotune tries for dtype (blocks 256/384/512/768 x both
+ * batch widths x both store widths): writes up to max_cands of them to cands
+ * (may be NULL) and returns how many there are. */
+uint32_t zig_autotune_candidates(zig_dtype dtype, zig_launch_config *cands, uint32_t max_cands);
+/*
+ * zig_autotune -- time every candidate configuration on the caller's own
+ * ZIG_ZIG128 request and record the fastest for the current device, prng,
+ * dtype and input form.  The arguments are zig_generate's (alg = ZIG_ZIG128).
+ * Each candidate runs once untimed and then `reps` times (1..1000) back to back
+ * on `stream`, timed with CUDA events; the call synchronizes on the events and
+ * returns the chosen configuration in *best and its mean time per call in
+ * *best_ms (either may be NULL).  out_dev holds the request's outputs when it
+ * returns, as after zig_generate.  ZIG_ERR_INVALID_ARG while the stream is
+ * being captured into a graph; other errors as zig_generate.
+ */
+zig_status zig_autotune(zig_prng prng, const uint64_t *seeds_dev, const uint64_t *lengths_dev,
+                        uint64_t uniform_len, uint64_t n_streams, uint32_t chunk_log2,
+                        zig_dtype dtype, void *out_dev, void *workspace_dev, size_t workspace_bytes,
+                        uint32_t reps, zig_launch_config *best, float *best_ms, void *stream);
+
+/*
  * zig_mutate -- Gaussian mutation x += sigma * N(0,1) in place (the paper's
  * motivating workload, Sec. 1: Gaussian mutation in an evolutionary algorithm).
  * x_dev: P x L binary32 row-major population (device).  Row p draws its L

@@ -35,6 +35,7 @@ EXPORTS = (
     "zig_generate_noalloc", "zig_mutate_batch_desc_bytes", "zig_mutate_batch",
     "zig_server_create", "zig_server_submit", "zig_server_wait", "zig_server_query",
     "zig_server_drain", "zig_server_stats", "zig_server_destroy",
+    "zig_launch_config_get", "zig_launch_config_set", "zig_autotune_candidates", "zig_autotune",
 )
 
 
@@ -42,6 +43,15 @@ class Mutation(C.Structure):
     """zig_mutation: one request of a mutation batch."""
     _fields_ = [("x_dev", C.c_void_p), ("P", C.c_uint64), ("L", C.c_uint64),
                 ("sigma", C.c_float), ("seed", C.c_uint64)]
+
+
+class LaunchConfig(C.Structure):
+    """zig_launch_config: block size, batch width and store width of the 128-level kernel."""
+    _fields_ = [("block", C.c_uint32), ("batch", C.c_uint32), ("store_bytes", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+    def as_dict(self):
+        return {"block": self.block, "batch": self.batch, "store_bytes": self.store_bytes}
 
 
 class ServingStats(C.Structure):
@@ -108,6 +118,14 @@ def load(build_if_missing: bool = True):
         for name in ("zig_mutate_batch", "zig_server_create", "zig_server_submit", "zig_server_wait",
                      "zig_server_query", "zig_server_drain", "zig_server_stats",
                      "zig_server_destroy"):
+            getattr(lib, name).restype = i32
+        lib.zig_launch_config_get.argtypes = [i32, i32, i32, i32, C.POINTER(LaunchConfig)]
+        lib.zig_launch_config_set.argtypes = [i32, i32, i32, i32, C.POINTER(LaunchConfig)]
+        lib.zig_autotune_candidates.argtypes = [i32, C.POINTER(LaunchConfig), C.c_uint32]
+        lib.zig_autotune_candidates.restype = C.c_uint32
+        lib.zig_autotune.argtypes = [i32, vp, vp, u64, u64, C.c_uint32, i32, vp, vp, C.c_size_t,
+                                     C.c_uint32, C.POINTER(LaunchConfig), C.POINTER(C.c_float), vp]
+        for name in ("zig_launch_config_get", "zig_launch_config_set", "zig_autotune"):
             getattr(lib, name).restype = i32
         lib.zig_device_status.argtypes = [i32, i32]
         lib.zig_status_string.argtypes = [i32]
@@ -202,6 +220,47 @@ def zig_mutate_batch(requests, prng: str = "splitmix64", desc=None, stream=None)
     st = load().zig_mutate_batch(arr, n, PRNG[prng], desc.data_ptr(), desc.numel(),
                                  _stream_ptr(stream))
     _check(st, "zig_mutate_batch")
+
+
+def zig_launch_config_get(prng: str, dtype: str, variable_lengths: bool, device: int = 0) -> dict:
+    c = LaunchConfig()
+    _check(load().zig_launch_config_get(device, PRNG[prng], DTYPE[dtype], int(bool(variable_lengths)),
+                                        C.byref(c)), "zig_launch_config_get")
+    return c.as_dict()
+
+
+def zig_launch_config_set(prng: str, dtype: str, variable_lengths: bool, cfg=None,
+                          device: int = 0) -> None:
+    """cfg: a dict with block, batch and store_bytes, or None for the default."""
+    ptr = None
+    if cfg is not None:
+        ptr = C.byref(LaunchConfig(int(cfg["block"]), int(cfg["batch"]), int(cfg["store_bytes"]), 0))
+    _check(load().zig_launch_config_set(device, PRNG[prng], DTYPE[dtype], int(bool(variable_lengths)),
+                                        ptr), "zig_launch_config_set")
+
+
+def zig_autotune_candidates(dtype: str) -> list:
+    lib = load()
+    n = int(lib.zig_autotune_candidates(DTYPE[dtype], None, 0))
+    arr = (LaunchConfig * n)()
+    lib.zig_autotune_candidates(DTYPE[dtype], arr, n)
+    return [c.as_dict() for c in arr]
+
+
+def zig_autotune(prng: str, seeds, out, lengths=None, uniform_len: int = 0, chunk_log2: int = 0,
+                 dtype: str = "f64", reps: int = 3, workspace=None, stream=None):
+    """Time every candidate on this request, record the fastest; returns (config, ms per call)."""
+    best, ms = LaunchConfig(), C.c_float()
+    ws_ptr, ws_bytes = (0, 0)
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    st = load().zig_autotune(PRNG[prng], seeds.data_ptr(),
+                             lengths.data_ptr() if lengths is not None else None, int(uniform_len),
+                             int(seeds.numel()), int(chunk_log2), DTYPE[dtype], out.data_ptr() or None,
+                             ws_ptr or None, ws_bytes, int(reps), C.byref(best), C.byref(ms),
+                             _stream_ptr(stream))
+    _check(st, "zig_autotune")
+    return best.as_dict(), float(ms.value)
 
 
 def zig_prng_fill(prng: str, seeds, n: int, out, skip: int = 0, kind: str = "u32",

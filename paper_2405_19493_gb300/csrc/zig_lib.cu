@@ -66,6 +66,7 @@ struct GenArgs {
     uint64_t mut_seed;         // mutation only: row p is seeded mut_seed + p
     const struct MutDesc* reqs;  // batched mutation: request descriptors
     uint32_t n_req;              // batched mutation: number of requests
+    uint32_t vec_store;          // generation: 1 = 16-byte vector stores at the flush
 };
 
 // One mutation request of a batch (device copy; ustart = its first unit).
@@ -526,12 +527,14 @@ struct RowInfo {
     uint32_t pad[3];
 };
 
-// Batch width: 32 slots per lane with 4-byte staging words, 16 with 8-byte words.
+// Batch width (candidates per lane per batch): by default 32 slots with 4-byte
+// staging words and 16 with 8-byte words (a 2 KB stage per warp); half that is
+// the other choice a launch configuration can make.
 template <int DT> struct ZBatch { static constexpr int B = (DT == ZIG_F64) ? 16 : 32; };
 
-template <class G, int DT>
+template <class G, int DT, int BW>
 struct ZWarp {
-    static constexpr int B = ZBatch<DT>::B;
+    static constexpr int B = BW;
     using S = typename ZStage<DT>::T;
     S stage[32 * B];
     uint8_t dd[32][B];                    // raw steps before a deferred wedge's uniform
@@ -540,19 +543,99 @@ struct ZWarp {
     RowInfo rowinfo[32];
 };
 
+// Slot (row, col) of a B-wide stage, swizzled so that the 32 lanes writing
+// column col of their own rows, and the lanes of a row reading it, hit distinct banks.
 template <int B, typename S>
-__device__ __forceinline__ int zslot(int row, int col) {   // bank-conflict-free swizzle
+__device__ __forceinline__ int zslot(int row, int col) {
+    static_assert(B == 32 || B == 16 || (B == 8 && sizeof(S) == 8), "unsupported batch width");
     if constexpr (B == 32) return row * 32 + (col ^ row);              // 4-byte words
+    else if constexpr (B == 8) return row * 8 + (col ^ ((row >> 1) & 7));
     else if constexpr (sizeof(S) == 8) return row * 16 + (col ^ (row & 15));
     else return row * 16 + (col ^ ((row >> 1) & 15));
 }
 
-constexpr int kZBlock = 768;              // 24 warps; one block per SM
-constexpr int kZWarps = kZBlock / 32;
+constexpr int kZBlock = 768;              // the default block: 24 warps, one block per SM
+constexpr int kZWarps = kZBlock / 32;     // the most warps a block may have
 
-template <class G, int DT>
+template <class G, int DT, int BW = ZBatch<DT>::B>
 __host__ __device__ constexpr size_t z128_warp_bytes() {
-    return (sizeof(ZWarp<G, DT>) + 15) & ~(size_t)15;
+    return (sizeof(ZWarp<G, DT, BW>) + 15) & ~(size_t)15;
+}
+
+// Phase C with 16-byte stores: each row's accepted values go out as the aligned
+// 16-byte vectors that cover them (T lanes per row, one vector per lane; a
+// vector that the row only partly covers is written element by element).
+// Writes exactly what the element-wide flush writes.
+template <typename OutT, typename S>
+__device__ __forceinline__ uint32_t z128_out_bits(S z) {
+    if constexpr (sizeof(OutT) == 8) return 0u;   // unused
+    else if constexpr (sizeof(OutT) == 4) return (uint32_t)z;
+    else return (uint32_t)f32_to_bf16_bits(__uint_as_float((uint32_t)z));
+}
+
+template <int B, typename S, typename OutT>
+__device__ __forceinline__ void z128_flush_vec(const S* stage, const RowInfo* rowinfo, int lane) {
+    constexpr int ESZ = (int)sizeof(OutT);
+    constexpr int V = 16 / ESZ;                         // elements per vector
+    constexpr int NV = B * ESZ / 16 + 1;                // vectors a row can touch
+    constexpr int T = NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32;   // lanes per row
+    constexpr int R = 32 / T;                           // rows per step
+    static_assert(NV <= T, "a row's vectors exceed its lanes");
+    const int sub = lane / T, c = lane % T;
+#pragma unroll 2
+    for (int k = 0; k < 32 / R; ++k) {
+        const int row = R * k + sub;
+        const RowInfo ri = rowinfo[row];
+        const uintptr_t base = (uintptr_t)ri.dst;
+        const int ab = (int)(base & 15) / ESZ;          // row elements before the first boundary
+        const int e0 = c * V - ab;                      // row index of this vector's first element
+        if (e0 >= ri.cnt || e0 + V <= 0) continue;
+        // slot of element max(e0, 0): skip the rejected slots at or below it
+        const int ef = e0 > 0 ? e0 : 0;
+        int src = ef;
+        for (uint32_t m = ri.rej; m; m &= m - 1) {
+            if (__ffs(m) - 1 <= src) ++src;
+            else break;
+        }
+        S val[V];
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+            const int e = e0 + t;
+            val[t] = 0;
+            if (e >= ef && e < ri.cnt) {
+                val[t] = stage[zslot<B, S>(row, src)];
+                ++src;
+                while ((ri.rej >> src) & 1u) ++src;
+            }
+        }
+        OutT* first = (OutT*)(base - (uintptr_t)(ab * ESZ)) + c * V;   // 16-byte aligned
+        if (e0 >= 0 && e0 + V <= ri.cnt) {
+            uint4 q;
+            if constexpr (ESZ == 8) {
+                q = make_uint4((uint32_t)val[0], (uint32_t)((uint64_t)val[0] >> 32), (uint32_t)val[1],
+                               (uint32_t)((uint64_t)val[1] >> 32));
+            } else if constexpr (ESZ == 4) {
+                q = make_uint4((uint32_t)val[0], (uint32_t)val[1], (uint32_t)val[2], (uint32_t)val[3]);
+            } else {
+                uint32_t h[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) h[t] = z128_out_bits<OutT, S>(val[t]);
+                q = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                               h[6] | (h[7] << 16));
+            }
+            __stcs((uint4*)first, q);
+        } else {
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                const int e = e0 + t;
+                if (e >= 0 && e < ri.cnt) {
+                    if constexpr (ESZ == 8) __stcs((unsigned long long*)first + t, (unsigned long long)val[t]);
+                    else if constexpr (ESZ == 4) __stcs((unsigned int*)first + t, (unsigned int)val[t]);
+                    else __stcs((unsigned short*)first + t, (unsigned short)z128_out_bits<OutT, S>(val[t]));
+                }
+            }
+        }
+    }
 }
 
 // Resolve a slow draw (j >= k[i]) of slot v.  A wedge is deferred to phase B
@@ -560,8 +643,8 @@ __host__ __device__ constexpr size_t z128_warp_bytes() {
 // unless the batch's step count has outgrown 8 bits (a batch normally takes
 // about B + 2 steps); a tail is decided here and a rejected tail draws again for
 // the same slot.  Returns the slot's word.
-template <class G, int DT>
-__device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab& t, ZWarp<G, DT>& ws,
+template <class G, int DT, class W>
+__device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab& t, W& ws,
                                                              int lane, int v, uint32_t i, uint32_t j,
                                                              uint32_t neg, uint32_t& drel, uint32_t& smask) {
     using S = typename ZStage<DT>::T;
@@ -596,12 +679,14 @@ __device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab&
 
 // MODE 0: generation into a.out; MODE 1: mutation x += sigma * z (binary32);
 // MODE 2: a batch of mutation requests (a.reqs), each row with its own sigma.
-template <int PRNG, int DT, int MODE>
+// BW is the batch width; the block may have any whole number of warps up to
+// kZWarps, each with its own z128_warp_bytes of dynamic shared memory.
+template <int PRNG, int DT, int MODE, int BW = ZBatch<DT>::B>
 __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
     using G = typename GenOf<PRNG>::T;
     using S = typename ZStage<DT>::T;
     using OutT = typename OutOf<DT>::T;
-    using W = ZWarp<G, DT>;
+    using W = ZWarp<G, DT, BW>;
     constexpr int B = W::B;
     __shared__ Z128Tab t;
     extern __shared__ __align__(16) unsigned char z128_dsm[];
@@ -610,7 +695,8 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    W& ws = *(W*)(z128_dsm + (size_t)wib * z128_warp_bytes<G, DT>());
+    const int n_warps = blockDim.x >> 5;
+    W& ws = *(W*)(z128_dsm + (size_t)wib * z128_warp_bytes<G, DT, BW>());
     if (MODE == 0 && a.out == nullptr) {   // only legal when every length is zero
         if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0)
             atomicOr(&d_err, kErrNullOutput);
@@ -618,8 +704,8 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
     }
     const uint64_t n_units = units_total(a);
     const uint64_t n_groups = (n_units + 31) >> 5;
-    const uint64_t warp_id = (uint64_t)blockIdx.x * kZWarps + wib;
-    const uint64_t warp_stride = (uint64_t)gridDim.x * kZWarps;
+    const uint64_t warp_id = (uint64_t)blockIdx.x * n_warps + wib;
+    const uint64_t warp_stride = (uint64_t)gridDim.x * n_warps;
     OutT* out = (OutT*)a.out;
 
     for (uint64_t grp = warp_id; grp < n_groups; grp += warp_stride) {
@@ -746,8 +832,10 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             ws.rowinfo[lane].rej = rj;
             ws.rowinfo[lane].sigma = sigma;
             __syncwarp();
-            {
-                constexpr int kLanesPerRow = (B == 32) ? 32 : 16;
+            if (MODE == 0 && a.vec_store) {
+                z128_flush_vec<B, S, OutT>(ws.stage, ws.rowinfo, lane);
+            } else {
+                constexpr int kLanesPerRow = B;
                 constexpr int kRowsPerStep = 32 / kLanesPerRow;
                 const int sub = lane / kLanesPerRow, c = lane % kLanesPerRow;
 #pragma unroll 4
@@ -963,12 +1051,12 @@ static zig_status current_device(int& dev) {
 typedef void (*GenFn)(GenArgs);
 
 template <int ALG, int PRNG>
-static GenFn pick_dt(int dt) {
+static GenFn pick_dt(int dt, bool half_batch) {
     if constexpr (ALG == ZIG_ZIG128) {
         switch (dt) {
-        case ZIG_F64: return z128_kernel<PRNG, ZIG_F64, 0>;
-        case ZIG_F32: return z128_kernel<PRNG, ZIG_F32, 0>;
-        default: return z128_kernel<PRNG, ZIG_BF16, 0>;
+        case ZIG_F64: return half_batch ? z128_kernel<PRNG, ZIG_F64, 0, 8> : z128_kernel<PRNG, ZIG_F64, 0>;
+        case ZIG_F32: return half_batch ? z128_kernel<PRNG, ZIG_F32, 0, 16> : z128_kernel<PRNG, ZIG_F32, 0>;
+        default: return half_batch ? z128_kernel<PRNG, ZIG_BF16, 0, 16> : z128_kernel<PRNG, ZIG_BF16, 0>;
         }
     } else {
         switch (dt) {
@@ -979,25 +1067,25 @@ static GenFn pick_dt(int dt) {
     }
 }
 template <int ALG>
-static GenFn pick_prng(int prng, int dt) {
+static GenFn pick_prng(int prng, int dt, bool half_batch) {
     switch (prng) {
-    case ZIG_LCG48: return pick_dt<ALG, 0>(dt);
-    case ZIG_SPLITMIX64: return pick_dt<ALG, 1>(dt);
-    default: return pick_dt<ALG, 2>(dt);
+    case ZIG_LCG48: return pick_dt<ALG, 0>(dt, half_batch);
+    case ZIG_SPLITMIX64: return pick_dt<ALG, 1>(dt, half_batch);
+    default: return pick_dt<ALG, 2>(dt, half_batch);
     }
 }
-static GenFn pick(int alg, int prng, int dt) {
+static GenFn pick(int alg, int prng, int dt, bool half_batch = false) {
     switch (alg) {
-    case ZIG_ZIG128: return pick_prng<ZIG_ZIG128>(prng, dt);
-    case ZIG_POLAR: return pick_prng<ZIG_POLAR>(prng, dt);
-    default: return pick_prng<ZIG_ZIG256>(prng, dt);
+    case ZIG_ZIG128: return pick_prng<ZIG_ZIG128>(prng, dt, half_batch);
+    case ZIG_POLAR: return pick_prng<ZIG_POLAR>(prng, dt, false);
+    default: return pick_prng<ZIG_ZIG256>(prng, dt, false);
     }
 }
 
 // Dynamic shared memory a kernel needs (0 for the kernels that use static only).
 // Every instantiation must fit one SM's shared memory (227 KB per block).
 template <class G, int DT>
-constexpr bool z128_fits() {
+constexpr bool z128_fits() {   // the default batch width is the larger one
     return z128_warp_bytes<G, DT>() * kZWarps + sizeof(Z128Tab) <= 227 * 1024;
 }
 static_assert(z128_fits<GenLcg48, ZIG_F64>() && z128_fits<GenLcg48, ZIG_F32>() &&
@@ -1006,17 +1094,44 @@ static_assert(z128_fits<GenLcg48, ZIG_F64>() && z128_fits<GenLcg48, ZIG_F32>() &
               "z128_kernel shared memory exceeds 227 KB per block");
 
 template <class G>
-static size_t z128_dyn_for(int dt) {
-    return (dt == ZIG_F64 ? z128_warp_bytes<G, ZIG_F64>() : z128_warp_bytes<G, ZIG_F32>()) * kZWarps;
+static size_t z128_dyn_for(int dt, bool half_batch, int warps) {
+    const size_t per = dt == ZIG_F64 ? (half_batch ? z128_warp_bytes<G, ZIG_F64, 8>() : z128_warp_bytes<G, ZIG_F64>())
+                                     : (half_batch ? z128_warp_bytes<G, ZIG_F32, 16>() : z128_warp_bytes<G, ZIG_F32>());
+    return per * (size_t)warps;
 }
 
-static size_t dyn_smem_of(int alg, int dt, int prng) {
+static size_t dyn_smem_of(int alg, int dt, int prng, bool half_batch = false, int block = kZBlock) {
     if (alg != ZIG_ZIG128) return 0;
-    return prng == ZIG_LCG48 ? z128_dyn_for<GenLcg48>(dt)
-         : prng == ZIG_SPLITMIX64 ? z128_dyn_for<GenSplitMix64>(dt) : z128_dyn_for<GenL64X128Mix>(dt);
+    const int warps = block / 32;
+    return prng == ZIG_LCG48 ? z128_dyn_for<GenLcg48>(dt, half_batch, warps)
+         : prng == ZIG_SPLITMIX64 ? z128_dyn_for<GenSplitMix64>(dt, half_batch, warps)
+                                  : z128_dyn_for<GenL64X128Mix>(dt, half_batch, warps);
 }
 
-static int block_of(int alg) { return alg == ZIG_ZIG128 ? kZBlock : kBlock; }
+// ---- launch configuration of the 128-level generation kernel ----
+// Per device, PRNG, output type and input form (uniform lengths or a lengths
+// array): threads per block, batch width and store width.  Any choice gives
+// the same outputs; zig_autotune times the candidates and keeps the fastest.
+struct LaunchCfg {
+    uint32_t block, batch, store_bytes;
+};
+static LaunchCfg g_cfg[kMaxDevices][3][3][2];
+static bool g_cfg_set[kMaxDevices][3][3][2];
+
+static uint32_t default_batch(int dt) { return dt == ZIG_F64 ? 16u : 32u; }
+static LaunchCfg default_cfg(int dt) { return LaunchCfg{(uint32_t)kZBlock, default_batch(dt), 0u}; }
+
+static bool cfg_valid(int dt, const LaunchCfg& c) {
+    const uint32_t b = default_batch(dt);
+    return c.block >= 64 && c.block <= (uint32_t)kZBlock && c.block % 32 == 0 &&
+           (c.batch == b || c.batch == b / 2) && (c.store_bytes == 0 || c.store_bytes == 16);
+}
+
+static LaunchCfg cfg_of(int dev, int prng, int dt, bool variable) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const int v = variable ? 1 : 0;
+    return g_cfg_set[dev][prng][dt][v] ? g_cfg[dev][prng][dt][v] : default_cfg(dt);
+}
 
 // Opt in to the dynamic shared memory a launch needs (static + dynamic may pass
 // the 48 KB default only with the attribute set).
@@ -1037,8 +1152,16 @@ static bool allow_dyn_smem(const void* fn, size_t bytes) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_facts_mu);
-    for (const LaunchFacts& f : g_facts)
-        if (f.fn == fn && f.dev == dev && f.dyn == bytes && f.block == -1) return true;
+    // one record per kernel and device (block = -1): the largest opt-in so far
+    for (LaunchFacts& f : g_facts) {
+        if (f.fn == fn && f.dev == dev && f.block == -1) {
+            if (bytes <= f.dyn) return true;
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+                return false;
+            f.dyn = bytes;
+            return true;
+        }
+    }
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return false;
     g_facts.push_back(LaunchFacts{fn, dev, bytes, -1, 0});
@@ -1064,6 +1187,23 @@ static int grid_for(const void* fn, int dev, uint64_t n_groups, size_t dyn = 0, 
     uint64_t need = (n_groups + warps - 1) / warps;
     if (need == 0) need = 1;
     return (int)std::min<uint64_t>(full, need);
+}
+
+// Launch the generation kernel of (alg, prng, dt) for the arguments in a, with
+// the configuration `force` or else the one recorded for this device.
+static zig_status launch_gen(int alg, int prng, int dt, int dev, bool variable, uint64_t n_groups_hint,
+                             GenArgs& a, cudaStream_t s, const LaunchCfg* force) {
+    const bool z128 = alg == ZIG_ZIG128;
+    const LaunchCfg c = force ? *force : z128 ? cfg_of(dev, prng, dt, variable) : default_cfg(dt);
+    const bool half = z128 && c.batch != default_batch(dt);
+    const int block = z128 ? (int)c.block : kBlock;
+    a.vec_store = (z128 && c.store_bytes == 16) ? 1u : 0u;
+    GenFn fn = pick(alg, prng, dt, half);
+    const size_t dyn = dyn_smem_of(alg, dt, prng, half, block);
+    if (!allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
+    const int grid = grid_for((const void*)fn, dev, n_groups_hint, dyn, block);
+    fn<<<grid, block, dyn, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
 }
 
 }  // namespace host
@@ -1098,10 +1238,14 @@ size_t zig_generate_workspace_bytes(uint64_t n_streams) {
     return (size_t)(16 * n_streams + 256);
 }
 
-zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
-                        const uint64_t* lengths_dev, uint64_t uniform_len, uint64_t n_streams,
-                        uint32_t chunk_log2, zig_dtype dtype, void* out_dev, void* workspace_dev,
-                        size_t workspace_bytes, void* stream) {
+}  // extern "C"
+
+namespace zig {
+namespace host {
+static zig_status generate_impl(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
+                                const uint64_t* lengths_dev, uint64_t uniform_len, uint64_t n_streams,
+                                uint32_t chunk_log2, zig_dtype dtype, void* out_dev, void* workspace_dev,
+                                size_t workspace_bytes, void* stream, const LaunchCfg* force) {
     if ((unsigned)prng > 2u || (unsigned)alg > 2u || (unsigned)dtype > 2u) return ZIG_ERR_INVALID_ARG;
     if (chunk_log2 != 0 && (chunk_log2 < 4 || chunk_log2 > 24)) return ZIG_ERR_INVALID_ARG;
     if (n_streams == 0) return ZIG_OK;
@@ -1159,13 +1303,112 @@ zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
         if (cudaGetLastError() != cudaSuccess) return ZIG_ERR_CUDA;
         n_groups_hint = ~0ull >> 8;   // unknown on the host: fill the device
     }
-    host::GenFn fn = host::pick(alg, prng, dtype);
-    const size_t dyn = host::dyn_smem_of(alg, dtype, prng);
-    if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
-    const int block = host::block_of(alg);
-    int grid = host::grid_for((const void*)fn, dev, n_groups_hint, dyn, block);
-    fn<<<grid, block, dyn, s>>>(a);
-    return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
+    return host::launch_gen(alg, prng, dtype, dev, lengths_dev != nullptr, n_groups_hint, a, s, force);
+}
+}  // namespace host
+}  // namespace zig
+
+extern "C" {
+
+zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
+                        const uint64_t* lengths_dev, uint64_t uniform_len, uint64_t n_streams,
+                        uint32_t chunk_log2, zig_dtype dtype, void* out_dev, void* workspace_dev,
+                        size_t workspace_bytes, void* stream) {
+    return host::generate_impl(prng, alg, seeds_dev, lengths_dev, uniform_len, n_streams, chunk_log2,
+                               dtype, out_dev, workspace_dev, workspace_bytes, stream, nullptr);
+}
+
+zig_status zig_launch_config_get(int device, zig_prng prng, zig_dtype dtype, int variable_lengths,
+                                 zig_launch_config* cfg) {
+    if (device < 0 || device >= host::kMaxDevices || (unsigned)prng > 2u || (unsigned)dtype > 2u || !cfg)
+        return ZIG_ERR_INVALID_ARG;
+    const host::LaunchCfg c = host::cfg_of(device, prng, dtype, variable_lengths != 0);
+    cfg->block = c.block;
+    cfg->batch = c.batch;
+    cfg->store_bytes = c.store_bytes;
+    cfg->reserved = 0;
+    return ZIG_OK;
+}
+
+zig_status zig_launch_config_set(int device, zig_prng prng, zig_dtype dtype, int variable_lengths,
+                                 const zig_launch_config* cfg) {
+    if (device < 0 || device >= host::kMaxDevices || (unsigned)prng > 2u || (unsigned)dtype > 2u)
+        return ZIG_ERR_INVALID_ARG;
+    const int v = variable_lengths ? 1 : 0;
+    std::lock_guard<std::mutex> lk(host::g_mu);
+    if (!cfg) {
+        host::g_cfg_set[device][prng][dtype][v] = false;
+        return ZIG_OK;
+    }
+    const host::LaunchCfg c{cfg->block, cfg->batch, cfg->store_bytes};
+    if (!host::cfg_valid(dtype, c)) return ZIG_ERR_INVALID_ARG;
+    host::g_cfg[device][prng][dtype][v] = c;
+    host::g_cfg_set[device][prng][dtype][v] = true;
+    return ZIG_OK;
+}
+
+uint32_t zig_autotune_candidates(zig_dtype dtype, zig_launch_config* cands, uint32_t max_cands) {
+    static const uint32_t blocks[] = {256, 384, 512, 768};
+    const uint32_t b = host::default_batch((unsigned)dtype > 2u ? ZIG_F64 : dtype);
+    uint32_t n = 0;
+    for (uint32_t bl : blocks)
+        for (uint32_t bw : {b / 2, b})
+            for (uint32_t sb : {0u, 16u}) {
+                if (cands && n < max_cands) cands[n] = zig_launch_config{bl, bw, sb, 0};
+                ++n;
+            }
+    return n;
+}
+
+zig_status zig_autotune(zig_prng prng, const uint64_t* seeds_dev, const uint64_t* lengths_dev,
+                        uint64_t uniform_len, uint64_t n_streams, uint32_t chunk_log2, zig_dtype dtype,
+                        void* out_dev, void* workspace_dev, size_t workspace_bytes, uint32_t reps,
+                        zig_launch_config* best, float* best_ms, void* stream) {
+    if ((unsigned)prng > 2u || (unsigned)dtype > 2u || reps == 0 || reps > 1000) return ZIG_ERR_INVALID_ARG;
+    int dev;
+    zig_status st = host::current_device(dev);
+    if (st != ZIG_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return ZIG_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return ZIG_ERR_INVALID_ARG;   // it synchronizes
+    zig_launch_config cands[64];
+    const uint32_t nc = zig_autotune_candidates(dtype, cands, 64);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return ZIG_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return ZIG_ERR_CUDA;
+    }
+    float best_t = -1.0f;
+    uint32_t best_k = 0;
+    for (uint32_t k = 0; k < nc && st == ZIG_OK; ++k) {
+        const host::LaunchCfg c{cands[k].block, cands[k].batch, cands[k].store_bytes};
+        // one untimed launch, then `reps` timed back to back on the caller's stream
+        for (uint32_t r = 0; r <= reps && st == ZIG_OK; ++r) {
+            if (r == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = ZIG_ERR_CUDA;
+            if (st == ZIG_OK)
+                st = host::generate_impl(prng, ZIG_ZIG128, seeds_dev, lengths_dev, uniform_len, n_streams,
+                                         chunk_log2, dtype, out_dev, workspace_dev, workspace_bytes, stream, &c);
+        }
+        float ms = 0.0f;
+        if (st == ZIG_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = ZIG_ERR_CUDA;
+        ms /= (float)reps;
+        if (st == ZIG_OK && (best_t < 0.0f || ms < best_t)) {
+            best_t = ms;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != ZIG_OK) return st;
+    st = zig_launch_config_set(dev, prng, dtype, lengths_dev != nullptr, &cands[best_k]);
+    if (st != ZIG_OK) return st;
+    if (best) *best = cands[best_k];
+    if (best_ms) *best_ms = best_t;
+    return ZIG_OK;
 }
 
 zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_t seed,
@@ -1364,11 +1607,5 @@ extern "C" zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uin
     scan_kernel<<<1, 1024, 0, s>>>(lengths_dev, n_streams, chunk_log2, (uint64_t*)a.offsets,
                                    (uint64_t*)a.ustart, (uint64_t*)a.totals);
     if (cudaGetLastError() != cudaSuccess) return ZIG_ERR_CUDA;
-    host::GenFn fn = host::pick(alg, prng, dtype);
-    const size_t dyn = host::dyn_smem_of(alg, dtype, prng);
-    if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
-    const int block = host::block_of(alg);
-    int grid = host::grid_for((const void*)fn, dev, ~0ull >> 8, dyn, block);
-    fn<<<grid, block, dyn, s>>>(a);
-    return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
+    return host::launch_gen(alg, prng, dtype, dev, true, ~0ull >> 8, a, s, nullptr);
 }

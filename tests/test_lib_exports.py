@@ -72,3 +72,30 @@ def test_host_side_argument_errors():
     assert lib.zig_mutate(8, float("nan"), 2, 5, 1, 0, None) == 1
     assert lib.zig_prng_fill(0, 8, 4, 4, 0, 5, 8, None) == 1
     assert Z.zig_generate_workspace_bytes(1000) >= 16 * 1000
+
+
+def test_launch_config_validation_and_candidates():
+    """Launch configurations: defaults, validation, set/reset; no CUDA call."""
+    for dt, b in (("f64", 16), ("f32", 32), ("bf16", 32)):
+        assert Z.zig_launch_config_get("splitmix64", dt, False, device=5) == \
+            {"block": 768, "batch": b, "store_bytes": 0}
+        cands = Z.zig_autotune_candidates(dt)
+        assert len(cands) == 16
+        assert {c["batch"] for c in cands} == {b // 2, b}
+        assert {c["block"] for c in cands} == {256, 384, 512, 768}
+        assert {c["store_bytes"] for c in cands} == {0, 16}
+        for bad in ({"block": 800, "batch": b, "store_bytes": 0},
+                    {"block": 100, "batch": b, "store_bytes": 0},
+                    {"block": 256, "batch": b * 2, "store_bytes": 0},
+                    {"block": 256, "batch": b, "store_bytes": 8}):
+            try:
+                Z.zig_launch_config_set("lcg48", dt, True, bad, device=5)
+                raise AssertionError(f"accepted {bad}")
+            except Z.ZigError as e:
+                assert e.status == 1
+    cfg = {"block": 384, "batch": 8, "store_bytes": 16}
+    Z.zig_launch_config_set("l64x128mix", "f64", True, cfg, device=5)
+    assert Z.zig_launch_config_get("l64x128mix", "f64", True, device=5) == cfg
+    assert Z.zig_launch_config_get("l64x128mix", "f64", False, device=5)["block"] == 768
+    Z.zig_launch_config_set("l64x128mix", "f64", True, None, device=5)
+    assert Z.zig_launch_config_get("l64x128mix", "f64", True, device=5)["batch"] == 16
