@@ -296,6 +296,8 @@ def run_gpu(args):
 
     # comparisons on the same seeds: other transforms and narrower outputs (rank 0 reports)
     line_extra["comparisons"] = compare_variants(Z, torch, seeds, stream, args)
+    if rank == 0 and not args.no_precision:
+        line_extra["precision"] = measure_precision(Z, torch, stream)
 
     # end to end through the public call: seeds from pinned host memory, result back to host
     e2e = measure_e2e(Z, torch, seeds_np, stream, args)
@@ -405,6 +407,42 @@ def compare_variants(Z, torch, seeds, stream, args):
     return res
 
 
+def measure_precision(Z, torch, stream, reps=3):
+    """2^31 variates in each output type from the same streams (2^21 x 1,024,
+    SplitMix64, 128-level ziggurat): rate, KS distance to Phi, tail mass beyond
+    |x| > 3, and the narrow outputs' error against the binary64 outputs of the
+    same streams (the binary64 path matches the oracle element by element in
+    the parity tests).  Statistics are computed on the device after timing."""
+    from paper_2405_19493_gb300 import quality as Q
+    from paper_2405_19493_gb300 import workloads as W
+    n_s, L = 1 << 21, 1024
+    n = n_s * L
+    sd = torch.from_numpy(W.seeds(n_s).view(np.int64)).cuda()
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+    res, z64 = {}, None
+    for dt in ("f64", "f32", "bf16"):
+        o = torch.empty(n, dtype=tdt[dt], device="cuda")
+        fn = lambda: Z.zig_generate("splitmix64", "zig128", sd, o, uniform_len=L, dtype=dt, stream=stream)
+        fn()
+        m = statistics.mean(time_launches(torch, stream, fn, reps))
+        r = {"variates_per_s": n / (m / 1e3), "ms_mean": m,
+             "write_gbs": n * o.element_size() / (m / 1e3) / 1e9,
+             "ks": Q.ks_grid(torch, o), "tail_beyond_3": Q.tail_mass(torch, o, dt)}
+        if dt == "bf16":
+            r["ks_exact_vs_rounded_normal"] = Q.ks_bf16_exact(torch, o)
+        if dt == "f64":
+            z64 = o
+        else:
+            r["error_vs_f64_output"] = Q.error_vs_f64(torch, o, z64, dt)
+            del o
+        res[dt] = r
+    del z64
+    torch.cuda.empty_cache()
+    return {"workload": "2^31 variates per dtype: 2^21 streams x 1,024, splitmix64, zig128, "
+                        "seeds 0x5EED+s; binary32 tables on the fast path of f32/bf16",
+            "dtypes": res}
+
+
 def measure_serving(Z, torch, rates=(1000, 10000, 50000), n_req=1500):
     """Gaussian-mutation requests, Poisson arrivals, through the native service.
 
@@ -507,6 +545,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--ncu-case", default=None,
                     help="run only alg:prng:dtype:n_streams:len[:chunk_log2] (for ncu)")
     ap.add_argument("--reps", type=int, default=2)
