@@ -134,7 +134,8 @@ def oracle_rate(n_streams: int, threads: int, seed_base: int = 0x5EED):
     parts = np.array_split(np.arange(n_streams), threads)
 
     def run(idx, prng):
-        O.generate(prng, "zig128", seeds[idx], uniform_len=PER_STREAM)
+        for a in range(0, len(idx), 4096):   # pieces of <= 4,096 streams (32 MiB of output)
+            O.generate(prng, "zig128", seeds[idx[a:a + 4096]], uniform_len=PER_STREAM)
 
     t0 = time.perf_counter()
     for prng in PRNGS:
@@ -148,15 +149,18 @@ def oracle_rate(n_streams: int, threads: int, seed_base: int = 0x5EED):
 
 
 def cpu_baseline():
+    """The oracle on the whole step's workload (3 x 2^30 variates: about 20 s of CPU
+    work), on every host core, plus a single-thread rate on 1/128 of it."""
     cores = os.cpu_count() or 1
-    n_all = 1 << 14       # 2^24 variates per generator across all cores
+    n_all = N_STREAMS
     rate_all, dt_all = oracle_rate(n_all, cores)
-    n_one = 1 << 11       # 2^21 variates per generator on one core
+    n_one = N_STREAMS >> 7
     rate_one, dt_one = oracle_rate(n_one, 1)
     return {"value": rate_all, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"{n_all} streams x 1,024 per generator (1/64 of the workload) on "
-                       f"{cores} threads in {dt_all:.2f} s; single thread {rate_one:.3e} "
-                       f"variates/s on {n_one} streams x 1,024 per generator")}
+            "sample": (f"the whole step: {n_all} streams x 1,024 per generator on {cores} "
+                       f"threads in {dt_all:.2f} s ({dt_all * cores:.1f} thread-s); single "
+                       f"thread {rate_one:.3e} variates/s on {n_one} streams x 1,024 per "
+                       f"generator in {dt_one:.2f} s")}
 
 
 def run_reference(args):
@@ -443,7 +447,8 @@ def measure_precision(Z, torch, stream, reps=3):
             "dtypes": res}
 
 
-def measure_serving(Z, torch, rates=(1000, 10000, 50000), n_req=1500):
+def measure_serving(Z, torch, rates=(1000, 10000, 50000), n_req=1500, mixed_rate=10000,
+                    mixed_generate_frac=0.5):
     """Gaussian-mutation requests, Poisson arrivals, through the native service.
 
     Populations live in one device arena (48 GB) handed out as a ring; the service
@@ -457,8 +462,10 @@ def measure_serving(Z, torch, rates=(1000, 10000, 50000), n_req=1500):
     arena = torch.empty(arena_bytes // 4, dtype=torch.float32, device="cuda")
     base = arena.data_ptr()
     out = {}
-    for rate in rates:
-        reqs = W.mutation_requests(n_req, rate_hz=rate, seed=11 + rate)
+    runs = [(f"{rate}_req_per_s", rate, 0.0) for rate in rates]
+    runs.append((f"mixed_{mixed_rate}_req_per_s", mixed_rate, mixed_generate_frac))
+    for label, rate, gfrac in runs:
+        reqs = W.mutation_requests(n_req, rate_hz=rate, seed=11 + rate, generate_frac=gfrac)
         offs, pos = [], 0
         for r in reqs:
             nb = r["P"] * r["L"] * 4
@@ -472,7 +479,8 @@ def measure_serving(Z, torch, rates=(1000, 10000, 50000), n_req=1500):
             srv.drain()
             st = srv.stats()
         span_s = st["span_us"] / 1e6
-        out[f"{rate}_req_per_s"] = {
+        out[label] = {
+            "generate_requests": sum(r["kind"] == "generate" for r in reqs),
             "requests": st["completed"], "latency_p50_ms": st["latency_p50_us"] / 1e3,
             "latency_p99_ms": st["latency_p99_us"] / 1e3,
             "throughput_req_per_s": st["completed"] / span_s if span_s else None,
@@ -484,7 +492,9 @@ def measure_serving(Z, torch, rates=(1000, 10000, 50000), n_req=1500):
     return {"workload": ("x += sigma*N(0,1) on float32 P x L populations, P log-uniform 16..4096, "
                          "L log-uniform 8..100,000, sigma U[0.01,1], per-request seed, Poisson "
                          f"arrivals, {n_req} requests per rate, 40 GB admission budget, 4 stream "
-                         "slots, up to 64 requests per launch"), "rates": out}
+                         "slots, up to 64 requests per launch; the mixed line turns about "
+                         f"{mixed_generate_frac:.0%} of the requests into x = N(0,1) generation "
+                         "requests"), "rates": out}
 
 
 def measure_e2e(Z, torch, seeds_np, stream, args):

@@ -231,12 +231,20 @@ zig_status zig_autotune(zig_prng prng, const uint64_t *seeds_dev, const uint64_t
 zig_status zig_mutate(float *x_dev, float sigma, uint64_t P, uint64_t L, uint64_t seed,
                       zig_prng prng, void *stream);
 
-/* One request of a mutation batch: x_dev (P x L binary32, device) += sigma * N(0,1),
- * rows seeded seed + p, exactly as zig_mutate. */
+/* Request kinds of a batch (zig_mutation.kind). */
+#define ZIG_REQ_MUTATE 0u   /* x_dev += sigma * N(0,1), exactly as zig_mutate */
+#define ZIG_REQ_GENERATE 1u /* x_dev = N(0,1) (sigma ignored): row p equals
+                               zig_generate(prng, ZIG_ZIG128, seeds = {seed + p},
+                               uniform_len = L, chunk_log2 = 10, ZIG_F32) */
+
+/* One request of a batch on a P x L binary32 row-major device buffer x_dev,
+ * rows seeded seed + p.  kind is ZIG_REQ_MUTATE (the zero default) or
+ * ZIG_REQ_GENERATE. */
 typedef struct {
     float *x_dev;
     uint64_t P, L;
     float sigma;
+    uint32_t kind;
     uint64_t seed;
 } zig_mutation;
 
@@ -253,8 +261,9 @@ zig_status zig_mutate_batch(const zig_mutation *reqs_host, uint32_t n_req, zig_p
                             void *desc_dev, size_t desc_bytes, void *stream);
 
 /*
- * Continuous-batching service for mutation requests (serving form of Sec. 1's
- * workload).  A worker thread admits submitted requests in arrival order while
+ * Continuous-batching service for mutation and generation requests (serving
+ * form of Sec. 1's workload); both kinds share the queue, the budget and the
+ * batched launches.  A worker thread admits submitted requests in arrival order while
  * the bytes of the populations in flight stay within budget_bytes, packs up to
  * max_batch of them into one zig_mutate_batch launch on one of n_slots streams,
  * and retires a launch when its CUDA event completes; requests that arrive
@@ -290,6 +299,10 @@ zig_status zig_server_create(int device, zig_prng prng, uint64_t budget_bytes, u
                              uint32_t max_batch, zig_server **out);
 zig_status zig_server_submit(zig_server *server, float *x_dev, uint64_t P, uint64_t L, float sigma,
                              uint64_t seed, uint64_t *ticket);
+/* A generation request (ZIG_REQ_GENERATE) into out_dev, P x L binary32; admitted,
+ * batched and reported like mutation requests (the same tickets and queue). */
+zig_status zig_server_submit_generate(zig_server *server, float *out_dev, uint64_t P, uint64_t L,
+                                      uint64_t seed, uint64_t *ticket);
 zig_status zig_server_wait(zig_server *server, uint64_t ticket, double timeout_s);
 zig_status zig_server_query(zig_server *server, uint64_t ticket, int *state, double *latency_us,
                             double *queue_us);

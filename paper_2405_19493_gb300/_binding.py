@@ -34,15 +34,18 @@ EXPORTS = (
     "zig_mutate", "zig_prng_fill", "zig_device_status", "zig_status_string", "zig_version",
     "zig_generate_noalloc", "zig_mutate_batch_desc_bytes", "zig_mutate_batch",
     "zig_server_create", "zig_server_submit", "zig_server_wait", "zig_server_query",
-    "zig_server_drain", "zig_server_stats", "zig_server_destroy",
+    "zig_server_drain", "zig_server_stats", "zig_server_destroy", "zig_server_submit_generate",
     "zig_launch_config_get", "zig_launch_config_set", "zig_autotune_candidates", "zig_autotune",
 )
 
 
+REQ_KIND = {"mutate": 0, "generate": 1}   # ZIG_REQ_MUTATE, ZIG_REQ_GENERATE
+
+
 class Mutation(C.Structure):
-    """zig_mutation: one request of a mutation batch."""
+    """zig_mutation: one request of a batch (kind: ZIG_REQ_MUTATE or ZIG_REQ_GENERATE)."""
     _fields_ = [("x_dev", C.c_void_p), ("P", C.c_uint64), ("L", C.c_uint64),
-                ("sigma", C.c_float), ("seed", C.c_uint64)]
+                ("sigma", C.c_float), ("kind", C.c_uint32), ("seed", C.c_uint64)]
 
 
 class LaunchConfig(C.Structure):
@@ -109,13 +112,15 @@ def load(build_if_missing: bool = True):
         lib.zig_mutate_batch.argtypes = [C.POINTER(Mutation), C.c_uint32, i32, vp, C.c_size_t, vp]
         lib.zig_server_create.argtypes = [i32, i32, u64, C.c_uint32, C.c_uint32, C.POINTER(vp)]
         lib.zig_server_submit.argtypes = [vp, vp, u64, u64, C.c_float, u64, C.POINTER(u64)]
+        lib.zig_server_submit_generate.argtypes = [vp, vp, u64, u64, u64, C.POINTER(u64)]
         lib.zig_server_wait.argtypes = [vp, u64, C.c_double]
         lib.zig_server_query.argtypes = [vp, u64, C.POINTER(i32), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]
         lib.zig_server_drain.argtypes = [vp, C.c_double]
         lib.zig_server_stats.argtypes = [vp, C.POINTER(ServingStats)]
         lib.zig_server_destroy.argtypes = [vp]
-        for name in ("zig_mutate_batch", "zig_server_create", "zig_server_submit", "zig_server_wait",
+        for name in ("zig_mutate_batch", "zig_server_create", "zig_server_submit",
+                     "zig_server_submit_generate", "zig_server_wait",
                      "zig_server_query", "zig_server_drain", "zig_server_stats",
                      "zig_server_destroy"):
             getattr(lib, name).restype = i32
@@ -207,13 +212,17 @@ def zig_mutate(x, sigma: float, P: int, L: int, seed: int, prng: str = "splitmix
 
 
 def zig_mutate_batch(requests, prng: str = "splitmix64", desc=None, stream=None) -> None:
-    """requests: list of (x, sigma, seed) with x a P x L float32 CUDA tensor."""
+    """requests: list of (x, sigma, seed) or (x, sigma, seed, kind) with x a P x L float32
+    CUDA tensor and kind "mutate" (x += sigma z, the default) or "generate" (x = z)."""
     import torch
     n = len(requests)
     arr = (Mutation * max(n, 1))()
-    for k, (x, sigma, seed) in enumerate(requests):
+    for k, req in enumerate(requests):
+        x, sigma, seed = req[:3]
+        kind = REQ_KIND[req[3]] if len(req) > 3 else 0
         P, L = (x.shape[0], x.shape[1]) if x.dim() == 2 else (1, x.numel())
-        arr[k] = Mutation(x.data_ptr() or None, P, L, float(sigma), int(seed) & (2 ** 64 - 1))
+        arr[k] = Mutation(x.data_ptr() or None, P, L, float(sigma or 0.0), kind,
+                          int(seed) & (2 ** 64 - 1))
     need = int(load().zig_mutate_batch_desc_bytes(n))
     if desc is None:
         desc = torch.empty(need, dtype=torch.uint8, device="cuda")

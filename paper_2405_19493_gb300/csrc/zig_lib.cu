@@ -74,7 +74,7 @@ struct MutDesc {
     float* x;
     uint64_t P, L, seed, upr, ustart;
     float sigma;
-    uint32_t pad;
+    uint32_t kind;   // ZIG_REQ_MUTATE: x += sigma z; ZIG_REQ_GENERATE: x = z
 };
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
@@ -524,7 +524,8 @@ struct RowInfo {
     int cnt;
     uint32_t rej;
     float sigma;       // mutation
-    uint32_t pad[3];
+    uint32_t kind;     // batched requests: ZIG_REQ_MUTATE or ZIG_REQ_GENERATE
+    uint32_t pad[2];
 };
 
 // Batch width (candidates per lane per batch): by default 32 slots with 4-byte
@@ -715,6 +716,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
         G g;
         g.seed(0);
         float sigma = a.sigma;
+        uint32_t kind = ZIG_REQ_MUTATE;
         if (u < n_units) {
             if constexpr (MODE == 2) {
                 // batched mutation: the request holding unit u (the last with ustart <= u)
@@ -731,6 +733,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                 rem = umin64(r.L - t0, 1024);
                 dst = (OutT*)(r.x + p * r.L + t0);
                 sigma = r.sigma;
+                kind = r.kind;
             } else {
                 uint64_t s, qd, off, n;
                 unit_info(a, u, s, qd, off, n);
@@ -831,6 +834,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             ws.rowinfo[lane].cnt = acc;
             ws.rowinfo[lane].rej = rj;
             ws.rowinfo[lane].sigma = sigma;
+            ws.rowinfo[lane].kind = kind;
             __syncwarp();
             if (MODE == 0 && a.vec_store) {
                 z128_flush_vec<B, S, OutT>(ws.stage, ws.rowinfo, lane);
@@ -852,7 +856,9 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                         OutT* rd = (OutT*)ri.dst;
                         // write-once output: global streaming stores (evict-first)
                         if constexpr (MODE != 0) {
-                            ((float*)rd)[c] = fmaf(ri.sigma, __uint_as_float((uint32_t)z), ((float*)rd)[c]);
+                            const float zf = __uint_as_float((uint32_t)z);
+                            if (MODE == 2 && ri.kind == ZIG_REQ_GENERATE) ((float*)rd)[c] = zf;
+                            else ((float*)rd)[c] = fmaf(ri.sigma, zf, ((float*)rd)[c]);
                         } else if constexpr (DT == ZIG_F64) {
                             __stcs((unsigned long long*)rd + c, (unsigned long long)z);
                         } else if constexpr (DT == ZIG_F32) {
@@ -1458,7 +1464,8 @@ zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_p
     uint64_t units = 0;
     for (uint32_t r = 0; r < n_req; ++r) {
         const zig_mutation& q = reqs_host[r];
-        if (!std::isfinite(q.sigma) || (q.P && q.L && (!q.x_dev || ((uintptr_t)q.x_dev) % 4)) ||
+        if (q.kind > ZIG_REQ_GENERATE || (q.kind == ZIG_REQ_MUTATE && !std::isfinite(q.sigma)) ||
+            (q.P && q.L && (!q.x_dev || ((uintptr_t)q.x_dev) % 4)) ||
             q.L > (1ull << 40) || (q.L && q.P > (1ull << 40) / q.L))
             return ZIG_ERR_INVALID_ARG;
         d[r].x = q.x_dev;
@@ -1468,7 +1475,7 @@ zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_p
         d[r].sigma = q.sigma;
         d[r].upr = q.L ? (q.L + 1023) >> 10 : 1;
         d[r].ustart = units;
-        d[r].pad = 0;
+        d[r].kind = q.kind;
         units += (q.P && q.L) ? q.P * d[r].upr : 0;
     }
     if (units == 0) return ZIG_OK;

@@ -1,8 +1,9 @@
 // Continuous-batching service for Gaussian-mutation requests (the paper's
-// motivating workload, Sec. 1: Gaussian mutation in an evolutionary algorithm).
+// motivating workload, Sec. 1: Gaussian mutation in an evolutionary algorithm)
+// and generation requests.
 //
-// Requests x += sigma * N(0,1) on device-resident binary32 populations arrive
-// at any time.  A worker thread admits them in arrival order while the bytes of
+// Requests x += sigma * N(0,1) on device-resident binary32 populations, or
+// x = N(0,1) into device buffers, arrive at any time.  A worker thread admits them in arrival order while the bytes of
 // the populations in flight stay within the budget, packs up to max_batch
 // admitted requests into one launch of zig_mutate_batch on a free stream slot,
 // and retires a slot when its CUDA event completes.  Requests that arrive while
@@ -219,16 +220,19 @@ zig_status zig_server_create(int device, zig_prng prng, uint64_t budget_bytes, u
     return ZIG_OK;
 }
 
-zig_status zig_server_submit(zig_server* S, float* x_dev, uint64_t P, uint64_t L, float sigma,
-                             uint64_t seed, uint64_t* ticket) {
-    if (!S || !ticket || !std::isfinite(sigma) || (P && L && !x_dev) ||
+}  // extern "C"
+
+namespace {
+zig_status submit(zig_server* S, float* x_dev, uint64_t P, uint64_t L, float sigma, uint32_t kind,
+                  uint64_t seed, uint64_t* ticket) {
+    if (!S || !ticket || (kind == ZIG_REQ_MUTATE && !std::isfinite(sigma)) || (P && L && !x_dev) ||
         (L && P > (1ull << 40) / L))
         return ZIG_ERR_INVALID_ARG;
     const uint64_t bytes = P * L * sizeof(float);
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stop) return ZIG_ERR_INVALID_ARG;
     Req r;
-    r.m = zig_mutation{x_dev, P, L, sigma, seed};
+    r.m = zig_mutation{x_dev, P, L, sigma, kind, seed};
     r.bytes = bytes;
     r.t_submit = now_us();
     r.t_launch = r.t_done = 0;
@@ -246,6 +250,19 @@ zig_status zig_server_submit(zig_server* S, float* x_dev, uint64_t P, uint64_t L
     S->queue.push_back(*ticket);
     S->cv_work.notify_one();
     return ZIG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+zig_status zig_server_submit(zig_server* S, float* x_dev, uint64_t P, uint64_t L, float sigma,
+                             uint64_t seed, uint64_t* ticket) {
+    return submit(S, x_dev, P, L, sigma, ZIG_REQ_MUTATE, seed, ticket);
+}
+
+zig_status zig_server_submit_generate(zig_server* S, float* out_dev, uint64_t P, uint64_t L,
+                                      uint64_t seed, uint64_t* ticket) {
+    return submit(S, out_dev, P, L, 0.0f, ZIG_REQ_GENERATE, seed, ticket);
 }
 
 zig_status zig_server_wait(zig_server* S, uint64_t ticket, double timeout_s) {

@@ -10,7 +10,8 @@ These are measurements of the library's outputs, not part of generation:
     rounding alone keeps near density x half a bfloat16 spacing.
   - tail_mass: the fraction of |x| > t against P(|RN_dtype(Z)| > t).
   - error_vs_f64: each narrow output against the binary64 output of the same
-    streams, in units of the narrow type's ulp at the binary64 value.
+    streams: how many representable steps it lies from the nearest value
+    RN_dtype(z64), and its distance from z64 in the narrow type's ulps.
 """
 
 from __future__ import annotations
@@ -95,22 +96,38 @@ def tail_mass(torch, x, dtype: str, t: float = 3.0, chunk: int = CHUNK) -> dict:
             "z_score": (obs - expect) / sd}
 
 
+def round_to_precision(torch, z64, p: int):
+    """RN-even of binary64 values to p significand bits, by integer arithmetic on
+    the bits (one rounding; normal results assumed), returned as binary64."""
+    k = 53 - p
+    b = z64.contiguous().view(torch.int64)
+    r = ((b + ((1 << (k - 1)) - 1) + ((b >> k) & 1)) >> k) << k
+    return r.view(torch.float64)
+
+
 def error_vs_f64(torch, x, z64, dtype: str, chunk: int = CHUNK) -> dict:
-    """x (f32 or bf16) against z64, the binary64 outputs of the same streams."""
+    """x (f32 or bf16) against z64, the binary64 outputs of the same streams:
+    steps (adjacent values) from RN_dtype(z64), and distance from z64 in ulps."""
     p = MANT_BITS[dtype]
+    ity = torch.int32 if dtype == "f32" else torch.int16
     n = x.numel()
-    worst, not_nearest, total_abs, max_rel = 0.0, 0, 0.0, 0.0
+    worst, not_nearest, total_abs, max_rel, max_steps = 0.0, 0, 0.0, 0.0, 0
     for a in range(0, n, chunk):
         r = z64[a:a + chunk]
-        d = (x[a:a + chunk].double() - r).abs()
+        xc = x[a:a + chunk]
+        rn = round_to_precision(torch, r, p).to(x.dtype)      # exact: representable
+        steps = (xc.view(ity).int() - rn.view(ity).int()).abs()
+        max_steps = max(max_steps, int(steps.max().item()))
+        not_nearest += int((steps != 0).sum().item())
+        d = (xc.double() - r).abs()
         nz = r != 0
         _, e = torch.frexp(r)                        # |r| in [2^(e-1), 2^e)
         ulp = torch.exp2((e - p).to(torch.float64))
         u = torch.where(nz, d / ulp, torch.zeros_like(d))
         worst = max(worst, float(u.max().item()))
-        not_nearest += int((u > 0.5).sum().item())
         total_abs += float(d.sum().item())
         rel = torch.where(nz, d / r.abs(), torch.zeros_like(d))
         max_rel = max(max_rel, float(rel.max().item()))
-    return {"max_err_ulp": worst, "outputs_not_nearest": not_nearest,
+    return {"max_steps_from_nearest": max_steps, "max_err_ulp": worst,
+            "outputs_not_nearest": not_nearest, "frac_not_nearest": not_nearest / max(n, 1),
             "mean_abs_err": total_abs / n, "max_rel_err": max_rel}

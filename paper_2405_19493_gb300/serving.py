@@ -14,7 +14,7 @@ from . import _binding as B
 
 
 class MutationServer:
-    """Continuous-batching service for x += sigma * N(0,1) requests.
+    """Continuous-batching service for x += sigma * N(0,1) and x = N(0,1) requests.
 
     device < 0 runs the scheduler with simulated launches (no GPU needed).
     """
@@ -42,6 +42,22 @@ class MutationServer:
         B._check(st, "zig_server_submit")
         if x is not None:
             self._keep[t.value] = x
+        return t.value
+
+    def submit_generate(self, out, seed: int, P: int | None = None, L: int | None = None,
+                        out_ptr: int | None = None) -> int:
+        """Enqueue out = N(0,1) (P x L float32 CUDA tensor, or a raw pointer + P, L)."""
+        if out is not None:
+            P, L = (out.shape[0], out.shape[1]) if out.dim() == 2 else (1, out.numel())
+            ptr = out.data_ptr() or None
+        else:
+            ptr = out_ptr
+        t = C.c_uint64()
+        st = self._lib.zig_server_submit_generate(self._h, ptr, int(P), int(L),
+                                                  int(seed) & (2 ** 64 - 1), C.byref(t))
+        B._check(st, "zig_server_submit_generate")
+        if out is not None:
+            self._keep[t.value] = out
         return t.value
 
     def wait(self, ticket: int, timeout_s: float = -1.0) -> None:
@@ -88,6 +104,10 @@ def drive_poisson(server: MutationServer, requests, ptr_of, clock=time.perf_coun
     for k, r in enumerate(requests):
         while clock() - t0 < r["arrival"]:
             pass
-        tickets.append(server.submit(None, r["sigma"], r["seed"], P=r["P"], L=r["L"],
-                                     x_ptr=ptr_of(k, r)))
+        if r.get("kind", "mutate") == "generate":
+            tickets.append(server.submit_generate(None, r["seed"], P=r["P"], L=r["L"],
+                                                  out_ptr=ptr_of(k, r)))
+        else:
+            tickets.append(server.submit(None, r["sigma"], r["seed"], P=r["P"], L=r["L"],
+                                         x_ptr=ptr_of(k, r)))
     return tickets

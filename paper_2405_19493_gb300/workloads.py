@@ -33,8 +33,10 @@ def log_uniform_int(rng, lo: int, hi: int, size=None):
 
 
 def mutation_requests(n: int, rate_hz: float, seed: int = 11, p_range=(16, 4096),
-                      l_range=(8, 100_000), max_elems: int | None = None):
-    """n mutation requests: dicts with P, L, sigma, seed, arrival (seconds)."""
+                      l_range=(8, 100_000), max_elems: int | None = None,
+                      generate_frac: float = 0.0):
+    """n requests: dicts with P, L, sigma, seed, arrival (seconds) and kind
+    ("mutate", or "generate" for about generate_frac of them)."""
     rng = np.random.default_rng(seed)
     P = log_uniform_int(rng, *p_range, size=n)
     L = log_uniform_int(rng, *l_range, size=n)
@@ -44,5 +46,7 @@ def mutation_requests(n: int, rate_hz: float, seed: int = 11, p_range=(16, 4096)
     sigma = rng.uniform(0.01, 1.0, size=n)
     rseed = rng.integers(0, 2 ** 63, size=n, dtype=np.int64)
     arrival = np.cumsum(rng.exponential(1.0 / rate_hz, size=n))
+    gen = rng.random(n) < generate_frac if generate_frac > 0 else np.zeros(n, dtype=bool)
     return [dict(P=int(P[k]), L=int(L[k]), sigma=float(sigma[k]), seed=int(rseed[k]),
-                 arrival=float(arrival[k])) for k in range(n)]
+                 arrival=float(arrival[k]), kind="generate" if gen[k] else "mutate")
+            for k in range(n)]

@@ -55,3 +55,24 @@ def test_dry_run_fifo_under_memory_pressure():
         q = [srv.query(t)["queue_us"] for t in tickets]
         assert all(q[k] <= q[k + 1] + 1e-6 for k in range(5))
         assert all(srv.query(t)["latency_us"] > 0 for t in tickets)
+
+
+def test_dry_run_generate_and_mutate_share_queue_and_budget():
+    budget = 16 << 20
+    with MutationServer(device=-1, budget_bytes=budget, n_slots=2, max_batch=4) as srv:
+        t = []
+        for k in range(12):
+            if k % 3 == 0:
+                t.append(srv.submit_generate(None, k, P=32, L=32768, out_ptr=FAKE))   # 4 MiB
+            else:
+                t.append(srv.submit(None, 0.2, k, P=32, L=32768, x_ptr=FAKE))
+        # a generation request ignores sigma, so it needs none; the budget still applies
+        with pytest.raises(B.ZigError) as e:
+            srv.submit_generate(None, 99, P=4096, L=4096, out_ptr=FAKE)          # 64 MiB
+        assert e.value.status == 4
+        srv.drain(timeout_s=30)
+        st = srv.stats()
+        assert st["completed"] == 12 and st["failed"] == 1
+        assert st["elements"] == 12 * 32 * 32768
+        assert st["peak_inflight_bytes"] <= budget
+        assert all(srv.query(k)["state"] == 2 for k in t)
