@@ -96,20 +96,6 @@ struct GenLcg48 {
         c = 0;
         s = (nd == 1) ? ((kA2 * s + kC2) & kMask48) : ((kA4 * s + kC4) & kMask48);
     }
-    // Batch-start state and the snapshot of a uniform d raw steps later (for
-    // deciding a deferred wedge without keeping a per-record snapshot).
-    struct Saved { uint64_t s; };
-    __device__ __forceinline__ Saved save() const { return Saved{s}; }
-    static __device__ __forceinline__ uint64_t snap_at(const Saved& st, uint32_t d, const JumpTab* jt) {
-        uint64_t t = st.s;
-        while (d) {
-            const int b = __ffs(d) - 1;
-            t = (jt->lcg48_A[b] * t + jt->lcg48_C[b]) & kMask48;
-            d &= d - 1;
-        }
-        return t;   // the state before the uniform's two steps
-    }
-    __device__ __forceinline__ void skip_double() { s = (kA2 * s + kC2) & kMask48; }
     static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t, int k) {
         uint64_t t = k ? ((kA2 * b + kC2) & kMask48) : b;
         t = (t * kLcgA + kLcgC) & kMask48;
@@ -136,12 +122,6 @@ struct GenSplitMix64 {
     static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t, int k) {
         return mix64(k ? b + kGamma : b) >> 11;
     }
-    struct Saved { uint64_t s; };
-    __device__ __forceinline__ Saved save() const { return Saved{s}; }
-    static __device__ __forceinline__ uint64_t snap_at(const Saved& st, uint32_t d, const JumpTab*) {
-        return st.s + (uint64_t)(d + 1) * kGamma;   // the state of the uniform's own step
-    }
-    __device__ __forceinline__ void skip_double() { s += kGamma; }
 };
 
 struct GenL64X128Mix {
@@ -181,15 +161,6 @@ struct GenL64X128Mix {
     static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t c, int k) {
         return mix_lea64(k ? c : b) >> 11;
     }
-    struct Saved { uint64_t a, s, x0, x1; };
-    __device__ __forceinline__ Saved save() const { return Saved{a, s, x0, x1}; }
-    static __device__ __forceinline__ uint64_t snap_at(const Saved& st, uint32_t d, const JumpTab*) {
-        GenL64X128Mix t;
-        t.a = st.a; t.s = st.s; t.x0 = st.x0; t.x1 = st.x1;
-        for (uint32_t k = 0; k < d; ++k) t.advance();   // replay d steps
-        return t.s + t.x0;                              // the uniform's mix input
-    }
-    __device__ __forceinline__ void skip_double() { advance(); }
     __device__ void jump(uint64_t n, const JumpTab* jt) {
         while (n) {
             int b = __ffsll((long long)n) - 1;
@@ -222,31 +193,6 @@ template <> struct GenOf<2> { using T = GenL64X128Mix; };
 
 __device__ __forceinline__ double m53_to_double(uint64_t m) {
     return (double)m * 0x1p-53;   // exact: m < 2^53
-}
-
-// ---------------------------------------------------------------------------
-// exact binary64 product RN(j * w) with w = M * 2^(E - 1075), M in [2^52, 2^53)
-// ---------------------------------------------------------------------------
-// j < 2^24.  Normalise j to jn = j << lz (bit 31 set); the 85-bit product
-// P' = jn * M = T * 2^32 + lo has T in [2^51, 2^53).  Keep the top 53 bits q,
-// round to nearest even on the remaining bits, and assemble the exponent by
-// hand: the result is q * 2^(32 - s - lz + E - 1075), s = 1 when T < 2^52.
-// Adding q (hidden bit included) to (exponent - 1) << 52 carries correctly when
-// rounding produces q = 2^53.  Bit-identical to IEEE RN-even j * w.
-__device__ __forceinline__ uint64_t mul_j_w_bits(uint32_t j, uint64_t M, int E) {
-    if (j == 0) return 0ull;
-    int lz = __clz((int)j);
-    uint32_t jn = j << lz;
-    uint64_t A = (uint64_t)jn * (uint32_t)M;
-    uint64_t B = (uint64_t)jn * (uint32_t)(M >> 32);
-    uint64_t T = B + (A >> 32);
-    uint32_t lo = (uint32_t)A;
-    uint32_t s = (uint32_t)(T >> 52) ^ 1u;
-    uint64_t q = (T << s) | ((uint64_t)lo >> (32 - s));
-    uint32_t rem = lo << s;
-    uint32_t up = (uint32_t)(rem > 0x80000000u) | ((uint32_t)(rem == 0x80000000u) & (uint32_t)q);
-    q += up;
-    return ((uint64_t)(E + 31 - (int)s - lz) << 52) + q;
 }
 
 // RN-even binary64 -> bfloat16 bits (finite, normal-range inputs).

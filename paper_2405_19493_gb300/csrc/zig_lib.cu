@@ -30,7 +30,6 @@ namespace zig {
 // device-resident immutable tables (filled by zig_tables_init)
 // ---------------------------------------------------------------------------
 __device__ uint32_t d_z128_kE[128];   // K[i] | (E(w[i]) - 900) << 24
-__device__ uint64_t d_z128_M[128];    // 53-bit significand of w[i], hidden bit set
 __device__ double d_z128_W[128];
 __device__ double d_z128_Y[128];
 __device__ float d_z128_W32[128];
@@ -66,7 +65,7 @@ struct GenArgs {
     uint64_t mut_seed;         // mutation only: row p is seeded mut_seed + p
     const struct MutDesc* reqs;  // batched mutation: request descriptors
     uint32_t n_req;              // batched mutation: number of requests
-    uint32_t vec_store;          // generation: 1 = 16-byte vector stores at the flush
+    uint32_t lane_sectors;       // generation: 1 = lane-per-row flush in 32-byte sectors
 };
 
 // One mutation request of a batch (device copy; ustart = its first unit).
@@ -332,24 +331,26 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
 // 128-level ziggurat (GSL form): one launch per bulk request
 // ---------------------------------------------------------------------------
 // Each lane owns one unit (stream or chunk) with its generator in registers.
-// A warp works in batches of up to 16 outputs per lane:
-//  A. the lanes draw candidates in lockstep, two per step.
+// A warp works in batches of B candidates per lane (B = 16 for binary64, 32
+// otherwise, or half that by launch configuration), staged in shared memory:
+//  A. the lanes draw their candidates in lockstep; one warp vote per candidate
+//     guards the rare slow draws.
 //     - fast path (j < k[i]): x = RN(j * w[i]) on the spot.  For binary64 this
 //       is one fused multiply-add, fma(2^52 + j, w, -2^52 w) = RN(j w) exactly
-//       (2^52 + j is built from j's bits; -2^52 w from w's bits), on GB300's
-//       narrow binary64 pipe; every fourth slot uses the same product in
-//       integer arithmetic instead, to balance that pipe against the integer
-//       pipes.  binary32/bfloat16 use fl32(j * w32[i]).
-//     - wedge (i < 127): the slot keeps RN(j w[i]), which is the output if the
-//       wedge test accepts; a 16-byte record (i, j, sign, row, slot, and a
-//       snapshot from which the test's uniform is rebuilt) goes to the warp's
-//       ring and the generator moves past that uniform at once.
+//       (2^52 + j is built from j's bits; -2^52 w from w's bits); GB300's
+//       narrow binary64 pipe keeps up with one per candidate, and the same
+//       product in integer arithmetic costs far more issue slots.
+//       binary32/bfloat16 use fl32(j * w32[i]).
+//     - wedge (i < 127): deferred.  The slot keeps j | i << 24 | negative << 31,
+//       the generator writes an 8-byte record from which the test's uniform is
+//       rebuilt (G::snap) and moves past that uniform at once.  A lane holds up
+//       to kZRec records per batch; a further wedge is decided on the spot.
 //     - tail (i = 127, j >= k[127]; 0.06 % of draws): decided in the lane.
-//  B. whenever 32 records wait (and at the end of the batch) the 32 lanes test
-//     32 wedges together in binary32 with a proven margin (binary64 only inside
-//     it) and flag the rejected slots.
-//  C. the rows are written two per warp store, skipping rejected slots; the
-//     stream continues in the next batch.
+//  B. at the end of the batch the warp's deferred wedges are tested 32 at a
+//     time, in binary32 with a proven margin (binary64 only inside it); an
+//     accepted slot gets RN(j w[i]), a rejected one is flagged.
+//  C. the rows are written with B lanes per row, skipping rejected slots; the
+//     unit continues in the next batch.
 // The outputs of a unit are its accepted candidates in draw order: exactly the
 // sequence a one-variate-at-a-time loop produces.
 
@@ -381,30 +382,6 @@ __device__ __forceinline__ void z128tab_load(Z128Tab& t) {
     }
 }
 
-// RN(j * w) as binary64 bits, j < 2^24, w a normal binary64 with bits (wh:wl):
-// integer arithmetic, no branch, j = 0 gives +0.  Normalise j (bit 31 set), take
-// the 85-bit product with the 53-bit significand, keep 53 bits, round to nearest
-// even, and assemble the exponent.
-__device__ __forceinline__ uint64_t mul_j_w_int(uint32_t j, uint32_t wh, uint32_t wl) {
-    const uint32_t ml = wl, mh = (wh & 0xFFFFFu) | 0x100000u;
-    const uint32_t lz = __clz((int)j);                 // 8..31; 32 for j = 0
-    const uint32_t jn = j << (lz & 31);
-    const uint64_t A = (uint64_t)jn * ml;
-    const uint64_t B = (uint64_t)jn * mh;
-    const uint64_t T = B + (A >> 32);
-    const uint32_t lo = (uint32_t)A;
-    const uint32_t Tl = (uint32_t)T, Th = (uint32_t)(T >> 32);
-    const bool s = Th < (1u << 20);                    // T < 2^52: shift one more bit in
-    const uint32_t qh = s ? __funnelshift_l(Tl, Th, 1) : Th;
-    const uint32_t ql = s ? __funnelshift_l(lo, Tl, 1) : Tl;
-    const uint32_t rem = s ? (lo << 1) : lo;
-    const uint32_t up = (uint32_t)(rem > 0x80000000u) | ((uint32_t)(rem == 0x80000000u) & ql);
-    const uint64_t q = (((uint64_t)qh << 32) | ql) + (up & 1u);
-    const uint32_t ex = (wh >> 20) + 31u - (uint32_t)s - lz;   // biased exponent - 1
-    const uint64_t bits = ((uint64_t)ex << 52) + q;
-    return j ? bits : 0ull;
-}
-
 // RN(j * w) with one binary64 fma: (2^52 + j) * w - 2^52 * w = j * w exactly
 // before the single rounding.  2^52 + j and -2^52 * w are built from bits.
 __device__ __forceinline__ uint64_t mul_j_w_fma(uint32_t j, double w) {
@@ -425,11 +402,8 @@ template <> struct Z128Out<ZIG_F64> {
     using T = double;
     using Pair = double2;
     static __device__ __forceinline__ double fast(const Z128Tab& t, uint32_t i, uint32_t j,
-                                                  uint32_t neg, int lane, bool use_int) {
-        const double w = t.W[i][lane & 15];
-        uint64_t b;
-        if (use_int) b = mul_j_w_int(j, (uint32_t)__double2hiint(w), (uint32_t)__double2loint(w));
-        else b = mul_j_w_fma(j, w);
+                                                  uint32_t neg, int lane) {
+        const uint64_t b = mul_j_w_fma(j, t.W[i][lane & 15]);
         return __longlong_as_double((long long)(b | ((uint64_t)neg << 63)));
     }
     static __device__ __forceinline__ double from64(double x, uint32_t neg) {
@@ -440,7 +414,7 @@ template <> struct Z128Out<ZIG_F32> {
     using T = float;
     using Pair = float2;
     static __device__ __forceinline__ float fast(const Z128Tab& t, uint32_t i, uint32_t j,
-                                                 uint32_t neg, int, bool) {
+                                                 uint32_t neg, int) {
         return __uint_as_float(__float_as_uint(__fmul_rn((float)j, t.W32[i])) | (neg << 31));
     }
     static __device__ __forceinline__ float from64(double x, uint32_t neg) {
@@ -505,11 +479,11 @@ template <> struct ZStage<ZIG_F64> { using T = uint64_t; };
 
 template <int DT>
 __device__ __forceinline__ typename ZStage<DT>::T z128_value(const Z128Tab& t, uint32_t i, uint32_t j,
-                                                              uint32_t neg, int lane, bool use_int) {
+                                                              uint32_t neg, int lane) {
     if constexpr (DT == ZIG_F64) {
-        return (uint64_t)__double_as_longlong(Z128Out<ZIG_F64>::fast(t, i, j, neg, lane, use_int));
+        return (uint64_t)__double_as_longlong(Z128Out<ZIG_F64>::fast(t, i, j, neg, lane));
     } else {
-        return __float_as_uint(Z128Out<ZIG_F32>::fast(t, i, j, neg, lane, false));
+        return __float_as_uint(Z128Out<ZIG_F32>::fast(t, i, j, neg, lane));
     }
 }
 
@@ -519,29 +493,31 @@ __device__ __forceinline__ typename ZStage<DT>::T z128_from64(double x, uint32_t
     else return __float_as_uint(Z128Out<ZIG_F32>::from64(x, neg));
 }
 
-struct RowInfo {
-    unsigned long long dst;
-    int cnt;
-    uint32_t rej;
-    float sigma;       // mutation
-    uint32_t kind;     // batched requests: ZIG_REQ_MUTATE or ZIG_REQ_GENERATE
-    uint32_t pad[2];
-};
 
 // Batch width (candidates per lane per batch): by default 32 slots with 4-byte
 // staging words and 16 with 8-byte words (a 2 KB stage per warp); half that is
 // the other choice a launch configuration can make.
 template <int DT> struct ZBatch { static constexpr int B = (DT == ZIG_F64) ? 16 : 32; };
 
+// Deferred wedges a lane may hold per batch (one 8-byte record each); a lane's
+// next wedge in the same batch is decided on the spot.  With 2.7 % wedges a
+// lane defers more than 4 of its 16 (32) candidates in about 6e-5 (3e-3) of
+// its batches.
+constexpr int kZRec = 4;
+
 template <class G, int DT, int BW>
 struct ZWarp {
     static constexpr int B = BW;
     using S = typename ZStage<DT>::T;
+    using OutT = typename OutOf<DT>::T;
+    static constexpr int EPS = 32 / (int)sizeof(OutT);   // output elements per 32-byte sector
+    // carry row width: at least EPS - 1 values, with a stride that spreads the
+    // 32 lanes' rows over distinct banks
+    static constexpr int CW = sizeof(S) == 8 ? 5 : (EPS == 8 ? 9 : 17);
     S stage[32 * B];
-    uint8_t dd[32][B];                    // raw steps before a deferred wedge's uniform
-    typename G::Saved saved[32];          // each lane's generator at the batch start
+    S carry[32 * CW];                     // values a lane has not written yet (lane-per-row flush)
+    uint64_t rec[32][kZRec];              // each deferred wedge's uniform record (G::snap)
     uint32_t smask[32], rej[32], excl[32];
-    RowInfo rowinfo[32];
 };
 
 // Slot (row, col) of a B-wide stage, swizzled so that the 32 lanes writing
@@ -563,87 +539,98 @@ __host__ __device__ constexpr size_t z128_warp_bytes() {
     return (sizeof(ZWarp<G, DT, BW>) + 15) & ~(size_t)15;
 }
 
-// Phase C with 16-byte stores: each row's accepted values go out as the aligned
-// 16-byte vectors that cover them (T lanes per row, one vector per lane; a
-// vector that the row only partly covers is written element by element).
-// Writes exactly what the element-wide flush writes.
+// Phase C, lane-per-row form: each lane writes its own row's accepted values,
+// in output order, as whole 32-byte sectors (one 256-bit store each), after the
+// values it carried over from its previous batch.  What does not fill a sector
+// is carried to the lane's next batch; element stores remain only before the
+// first sector boundary of a unit and at the unit's end.  (A GB300 writes
+// per-lane full sectors at nearly the rate of coalesced warp stores, but
+// partial-sector stores from many lanes at a fraction of it.)
 template <typename OutT, typename S>
-__device__ __forceinline__ uint32_t z128_out_bits(S z) {
-    if constexpr (sizeof(OutT) == 8) return 0u;   // unused
-    else if constexpr (sizeof(OutT) == 4) return (uint32_t)z;
-    else return (uint32_t)f32_to_bf16_bits(__uint_as_float((uint32_t)z));
+__device__ __forceinline__ void z128_store1(OutT* p, S z) {
+    if constexpr (sizeof(OutT) == 8) __stcs((unsigned long long*)p, (unsigned long long)z);
+    else if constexpr (sizeof(OutT) == 4) __stcs((unsigned int*)p, (unsigned int)z);
+    else __stcs((unsigned short*)p, f32_to_bf16_bits(__uint_as_float((uint32_t)z)));
 }
 
-template <int B, typename S, typename OutT>
-__device__ __forceinline__ void z128_flush_vec(const S* stage, const RowInfo* rowinfo, int lane) {
-    constexpr int ESZ = (int)sizeof(OutT);
-    constexpr int V = 16 / ESZ;                         // elements per vector
-    constexpr int NV = B * ESZ / 16 + 1;                // vectors a row can touch
-    constexpr int T = NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32;   // lanes per row
-    constexpr int R = 32 / T;                           // rows per step
-    static_assert(NV <= T, "a row's vectors exceed its lanes");
-    const int sub = lane / T, c = lane % T;
-#pragma unroll 2
-    for (int k = 0; k < 32 / R; ++k) {
-        const int row = R * k + sub;
-        const RowInfo ri = rowinfo[row];
-        const uintptr_t base = (uintptr_t)ri.dst;
-        const int ab = (int)(base & 15) / ESZ;          // row elements before the first boundary
-        const int e0 = c * V - ab;                      // row index of this vector's first element
-        if (e0 >= ri.cnt || e0 + V <= 0) continue;
-        // slot of element max(e0, 0): skip the rejected slots at or below it
-        const int ef = e0 > 0 ? e0 : 0;
-        int src = ef;
-        for (uint32_t m = ri.rej; m; m &= m - 1) {
-            if (__ffs(m) - 1 <= src) ++src;
-            else break;
-        }
-        S val[V];
+template <typename OutT, typename S, int EPS>
+__device__ __forceinline__ void z128_store_sector(OutT* p, const S (&v)[EPS]) {
+    uint64_t q[4];
+    if constexpr (sizeof(OutT) == 8) {
 #pragma unroll
-        for (int t = 0; t < V; ++t) {
-            const int e = e0 + t;
-            val[t] = 0;
-            if (e >= ef && e < ri.cnt) {
-                val[t] = stage[zslot<B, S>(row, src)];
-                ++src;
-                while ((ri.rej >> src) & 1u) ++src;
-            }
-        }
-        OutT* first = (OutT*)(base - (uintptr_t)(ab * ESZ)) + c * V;   // 16-byte aligned
-        if (e0 >= 0 && e0 + V <= ri.cnt) {
-            uint4 q;
-            if constexpr (ESZ == 8) {
-                q = make_uint4((uint32_t)val[0], (uint32_t)((uint64_t)val[0] >> 32), (uint32_t)val[1],
-                               (uint32_t)((uint64_t)val[1] >> 32));
-            } else if constexpr (ESZ == 4) {
-                q = make_uint4((uint32_t)val[0], (uint32_t)val[1], (uint32_t)val[2], (uint32_t)val[3]);
-            } else {
-                uint32_t h[8];
+        for (int k = 0; k < 4; ++k) q[k] = (uint64_t)v[k];
+    } else if constexpr (sizeof(OutT) == 4) {
 #pragma unroll
-                for (int t = 0; t < 8; ++t) h[t] = z128_out_bits<OutT, S>(val[t]);
-                q = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
-                               h[6] | (h[7] << 16));
-            }
-            __stcs((uint4*)first, q);
-        } else {
+        for (int k = 0; k < 4; ++k) q[k] = (uint64_t)(uint32_t)v[2 * k] | ((uint64_t)(uint32_t)v[2 * k + 1] << 32);
+    } else {
 #pragma unroll
-            for (int t = 0; t < V; ++t) {
-                const int e = e0 + t;
-                if (e >= 0 && e < ri.cnt) {
-                    if constexpr (ESZ == 8) __stcs((unsigned long long*)first + t, (unsigned long long)val[t]);
-                    else if constexpr (ESZ == 4) __stcs((unsigned int*)first + t, (unsigned int)val[t]);
-                    else __stcs((unsigned short*)first + t, (unsigned short)z128_out_bits<OutT, S>(val[t]));
-                }
-            }
+        for (int k = 0; k < 4; ++k) {
+            uint64_t w = 0;
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+                w |= (uint64_t)f32_to_bf16_bits(__uint_as_float((uint32_t)v[4 * k + h])) << (16 * h);
+            q[k] = w;
         }
     }
+    asm volatile("st.global.cs.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(q[0]), "l"(q[1]), "l"(q[2]),
+                 "l"(q[3])
+                 : "memory");
+}
+
+// Writes the lane's nc carried values (carry[0..nc)) and the row's accepted
+// slots (the `produced` slots minus the rejected ones in rj) from dst on.
+// Advances dst past what was written and leaves the rest in carry / nc, or
+// writes everything when the unit ends with this batch.
+template <int B, int EPS, int CW, typename S, typename OutT>
+__device__ __forceinline__ void z128_flush_lane(const S* stage, S* carry, int lane, uint32_t rj, int n_acc,
+                                                bool unit_end, OutT*& dst, int& nc) {
+    constexpr int ESZ = (int)sizeof(OutT);
+    const int total = nc + n_acc;
+    const int mis = (int)(((uintptr_t)dst & 31) / ESZ);   // nonzero only at a unit's start
+    const int h = umin64(mis ? EPS - mis : 0, total);       // elements before the first boundary
+    const int body = (total - h) / EPS;                     // whole sectors
+    const int tail = total - h - body * EPS;
+    S* const cr = carry + lane * CW;
+    int e = 0;                                              // next element, in output order
+    int src = 0;                                            // next stage slot to read
+    while (((uint64_t)rj >> src) & 1u) ++src;
+    auto next = [&]() -> S {
+        S z;
+        if (e < nc) {
+            z = cr[e];
+        } else {
+            z = stage[zslot<B, S>(lane, src)];
+            ++src;
+            while (((uint64_t)rj >> src) & 1u) ++src;
+        }
+        ++e;
+        return z;
+    };
+    for (int k = 0; k < h; ++k) z128_store1<OutT, S>(dst + k, next());
+    OutT* p = dst + h;
+    for (int q = 0; q < body; ++q) {
+        S v[EPS];
+#pragma unroll
+        for (int k = 0; k < EPS; ++k) v[k] = next();
+        z128_store_sector<OutT, S, EPS>(p, v);
+        p += EPS;
+    }
+    // the remainder: written if the unit ends, else carried (position k <= e:
+    // a carried value is never overwritten before it is read)
+    for (int k = 0; k < tail; ++k) {
+        const S z = next();
+        if (unit_end) z128_store1<OutT, S>(p + k, z);
+        else cr[k] = z;
+    }
+    dst = unit_end ? p + tail : p;
+    nc = unit_end ? 0 : tail;
 }
 
 // Resolve a slow draw (j >= k[i]) of slot v.  A wedge is deferred to phase B
-// (its slot keeps j | i << 24 | negative << 31 and its step count goes to dd)
-// unless the batch's step count has outgrown 8 bits (a batch normally takes
-// about B + 2 steps); a tail is decided here and a rejected tail draws again for
-// the same slot.  Returns the slot's word.
+// (its slot keeps j | i << 24 | negative << 31 and the generator's record of
+// the test's uniform goes to rec) unless the lane already holds kZRec records
+// in this batch; a tail, or a wedge that is not deferred, is decided here, and
+// a rejected one draws again for the same slot.  Returns the slot's word.
 template <class G, int DT, class W>
 __device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab& t, W& ws,
                                                              int lane, int v, uint32_t i, uint32_t j,
@@ -651,16 +638,18 @@ __device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab&
     using S = typename ZStage<DT>::T;
     for (;;) {
         if (i < 127) {
-            if (drel <= 0xFFu) {
-                ws.dd[lane][v] = (uint8_t)drel;
-                g.skip_double();
+            const int nw = __popc(smask);
+            if (nw < kZRec) {
+                uint64_t b, c;
+                g.snap(1, b, c);   // record the uniform and move past it
+                ws.rec[lane][nw] = b;
                 drel += G::kStepsPerDouble;
                 smask |= 1u << v;
                 return (S)(j | (i << 24) | (neg << 31));
             }
             const uint64_t mu = g.next_m53();
             drel += G::kStepsPerDouble;
-            if (z128_wedge_accept(t, i, j, mu)) return z128_value<DT>(t, i, j, neg, lane, false);
+            if (z128_wedge_accept(t, i, j, mu)) return z128_value<DT>(t, i, j, neg, lane);
         } else {
             const uint64_t m1 = g.next_m53();
             const uint64_t m2 = g.next_m53();
@@ -674,7 +663,7 @@ __device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab&
         i = w & 0x7Fu;
         neg = (~w >> 7) & 1u;
         j = w >> 8;
-        if (j < t.K[i][lane]) return z128_value<DT>(t, i, j, neg, lane, false);
+        if (j < t.K[i][lane]) return z128_value<DT>(t, i, j, neg, lane);
     }
 }
 
@@ -744,10 +733,10 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             }
         }
         uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
+        int nc = 0;           // values carried to the next batch (lane-per-row flush)
         const bool check_chunk = (MODE == 2 || a.chunk_log2 != 0) && rem != 0;
 
         while (__any_sync(kFull, rem > 0)) {
-            ws.saved[lane] = g.save();
             ws.rej[lane] = 0;
             uint32_t drel = 0, smask = 0;
             int produced;
@@ -763,7 +752,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                     const uint32_t i = w & 0x7Fu;
                     const uint32_t neg = (~w >> 7) & 1u;   // bit 7 set -> positive
                     const uint32_t j = w >> 8;
-                    S val = z128_value<DT>(t, i, j, neg, lane, (v & 3) == 3);
+                    S val = z128_value<DT>(t, i, j, neg, lane);
                     const bool slow = j >= t.K[i][lane];
                     if (__any_sync(kFull, slow)) {
                         if (slow) val = z128_slow<G, DT>(g, t, ws, lane, v, i, j, neg, drel, smask);
@@ -783,7 +772,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                         const uint32_t i = w & 0x7Fu;
                         const uint32_t neg = (~w >> 7) & 1u;
                         const uint32_t j = w >> 8;
-                        S val = z128_value<DT>(t, i, j, neg, lane, false);
+                        S val = z128_value<DT>(t, i, j, neg, lane);
                         if (j >= t.K[i][lane]) val = z128_slow<G, DT>(g, t, ws, lane, v, i, j, neg, drel, smask);
                         ws.stage[zslot<B, S>(lane, v)] = val;
                         produced = v + 1;
@@ -813,14 +802,14 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
 #pragma unroll
                         for (int step = 16; step; step >>= 1)
                             if (ws.excl[o + step] <= (uint32_t)r) o += step;
+                        const int kr = r - (int)ws.excl[o];   // the row's kr-th deferred wedge
                         uint32_t m = ws.smask[o];
-                        for (int k = r - (int)ws.excl[o]; k > 0; --k) m &= m - 1;
+                        for (int k = kr; k > 0; --k) m &= m - 1;
                         const int slot = __ffs(m) - 1;
                         const uint32_t meta = (uint32_t)ws.stage[zslot<B, S>(o, slot)];
                         const uint32_t j = meta & 0xFFFFFFu, i = (meta >> 24) & 0x7Fu, neg = meta >> 31;
-                        const uint64_t b = G::snap_at(ws.saved[o], ws.dd[o][slot], &d_jump);
-                        if (z128_wedge_accept(t, i, j, G::m53_of(b, 0, 0)))
-                            ws.stage[zslot<B, S>(o, slot)] = z128_value<DT>(t, i, j, neg, lane, false);
+                        if (z128_wedge_accept(t, i, j, G::m53_of(ws.rec[o][kr], 0, 0)))
+                            ws.stage[zslot<B, S>(o, slot)] = z128_value<DT>(t, i, j, neg, lane);
                         else
                             atomicOr(&ws.rej[o], 1u << slot);
                     }
@@ -830,48 +819,45 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             // ---- C: write the rows, skipping rejected slots ----
             const uint32_t rj = ws.rej[lane];
             const int acc = produced - __popc(rj);
-            ws.rowinfo[lane].dst = (unsigned long long)dst;
-            ws.rowinfo[lane].cnt = acc;
-            ws.rowinfo[lane].rej = rj;
-            ws.rowinfo[lane].sigma = sigma;
-            ws.rowinfo[lane].kind = kind;
-            __syncwarp();
-            if (MODE == 0 && a.vec_store) {
-                z128_flush_vec<B, S, OutT>(ws.stage, ws.rowinfo, lane);
+            rem -= (uint64_t)acc;
+            if (MODE == 0 && a.lane_sectors) {
+                z128_flush_lane<B, W::EPS, W::CW, S, OutT>(ws.stage, ws.carry, lane, rj, acc, rem == 0, dst, nc);
             } else {
-                constexpr int kLanesPerRow = B;
-                constexpr int kRowsPerStep = 32 / kLanesPerRow;
-                const int sub = lane / kLanesPerRow, c = lane % kLanesPerRow;
+                // warp-cooperative: B lanes per row, one element each; the row's
+                // pointer, count, rejections (and sigma, kind) come from its lane
+                constexpr int kRowsPerStep = 32 / B;
+                const int sub = lane / B, c = lane % B;
 #pragma unroll 4
                 for (int k = 0; k < 32 / kRowsPerStep; ++k) {
                     const int row = kRowsPerStep * k + sub;
-                    const RowInfo ri = ws.rowinfo[row];
-                    if (c < ri.cnt) {
+                    OutT* const rd = (OutT*)__shfl_sync(kFull, (unsigned long long)dst, row);
+                    const int rcnt = __shfl_sync(kFull, acc, row);
+                    const uint32_t rrej = __shfl_sync(kFull, rj, row);
+                    float rsig = 0.0f;
+                    uint32_t rkind = ZIG_REQ_MUTATE;
+                    if constexpr (MODE != 0) {
+                        rsig = __shfl_sync(kFull, sigma, row);
+                        rkind = __shfl_sync(kFull, kind, row);
+                    }
+                    if (c < rcnt) {
                         int src = c;   // slot of the row's c-th accepted candidate
-                        for (uint32_t m = ri.rej; m; m &= m - 1) {
+                        for (uint32_t m = rrej; m; m &= m - 1) {
                             if (__ffs(m) - 1 <= src) ++src;
                             else break;
                         }
                         const S z = ws.stage[zslot<B, S>(row, src)];
-                        OutT* rd = (OutT*)ri.dst;
-                        // write-once output: global streaming stores (evict-first)
                         if constexpr (MODE != 0) {
                             const float zf = __uint_as_float((uint32_t)z);
-                            if (MODE == 2 && ri.kind == ZIG_REQ_GENERATE) ((float*)rd)[c] = zf;
-                            else ((float*)rd)[c] = fmaf(ri.sigma, zf, ((float*)rd)[c]);
-                        } else if constexpr (DT == ZIG_F64) {
-                            __stcs((unsigned long long*)rd + c, (unsigned long long)z);
-                        } else if constexpr (DT == ZIG_F32) {
-                            __stcs((unsigned int*)rd + c, (unsigned int)z);
+                            if (MODE == 2 && rkind == ZIG_REQ_GENERATE) ((float*)rd)[c] = zf;
+                            else ((float*)rd)[c] = fmaf(rsig, zf, ((float*)rd)[c]);
                         } else {
-                            __stcs((unsigned short*)rd + c, f32_to_bf16_bits(__uint_as_float((uint32_t)z)));
+                            z128_store1<OutT, S>(rd + c, z);   // write-once output: streaming store
                         }
                     }
                 }
+                dst += acc;
             }
             __syncwarp();
-            dst += acc;
-            rem -= (uint64_t)acc;
         }
         if (check_chunk && draws > kChunkDraws) atomicOr(&d_err, kErrChunkOverflow);
     }
@@ -1003,17 +989,14 @@ static zig_status init_device(int device) {
     ZIG_CUDA(cudaGetDeviceProperties(&prop, device));
     if (!(prop.major == 10 && prop.minor == 3)) return ZIG_ERR_UNSUPPORTED;
     uint32_t kE[128];
-    uint64_t M[128];
     for (int i = 0; i < 128; ++i) {
         uint64_t bits;
         std::memcpy(&bits, &zigtab::ZIG128_W[i], 8);
         int E = (int)((bits >> 52) & 0x7FF);
         if (E - 900 < 0 || E - 900 > 255) return ZIG_ERR_UNSUPPORTED;
         kE[i] = zigtab::ZIG128_K[i] | ((uint32_t)(E - 900) << 24);
-        M[i] = (bits & ((1ull << 52) - 1)) | (1ull << 52);
     }
     ZIG_CUDA(cudaMemcpyToSymbol(d_z128_kE, kE, sizeof(kE)));
-    ZIG_CUDA(cudaMemcpyToSymbol(d_z128_M, M, sizeof(M)));
     ZIG_CUDA(cudaMemcpyToSymbol(d_z128_W, zigtab::ZIG128_W, sizeof(zigtab::ZIG128_W)));
     ZIG_CUDA(cudaMemcpyToSymbol(d_z128_Y, zigtab::ZIG128_Y, sizeof(zigtab::ZIG128_Y)));
     ZIG_CUDA(cudaMemcpyToSymbol(d_z128_W32, zigtab::ZIG128_W32, sizeof(zigtab::ZIG128_W32)));
@@ -1095,14 +1078,22 @@ constexpr bool z128_fits() {   // the default batch width is the larger one
     return z128_warp_bytes<G, DT>() * kZWarps + sizeof(Z128Tab) <= 227 * 1024;
 }
 static_assert(z128_fits<GenLcg48, ZIG_F64>() && z128_fits<GenLcg48, ZIG_F32>() &&
-                  z128_fits<GenSplitMix64, ZIG_F64>() && z128_fits<GenSplitMix64, ZIG_F32>() &&
-                  z128_fits<GenL64X128Mix, ZIG_F64>() && z128_fits<GenL64X128Mix, ZIG_F32>(),
+                  z128_fits<GenLcg48, ZIG_BF16>() && z128_fits<GenSplitMix64, ZIG_F64>() &&
+                  z128_fits<GenSplitMix64, ZIG_F32>() && z128_fits<GenSplitMix64, ZIG_BF16>() &&
+                  z128_fits<GenL64X128Mix, ZIG_F64>() && z128_fits<GenL64X128Mix, ZIG_F32>() &&
+                  z128_fits<GenL64X128Mix, ZIG_BF16>(),
               "z128_kernel shared memory exceeds 227 KB per block");
 
+// Exactly the per-warp bytes the kernel instantiation for (G, dt, batch width)
+// indexes (its carry rows depend on the output type, not only the staging word).
 template <class G>
 static size_t z128_dyn_for(int dt, bool half_batch, int warps) {
-    const size_t per = dt == ZIG_F64 ? (half_batch ? z128_warp_bytes<G, ZIG_F64, 8>() : z128_warp_bytes<G, ZIG_F64>())
-                                     : (half_batch ? z128_warp_bytes<G, ZIG_F32, 16>() : z128_warp_bytes<G, ZIG_F32>());
+    size_t per;
+    switch (dt) {
+    case ZIG_F64: per = half_batch ? z128_warp_bytes<G, ZIG_F64, 8>() : z128_warp_bytes<G, ZIG_F64>(); break;
+    case ZIG_F32: per = half_batch ? z128_warp_bytes<G, ZIG_F32, 16>() : z128_warp_bytes<G, ZIG_F32>(); break;
+    default: per = half_batch ? z128_warp_bytes<G, ZIG_BF16, 16>() : z128_warp_bytes<G, ZIG_BF16>(); break;
+    }
     return per * (size_t)warps;
 }
 
@@ -1130,7 +1121,7 @@ static LaunchCfg default_cfg(int dt) { return LaunchCfg{(uint32_t)kZBlock, defau
 static bool cfg_valid(int dt, const LaunchCfg& c) {
     const uint32_t b = default_batch(dt);
     return c.block >= 64 && c.block <= (uint32_t)kZBlock && c.block % 32 == 0 &&
-           (c.batch == b || c.batch == b / 2) && (c.store_bytes == 0 || c.store_bytes == 16);
+           (c.batch == b || c.batch == b / 2) && (c.store_bytes == 0 || c.store_bytes == 32);
 }
 
 static LaunchCfg cfg_of(int dev, int prng, int dt, bool variable) {
@@ -1203,7 +1194,7 @@ static zig_status launch_gen(int alg, int prng, int dt, int dev, bool variable, 
     const LaunchCfg c = force ? *force : z128 ? cfg_of(dev, prng, dt, variable) : default_cfg(dt);
     const bool half = z128 && c.batch != default_batch(dt);
     const int block = z128 ? (int)c.block : kBlock;
-    a.vec_store = (z128 && c.store_bytes == 16) ? 1u : 0u;
+    a.lane_sectors = (z128 && c.store_bytes == 32) ? 1u : 0u;
     GenFn fn = pick(alg, prng, dt, half);
     const size_t dyn = dyn_smem_of(alg, dt, prng, half, block);
     if (!allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
@@ -1359,7 +1350,7 @@ uint32_t zig_autotune_candidates(zig_dtype dtype, zig_launch_config* cands, uint
     uint32_t n = 0;
     for (uint32_t bl : blocks)
         for (uint32_t bw : {b / 2, b})
-            for (uint32_t sb : {0u, 16u}) {
+            for (uint32_t sb : {0u, 32u}) {
                 if (cands && n < max_cands) cands[n] = zig_launch_config{bl, bw, sb, 0};
                 ++n;
             }

@@ -83,17 +83,17 @@ def test_launch_config_validation_and_candidates():
         assert len(cands) == 16
         assert {c["batch"] for c in cands} == {b // 2, b}
         assert {c["block"] for c in cands} == {256, 384, 512, 768}
-        assert {c["store_bytes"] for c in cands} == {0, 16}
+        assert {c["store_bytes"] for c in cands} == {0, 32}
         for bad in ({"block": 800, "batch": b, "store_bytes": 0},
                     {"block": 100, "batch": b, "store_bytes": 0},
                     {"block": 256, "batch": b * 2, "store_bytes": 0},
-                    {"block": 256, "batch": b, "store_bytes": 8}):
+                    {"block": 256, "batch": b, "store_bytes": 16}):
             try:
                 Z.zig_launch_config_set("lcg48", dt, True, bad, device=5)
                 raise AssertionError(f"accepted {bad}")
             except Z.ZigError as e:
                 assert e.status == 1
-    cfg = {"block": 384, "batch": 8, "store_bytes": 16}
+    cfg = {"block": 384, "batch": 8, "store_bytes": 32}
     Z.zig_launch_config_set("l64x128mix", "f64", True, cfg, device=5)
     assert Z.zig_launch_config_get("l64x128mix", "f64", True, device=5) == cfg
     assert Z.zig_launch_config_get("l64x128mix", "f64", False, device=5)["block"] == 768
