@@ -754,8 +754,25 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                     const uint32_t j = w >> 8;
                     S val = z128_value<DT>(t, i, j, neg, lane);
                     const bool slow = j >= t.K[i][lane];
-                    if (__any_sync(kFull, slow)) {
-                        if (slow) val = z128_slow<G, DT>(g, t, ws, lane, v, i, j, neg, drel, smask);
+                    bool other = slow;   // what needs the divergent slow handler
+                    if constexpr (PRNG != ZIG_L64X128MIX) {
+                        // a wedge is deferred without a branch: recording its uniform
+                        // and stepping past it cost a few predicated instructions
+                        // (LXM's step is too long to run predicated on every candidate)
+                        const int nw = __popc(smask);
+                        const bool wedge = slow && i < 127 && nw < kZRec;
+                        if (wedge) {
+                            uint64_t b, c;
+                            g.snap(1, b, c);
+                            ws.rec[lane][nw] = b;
+                            drel += G::kStepsPerDouble;
+                            smask |= 1u << v;
+                            val = (S)(j | (i << 24) | (neg << 31));
+                        }
+                        other = slow && !wedge;
+                    }
+                    if (__any_sync(kFull, other)) {
+                        if (other) val = z128_slow<G, DT>(g, t, ws, lane, v, i, j, neg, drel, smask);
                     }
                     ws.stage[zslot<B, S>(lane, v)] = val;
                 }
