@@ -282,7 +282,8 @@ def run_gpu(args):
     line_extra = {
         "per_prng": {p: {"variates_per_s": N_STREAMS * PER_STREAM / (statistics.mean(per_launch[p]) / 1e3),
                          "ms_p50": float(np.percentile(per_launch[p], 50)),
-                         "ms_p99": float(np.percentile(per_launch[p], 99))} for p in PRNGS},
+                         "ms_p99": float(np.percentile(per_launch[p], 99)),
+                         "ms_mean_ci999": mean_ci(per_launch[p])} for p in PRNGS},
         "launch_ms_p50": float(np.percentile(all_ms, 50)),
         "launch_ms_p99": float(np.percentile(all_ms, 99)),
     }
@@ -330,6 +331,15 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def mean_ci(xs, z=3.2905):
+    """99.9 % confidence interval of the mean launch time (normal approximation)."""
+    if len(xs) < 2:
+        return None
+    m, sd = statistics.mean(xs), statistics.stdev(xs)
+    h = z * sd / math.sqrt(len(xs))
+    return [m - h, m + h]
 
 
 def time_launches(torch, stream, fn, reps):

@@ -334,6 +334,19 @@ zig_status zig_device_status(int device, int clear);
 const char *zig_status_string(zig_status status);
 
 /* Library version as major * 10000 + minor * 100 + patch. */
+/*
+ * zig_selfcheck -- exhaustive check of the fast path's arithmetic on the current
+ * device (test support; the paper has no counterpart).  Computes RN(j * w[i]) by
+ * the kernel's fused multiply-add construction for every abscissa j < 2^24 of
+ * every layer i < 128 and compares it with IEEE multiplication (__dmul_rn), and
+ * rounds every finite binary32 bit pattern to bfloat16 by the kernel's routine
+ * and compares it with __float2bfloat16_rn.  Writes counts_host[0] = product
+ * mismatches, [1] = bfloat16 mismatches, [2] = products checked (2^31),
+ * [3] = patterns checked.  Synchronous; allocates 32 bytes of device memory for
+ * the call.  ZIG_ERR_NOT_INITIALIZED without zig_tables_init.
+ */
+zig_status zig_selfcheck(uint64_t counts_host[4]);
+
 int zig_version(void);
 
 #ifdef __cplusplus

@@ -36,6 +36,7 @@ EXPORTS = (
     "zig_server_create", "zig_server_submit", "zig_server_wait", "zig_server_query",
     "zig_server_drain", "zig_server_stats", "zig_server_destroy", "zig_server_submit_generate",
     "zig_launch_config_get", "zig_launch_config_set", "zig_autotune_candidates", "zig_autotune",
+    "zig_selfcheck",
 )
 
 
@@ -132,6 +133,8 @@ def load(build_if_missing: bool = True):
                                      C.c_uint32, C.POINTER(LaunchConfig), C.POINTER(C.c_float), vp]
         for name in ("zig_launch_config_get", "zig_launch_config_set", "zig_autotune"):
             getattr(lib, name).restype = i32
+        lib.zig_selfcheck.argtypes = [C.POINTER(u64)]
+        lib.zig_selfcheck.restype = i32
         lib.zig_device_status.argtypes = [i32, i32]
         lib.zig_status_string.argtypes = [i32]
         lib.zig_status_string.restype = C.c_char_p
@@ -277,6 +280,14 @@ def zig_prng_fill(prng: str, seeds, n: int, out, skip: int = 0, kind: str = "u32
     st = load().zig_prng_fill(PRNG[prng], seeds.data_ptr(), int(seeds.numel()), int(n),
                               int(skip), FILL_KIND[kind], out.data_ptr(), _stream_ptr(stream))
     _check(st, "zig_prng_fill")
+
+
+def zig_selfcheck() -> dict:
+    """Exhaustive check of the fast-path product and the bfloat16 rounding (see zig.h)."""
+    c = (C.c_uint64 * 4)()
+    _check(load().zig_selfcheck(c), "zig_selfcheck")
+    return {"product_mismatches": int(c[0]), "bf16_mismatches": int(c[1]),
+            "products_checked": int(c[2]), "patterns_checked": int(c[3])}
 
 
 def zig_device_status(device: int = 0, clear: bool = False) -> int:

@@ -12,6 +12,7 @@
 //   zig256  modified ziggurat after McFarland: 253 equal-area rectangles under
 //           the curve are accepted with no test; overhangs and the tail are
 //           picked by a 256-bin alias table and sampled by rejection.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -880,6 +881,34 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
     }
 }
 
+// Exhaustive check of the fast path's arithmetic against CUDA's IEEE operations:
+// RN(j * w[i]) by the fused multiply-add construction against __dmul_rn for all
+// 2^24 abscissae j of all 128 layers, and the bfloat16 rounding of every finite
+// binary32 pattern against __float2bfloat16_rn.  counts: product mismatches,
+// bfloat16 mismatches, products checked, patterns checked.
+__global__ void __launch_bounds__(256) selfcheck_kernel(unsigned long long* counts) {
+    unsigned long long bad_p = 0, bad_b = 0, n_p = 0, n_b = 0;
+    const uint64_t n = 1ull << 31;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = (uint32_t)(k >> 24), j = (uint32_t)k & 0xFFFFFFu;
+        const double w = d_z128_W[i];
+        bad_p += mul_j_w_fma(j, w) != (uint64_t)__double_as_longlong(__dmul_rn((double)j, w));
+        ++n_p;
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+            const float f = __uint_as_float((uint32_t)k | (h << 31));
+            if (isfinite(f)) {
+                bad_b += f32_to_bf16_bits(f) != __bfloat16_as_ushort(__float2bfloat16_rn(f));
+                ++n_b;
+            }
+        }
+    }
+    atomicAdd(&counts[0], bad_p);
+    atomicAdd(&counts[1], bad_b);
+    atomicAdd(&counts[2], n_p);
+    atomicAdd(&counts[3], n_b);
+}
+
 // Exclusive prefix sums of lengths and unit counts (one block).
 __global__ void __launch_bounds__(1024) scan_kernel(const uint64_t* lengths, uint64_t n,
                                                     uint32_t chunk_log2, uint64_t* offsets,
@@ -1563,6 +1592,25 @@ const char* zig_status_string(zig_status status) {
 }
 
 int zig_version(void) { return 100; }
+
+zig_status zig_selfcheck(uint64_t counts_host[4]) {
+    if (!counts_host) return ZIG_ERR_INVALID_ARG;
+    int dev;
+    zig_status st = host::current_device(dev);
+    if (st != ZIG_OK) return st;
+    unsigned long long* d = nullptr;
+    ZIG_CUDA(cudaMalloc(&d, 4 * sizeof(unsigned long long)));
+    st = ZIG_OK;
+    if (cudaMemset(d, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) st = ZIG_ERR_CUDA;
+    if (st == ZIG_OK) {
+        selfcheck_kernel<<<host::g_sms[dev] * 8, 256>>>(d);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(counts_host, d, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = ZIG_ERR_CUDA;
+    }
+    cudaFree(d);
+    return st;
+}
 
 }  // extern "C"
 
