@@ -83,25 +83,25 @@ struct GenLcg48 {
             n &= n - 1;
         }
     }
-    // Deferred doubles: snap() records what the next nd (1 or 2) nextDouble
-    // calls need and moves the state past them (nextDouble = 2 steps); m53_of()
-    // rebuilds the k-th of those doubles later, from the record alone.
+    // Deferred doubles: snap() returns a record of the next nextDouble call and
+    // moves the state past it (nextDouble = 2 steps); m53_of() rebuilds that
+    // double's 53-bit integer later from the record alone.  (The kOut choice
+    // only matters for L64X128Mix.)
     static constexpr uint64_t kA2 = (kLcgA * kLcgA) & kMask48;
     static constexpr uint64_t kC2 = (kLcgA * kLcgC + kLcgC) & kMask48;
-    static constexpr uint64_t kA4 = (kA2 * kA2) & kMask48;
-    static constexpr uint64_t kC4 = (kA2 * kC2 + kC2) & kMask48;
     static constexpr uint32_t kStepsPerDouble = 2;
-    __device__ __forceinline__ void snap(int nd, uint64_t& b, uint64_t& c) {
-        b = s;
-        c = 0;
-        s = (nd == 1) ? ((kA2 * s + kC2) & kMask48) : ((kA4 * s + kC4) & kMask48);
+    template <bool kOut = false>
+    __device__ __forceinline__ uint64_t snap() {
+        const uint64_t b = s;
+        s = (kA2 * s + kC2) & kMask48;
+        return b;
     }
-    static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t, int k) {
-        uint64_t t = k ? ((kA2 * b + kC2) & kMask48) : b;
+    template <bool kOut = false>
+    static __device__ __forceinline__ uint64_t m53_of(uint64_t b) {
+        uint64_t t = (b * kLcgA + kLcgC) & kMask48;
+        const uint64_t hi = t >> 22;   // next(26)
         t = (t * kLcgA + kLcgC) & kMask48;
-        uint64_t hi = t >> 22;   // next(26)
-        t = (t * kLcgA + kLcgC) & kMask48;
-        uint64_t lo = t >> 21;   // next(27)
+        const uint64_t lo = t >> 21;   // next(27)
         return (hi << 27) + lo;
     }
 };
@@ -114,14 +114,11 @@ struct GenSplitMix64 {
     __device__ __forceinline__ uint64_t next_m53() { s += kGamma; return mix64(s) >> 11; }
     __device__ __forceinline__ void jump(uint64_t n, const JumpTab*) { s += n * kGamma; }
     static constexpr uint32_t kStepsPerDouble = 1;
-    __device__ __forceinline__ void snap(int nd, uint64_t& b, uint64_t& c) {
-        b = s + kGamma;
-        c = 0;
-        s += (nd == 1) ? kGamma : 2 * kGamma;
-    }
-    static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t, int k) {
-        return mix64(k ? b + kGamma : b) >> 11;
-    }
+    // the record of the next nextDouble is the state of its step
+    template <bool kOut = false>
+    __device__ __forceinline__ uint64_t snap() { s += kGamma; return s; }
+    template <bool kOut = false>
+    static __device__ __forceinline__ uint64_t m53_of(uint64_t b) { return mix64(b) >> 11; }
 };
 
 struct GenL64X128Mix {
@@ -152,14 +149,22 @@ struct GenL64X128Mix {
         x1 = rotl64(q1, 37);
     }
     static constexpr uint32_t kStepsPerDouble = 1;
-    __device__ __forceinline__ void snap(int nd, uint64_t& b, uint64_t& c) {
-        b = s + x0;   // the mix input of the next step
-        advance();
-        c = s + x0;
-        if (nd == 2) advance();
+    // the record of the next nextDouble is that step's mix input s + x0, or
+    // (kOut) its nextLong output itself, for a caller that computes it anyway
+    template <bool kOut = false>
+    __device__ __forceinline__ uint64_t snap() {
+        if constexpr (kOut) {
+            return next_u64();
+        } else {
+            const uint64_t b = s + x0;
+            advance();
+            return b;
+        }
     }
-    static __device__ __forceinline__ uint64_t m53_of(uint64_t b, uint64_t c, int k) {
-        return mix_lea64(k ? c : b) >> 11;
+    template <bool kOut = false>
+    static __device__ __forceinline__ uint64_t m53_of(uint64_t b) {
+        if constexpr (kOut) return b >> 11;
+        else return mix_lea64(b) >> 11;
     }
     __device__ void jump(uint64_t n, const JumpTab* jt) {
         while (n) {

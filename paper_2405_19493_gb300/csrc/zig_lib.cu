@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/zig.h"
@@ -500,6 +501,12 @@ __device__ __forceinline__ typename ZStage<DT>::T z128_from64(double x, uint32_t
 // the other choice a launch configuration can make.
 template <int DT> struct ZBatch { static constexpr int B = (DT == ZIG_F64) ? 16 : 32; };
 
+// The kind of wedge record a kernel instantiation keeps: L64X128Mix binary64
+// batches draw every output with nextLong anyway and record that output; the
+// other instantiations record the generator's cheaper snapshot (G::snap).
+template <class G, int DT>
+constexpr bool kRecOut = std::is_same<G, GenL64X128Mix>::value && DT == ZIG_F64;
+
 // Deferred wedges a lane may hold per batch (one 8-byte record each); a lane's
 // next wedge in the same batch is decided on the spot.  With 2.7 % wedges a
 // lane defers more than 4 of its 16 (32) candidates in about 6e-5 (3e-3) of
@@ -641,9 +648,7 @@ __device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab&
         if (i < 127) {
             const int nw = __popc(smask);
             if (nw < kZRec) {
-                uint64_t b, c;
-                g.snap(1, b, c);   // record the uniform and move past it
-                ws.rec[lane][nw] = b;
+                ws.rec[lane][nw] = g.template snap<kRecOut<G, DT>>();   // record the uniform, move past it
                 drel += G::kStepsPerDouble;
                 smask |= 1u << v;
                 return (S)(j | (i << 24) | (neg << 31));
@@ -742,7 +747,50 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             uint32_t drel = 0, smask = 0;
             int produced;
             // ---- A: draw the batch's candidates ----
-            if (__all_sync(kFull, rem >= (uint64_t)B)) {
+            if (PRNG == ZIG_L64X128MIX && DT == ZIG_F64 && __all_sync(kFull, rem >= (uint64_t)B)) {
+                // LXM: nextInt and nextDouble are both cut from nextLong, so a deferred
+                // wedge's uniform is simply the next output.  Every iteration takes one
+                // output: a candidate, or the record of the wedge deferred just before.
+                // No lane ever steps its generator in a divergent branch for a wedge;
+                // a lane ends the batch with B minus its deferred wedges candidates.
+                // (Measured faster for binary64 only; the 32-wide binary32 batches
+                // keep the candidate loop below.)
+                int slot = 0;
+                bool pend = false;
+#pragma unroll 2
+                for (int it = 0; it < B; ++it) {
+                    const uint64_t r = g.next_u64();   // this output is its own record
+                    ++drel;
+                    if (pend) {
+                        ws.rec[lane][__popc(smask) - 1] = r;
+                        pend = false;
+                    } else {
+                        const uint32_t w = (uint32_t)(r >> 32);   // nextInt
+                        const uint32_t i = w & 0x7Fu;
+                        const uint32_t neg = (~w >> 7) & 1u;   // bit 7 set -> positive
+                        const uint32_t j = w >> 8;
+                        S val = z128_value<DT>(t, i, j, neg, lane);
+                        const bool slow = j >= t.K[i][lane];
+                        const bool wedge = slow && i < 127 && __popc(smask) < kZRec;
+                        if (wedge) {
+                            smask |= 1u << slot;
+                            val = (S)(j | (i << 24) | (neg << 31));
+                            pend = true;
+                        }
+                        const bool other = slow && !wedge;   // a tail, or no record left
+                        if (__any_sync(__activemask(), other)) {
+                            if (other) val = z128_slow<G, DT>(g, t, ws, lane, slot, i, j, neg, drel, smask);
+                        }
+                        ws.stage[zslot<B, S>(lane, slot)] = val;
+                        ++slot;
+                    }
+                }
+                if (pend) {   // the last candidate was a deferred wedge: its uniform is next
+                    ws.rec[lane][__popc(smask) - 1] = g.next_u64();
+                    ++drel;
+                }
+                produced = slot;
+            } else if (__all_sync(kFull, rem >= (uint64_t)B)) {
                 // full batch: B candidates per lane, one warp vote per candidate guarding
                 // the rare slow draws (unrolled by two: deeper unrolling copies the slow
                 // handler into the instruction stream and costs more than it saves)
@@ -763,9 +811,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                         const int nw = __popc(smask);
                         const bool wedge = slow && i < 127 && nw < kZRec;
                         if (wedge) {
-                            uint64_t b, c;
-                            g.snap(1, b, c);
-                            ws.rec[lane][nw] = b;
+                            ws.rec[lane][nw] = g.template snap<kRecOut<G, DT>>();
                             drel += G::kStepsPerDouble;
                             smask |= 1u << v;
                             val = (S)(j | (i << 24) | (neg << 31));
@@ -826,7 +872,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                         const int slot = __ffs(m) - 1;
                         const uint32_t meta = (uint32_t)ws.stage[zslot<B, S>(o, slot)];
                         const uint32_t j = meta & 0xFFFFFFu, i = (meta >> 24) & 0x7Fu, neg = meta >> 31;
-                        if (z128_wedge_accept(t, i, j, G::m53_of(ws.rec[o][kr], 0, 0)))
+                        if (z128_wedge_accept(t, i, j, G::template m53_of<kRecOut<G, DT>>(ws.rec[o][kr])))
                             ws.stage[zslot<B, S>(o, slot)] = z128_value<DT>(t, i, j, neg, lane);
                         else
                             atomicOr(&ws.rej[o], 1u << slot);
