@@ -259,17 +259,4 @@ __device__ __forceinline__ void stage_flush(const T* stage, T* my_dst, int my_cn
     }
 }
 
-// Read-modify-write variant for in-place mutation: dst[c] = fmaf(sigma, z, dst[c]).
-__device__ __forceinline__ void stage_flush_fma(const float* stage, float* my_dst, int my_cnt,
-                                                int lane, float sigma) {
-    const int half = lane >> 4, c = lane & 15;
-#pragma unroll 4
-    for (int k = 0; k < 16; ++k) {
-        int row = 2 * k + half;
-        float* dst = (float*)__shfl_sync(kFull, (unsigned long long)my_dst, row);
-        int cnt = __shfl_sync(kFull, my_cnt, row);
-        if (c < cnt) dst[c] = fmaf(sigma, stage[stage_idx<float>(row, c)], dst[c]);
-    }
-}
-
 }  // namespace zig
