@@ -360,7 +360,8 @@ def compare_variants(Z, torch, seeds, stream, args):
     n = N_STREAMS * PER_STREAM
     for alg, prng, dt in (("polar", "lcg48", "f64"), ("zig256", "splitmix64", "f64"),
                           ("zig128", "splitmix64", "f32"), ("zig128", "splitmix64", "bf16"),
-                          ("zig128", "lcg48", "f32")):
+                          ("zig128", "lcg48", "f32"), ("zig128", "xoroshiro128pp", "f64"),
+                          ("zig256", "xoroshiro128pp", "f64")):
         tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dt]
         o = torch.empty(n, dtype=tdt, device="cuda")
         fn = lambda: Z.zig_generate(prng, alg, seeds, o, uniform_len=PER_STREAM, dtype=dt, stream=stream)

@@ -55,8 +55,12 @@ typedef enum {
                             seeded (seed ^ 0x5DEECE66D) mod 2^48; nextInt = s >> 16 */
     ZIG_SPLITMIX64 = 1,  /* SplittableRandom / ThreadLocalRandom: s += 0x9E3779B97F4A7C15;
                             nextInt = mix32(s), nextLong = mix64(s) */
-    ZIG_L64X128MIX = 2   /* LXM: 64-bit LCG (M = 0xD1342543DE82EF95) + xoroshiro128
+    ZIG_L64X128MIX = 2,  /* LXM: 64-bit LCG (M = 0xD1342543DE82EF95) + xoroshiro128
                             (24, 16, 37) + Lea's mix; seeded from 4 SplitMix64 outputs */
+    ZIG_XOROSHIRO128PP = 3 /* Xoroshiro128PlusPlus, an XBG generator (Sec. 3 names the
+                            XBG family): nextLong = rotl(x0 + x1, 17) + x0, then the
+                            xoroshiro128 engine (49, 21, 28); seeded from 2 SplitMix64
+                            outputs; nextInt = nextLong >>> 32 */
 } zig_prng;
 
 /* Gaussian transforms (Sec. 2, second list). */

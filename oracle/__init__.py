@@ -33,7 +33,7 @@ SRC = os.path.join(HERE, "zig_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 TABLE_DIR = os.path.join(HERE, "tables")
 
-PRNGS = {"lcg48": 0, "splitmix64": 1, "l64x128mix": 2}
+PRNGS = {"lcg48": 0, "splitmix64": 1, "l64x128mix": 2, "xoroshiro128pp": 3}
 ALGS = {"zig128": 0, "polar": 1, "zig256": 2}
 FILL_KINDS = {"u32": 0, "u64": 1, "m53": 2}
 

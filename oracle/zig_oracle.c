@@ -14,7 +14,8 @@
  *  - PRNGs (Sec. 2, first list; Sec. 3 on LXM):
  *      java.util.Random 48-bit LCG (Knuth vol. 2 LCG, a = 0x5DEECE66D, c = 0xB),
  *      SplittableRandom / ThreadLocalRandom = SplitMix64 (Steele, Lea & Flood),
- *      L64X128MixRandom (LXM: 64-bit LCG + xoroshiro128 + Lea's mix).
+ *      L64X128MixRandom (LXM: 64-bit LCG + xoroshiro128 + Lea's mix), and
+ *      Xoroshiro128PlusPlus (an XBG generator; Sec. 3 names the XBG family).
  *    Draw semantics follow the Java methods the paper's calls use: nextInt,
  *    nextLong, nextDouble.
  *  - Original ziggurat, GSL form (Sec. 1; Sec. 2 "Ziggurat" bullet): one 32-bit
@@ -34,6 +35,7 @@
 #define ORC_LCG48 0
 #define ORC_SPLITMIX64 1
 #define ORC_L64X128MIX 2
+#define ORC_XOROSHIRO128PP 3
 #define ORC_SCRIPTED 9
 
 #define ORC_ZIG128 0
@@ -51,7 +53,7 @@ typedef struct {
     int kind;
     uint64_t s;       /* LCG48 state, SplitMix64 seed, or LXM's LCG state */
     uint64_t a;       /* LXM additive parameter (odd) */
-    uint64_t x0, x1;  /* LXM xoroshiro128 state */
+    uint64_t x0, x1;  /* LXM's xoroshiro128 state, or Xoroshiro128PlusPlus's state */
     const uint64_t *script; /* ORC_SCRIPTED: words returned in order */
     uint64_t script_len, script_pos;
     int script_overrun;
@@ -109,6 +111,13 @@ void orc_seed(orc_prng *g, int kind, uint64_t seed) {
         t += GOLDEN_GAMMA; g->x0 = mix64(t);
         t += GOLDEN_GAMMA; g->x1 = mix64(t);
         if ((g->x0 | g->x1) == 0) g->x1 = GOLDEN_GAMMA;
+    } else if (kind == ORC_XOROSHIRO128PP) {
+        /* Seed expansion (reading): two consecutive SplitMix64 outputs of a
+         * generator seeded with `seed` give x0, x1 (never both zero). */
+        uint64_t t = seed;
+        t += GOLDEN_GAMMA; g->x0 = mix64(t);
+        t += GOLDEN_GAMMA; g->x1 = mix64(t);
+        if ((g->x0 | g->x1) == 0) g->x1 = GOLDEN_GAMMA;
     }
 }
 
@@ -137,6 +146,18 @@ static uint64_t lxm_next(orc_prng *g) {
     g->x1 = q1;
     return result;
 }
+/* One Xoroshiro128PlusPlus step (the XBG generator's nextLong): the ++
+ * scrambler of the current state, then the xoroshiro128 linear engine with
+ * rotation/shift constants (49, 21, 28). */
+static uint64_t xpp_next(orc_prng *g) {
+    const uint64_t s0 = g->x0;
+    uint64_t s1 = g->x1;
+    const uint64_t result = rotl64(s0 + s1, 17) + s0;
+    s1 ^= s0;
+    g->x0 = rotl64(s0, 49) ^ s1 ^ (s1 << 21);
+    g->x1 = rotl64(s1, 28);
+    return result;
+}
 
 static uint64_t script_next(orc_prng *g) {
     if (g->script_pos >= g->script_len) {
@@ -152,6 +173,7 @@ uint32_t orc_next_u32(orc_prng *g, orc_stats *st) {
     case ORC_LCG48: if (st) st->draws += 1; return lcg_next(g, 32);
     case ORC_SPLITMIX64: if (st) st->draws += 1; g->s += GOLDEN_GAMMA; return mix32(g->s);
     case ORC_L64X128MIX: if (st) st->draws += 1; return (uint32_t)(lxm_next(g) >> 32);
+    case ORC_XOROSHIRO128PP: if (st) st->draws += 1; return (uint32_t)(xpp_next(g) >> 32);
     default: return (uint32_t)script_next(g);
     }
 }
@@ -168,6 +190,7 @@ uint64_t orc_next_u64(orc_prng *g, orc_stats *st) {
     }
     case ORC_SPLITMIX64: if (st) st->draws += 1; g->s += GOLDEN_GAMMA; return mix64(g->s);
     case ORC_L64X128MIX: if (st) st->draws += 1; return lxm_next(g);
+    case ORC_XOROSHIRO128PP: if (st) st->draws += 1; return xpp_next(g);
     default: return script_next(g);
     }
 }
@@ -183,6 +206,7 @@ uint64_t orc_next_m53(orc_prng *g, orc_stats *st) {
     }
     case ORC_SPLITMIX64: if (st) st->draws += 1; g->s += GOLDEN_GAMMA; return mix64(g->s) >> 11;
     case ORC_L64X128MIX: if (st) st->draws += 1; return lxm_next(g) >> 11;
+    case ORC_XOROSHIRO128PP: if (st) st->draws += 1; return xpp_next(g) >> 11;
     default: return script_next(g) >> 11;
     }
 }
@@ -228,20 +252,22 @@ static void gf2_apply(const gf2map *m, const uint64_t v[2], uint64_t out[2]) {
     out[1] = r1;
 }
 
-static void xoro_step_vec(uint64_t v[2]) {
+/* One step of a xoroshiro128 linear engine with constants (a, b, c):
+ * (24, 16, 37) inside LXM, (49, 21, 28) for Xoroshiro128PlusPlus. */
+static void xoro_step_vec(uint64_t v[2], int a, int b, int c) {
     uint64_t q0 = v[0], q1 = v[1];
     q1 ^= q0;
-    q0 = rotl64(q0, 24) ^ q1 ^ (q1 << 16);
-    q1 = rotl64(q1, 37);
+    q0 = rotl64(q0, a) ^ q1 ^ (q1 << b);
+    q1 = rotl64(q1, c);
     v[0] = q0;
     v[1] = q1;
 }
 
-static void gf2_one_step(gf2map *m) {
+static void gf2_one_step(gf2map *m, int a, int b, int cc) {
     for (int c = 0; c < 128; c++) {
         uint64_t v[2] = {0, 0};
         if (c < 64) v[0] = UINT64_C(1) << c; else v[1] = UINT64_C(1) << (c - 64);
-        xoro_step_vec(v);
+        xoro_step_vec(v, a, b, cc);
         m->col[c][0] = v[0];
         m->col[c][1] = v[1];
     }
@@ -272,7 +298,7 @@ typedef struct {
     int kind;
     uint64_t n;
     affine lcg;      /* LCG48 (masked) or LXM's 64-bit LCG */
-    gf2map xoro;     /* LXM only */
+    gf2map xoro;     /* LXM and Xoroshiro128PlusPlus */
 } orc_jump;
 
 void orc_jump_init(orc_jump *j, int kind, uint64_t n) {
@@ -282,9 +308,13 @@ void orc_jump_init(orc_jump *j, int kind, uint64_t n) {
     if (kind == ORC_LCG48) {
         affine one = {LCG_A, LCG_C};
         j->lcg = affine_pow(one, n);
+    } else if (kind == ORC_XOROSHIRO128PP) {
+        gf2map one;
+        gf2_one_step(&one, 49, 21, 28);
+        gf2_pow(&one, n, &j->xoro);
     } else if (kind == ORC_L64X128MIX) {
         gf2map one;
-        gf2_one_step(&one);
+        gf2_one_step(&one, 24, 16, 37);
         gf2_pow(&one, n, &j->xoro);
         /* the LCG part's additive term depends on the stream's `a`; keep A only */
         affine one_a = {LXM_M, 0};
@@ -306,6 +336,11 @@ void orc_jump_apply(const orc_jump *j, orc_prng *g) {
         g->s += j->n * GOLDEN_GAMMA;
     } else if (g->kind == ORC_L64X128MIX) {
         g->s = j->lcg.A * g->s + g->a * geom_sum(LXM_M, j->n);
+        uint64_t v[2] = {g->x0, g->x1}, o[2];
+        gf2_apply(&j->xoro, v, o);
+        g->x0 = o[0];
+        g->x1 = o[1];
+    } else if (g->kind == ORC_XOROSHIRO128PP) {
         uint64_t v[2] = {g->x0, g->x1}, o[2];
         gf2_apply(&j->xoro, v, o);
         g->x0 = o[0];
@@ -519,7 +554,9 @@ int orc_generate(int prng, int alg, const uint64_t *seeds, const uint64_t *lengt
                  uint64_t uniform_len, uint64_t n_streams, uint32_t chunk_log2,
                  const orc_zig128_tab *t128, const orc_zig256_tab *t256, double *out,
                  double *margins, orc_stats *st) {
-    if (prng != ORC_LCG48 && prng != ORC_SPLITMIX64 && prng != ORC_L64X128MIX) return -1;
+    if (prng != ORC_LCG48 && prng != ORC_SPLITMIX64 && prng != ORC_L64X128MIX &&
+        prng != ORC_XOROSHIRO128PP)
+        return -1;
     if (alg == ORC_ZIG128 && !t128) return -1;
     if (alg == ORC_ZIG256 && !t256) return -1;
     if (alg != ORC_ZIG128 && alg != ORC_POLAR && alg != ORC_ZIG256) return -1;
@@ -563,7 +600,9 @@ int orc_generate(int prng, int alg, const uint64_t *seeds, const uint64_t *lengt
  * `skip` raw steps (closed-form jump) before its n draws. */
 int orc_prng_fill(int prng, const uint64_t *seeds, uint64_t n_streams, uint64_t n,
                   uint64_t skip, int kind, uint64_t *out) {
-    if (prng != ORC_LCG48 && prng != ORC_SPLITMIX64 && prng != ORC_L64X128MIX) return -1;
+    if (prng != ORC_LCG48 && prng != ORC_SPLITMIX64 && prng != ORC_L64X128MIX &&
+        prng != ORC_XOROSHIRO128PP)
+        return -1;
     orc_jump *jump = NULL;
     if (skip) {
         jump = (orc_jump *)malloc(sizeof(orc_jump));

@@ -22,7 +22,7 @@ STATUS_NAMES = {
 }
 # fixed scratch capacity of zig_generate_noalloc (ZIG_NOALLOC_MAX_STREAMS in include/zig.h)
 NOALLOC_MAX_STREAMS = 65536
-PRNG = {"lcg48": 0, "splitmix64": 1, "l64x128mix": 2}
+PRNG = {"lcg48": 0, "splitmix64": 1, "l64x128mix": 2, "xoroshiro128pp": 3}
 ALG = {"zig128": 0, "polar": 1, "zig256": 2}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2}
 ESIZE = {"f64": 8, "f32": 4, "bf16": 2}

@@ -25,7 +25,8 @@ constexpr unsigned kErrNullOutput = 4u;   // variable lengths summed > 0 with ou
 struct JumpTab {
     uint64_t lcg48_A[64], lcg48_C[64];   // s -> (A s + C) mod 2^48
     uint64_t lxm_A[64], lxm_G[64];       // LXM LCG: s -> A s + a G (mod 2^64)
-    uint64_t xoro[64][256];              // xoroshiro128 T^(2^b): column c at [2c], [2c+1]
+    uint64_t xoro[64][256];              // LXM's xoroshiro128 T^(2^b): column c at [2c], [2c+1]
+    uint64_t xpp[64][256];               // Xoroshiro128PlusPlus's engine, same layout
 };
 
 // ---------------------------------------------------------------------------
@@ -191,10 +192,63 @@ struct GenL64X128Mix {
     }
 };
 
+// Xoroshiro128PlusPlus, an XBG generator: nextLong = rotl(x0 + x1, 17) + x0,
+// then the xoroshiro128 engine with constants (49, 21, 28).  Seeded (a
+// reading) from two consecutive SplitMix64 outputs.  A deferred wedge's
+// record is its nextLong output itself (the scrambler is cheap).
+struct GenXoroshiro128PP {
+    uint64_t x0, x1;
+    __device__ __forceinline__ void seed(uint64_t x) {
+        uint64_t t = x;
+        t += kGamma; x0 = mix64(t);
+        t += kGamma; x1 = mix64(t);
+        if ((x0 | x1) == 0) x1 = kGamma;
+    }
+    __device__ __forceinline__ uint64_t next_u64() {
+        const uint64_t s0 = x0;
+        uint64_t s1 = x1;
+        const uint64_t r = rotl64(s0 + s1, 17) + s0;
+        s1 ^= s0;
+        x0 = rotl64(s0, 49) ^ s1 ^ (s1 << 21);
+        x1 = rotl64(s1, 28);
+        return r;
+    }
+    __device__ __forceinline__ uint32_t next_u32() { return (uint32_t)(next_u64() >> 32); }
+    __device__ __forceinline__ uint64_t next_m53() { return next_u64() >> 11; }
+    static constexpr uint32_t kStepsPerDouble = 1;
+    template <bool kOut = false>
+    __device__ __forceinline__ uint64_t snap() { return next_u64(); }
+    template <bool kOut = false>
+    static __device__ __forceinline__ uint64_t m53_of(uint64_t r) { return r >> 11; }
+    __device__ void jump(uint64_t n, const JumpTab* jt) {
+        while (n) {
+            const int b = __ffsll((long long)n) - 1;
+            const uint64_t* m = jt->xpp[b];
+            uint64_t r0 = 0, r1 = 0;
+#pragma unroll 8
+            for (int c = 0; c < 64; ++c) {
+                const uint64_t mask = 0ull - ((x0 >> c) & 1ull);
+                r0 ^= m[2 * c] & mask;
+                r1 ^= m[2 * c + 1] & mask;
+            }
+#pragma unroll 8
+            for (int c = 0; c < 64; ++c) {
+                const uint64_t mask = 0ull - ((x1 >> c) & 1ull);
+                r0 ^= m[128 + 2 * c] & mask;
+                r1 ^= m[128 + 2 * c + 1] & mask;
+            }
+            x0 = r0;
+            x1 = r1;
+            n &= n - 1;
+        }
+    }
+};
+
 template <int PRNG> struct GenOf;
 template <> struct GenOf<0> { using T = GenLcg48; };
 template <> struct GenOf<1> { using T = GenSplitMix64; };
 template <> struct GenOf<2> { using T = GenL64X128Mix; };
+template <> struct GenOf<3> { using T = GenXoroshiro128PP; };
 
 __device__ __forceinline__ double m53_to_double(uint64_t m) {
     return (double)m * 0x1p-53;   // exact: m < 2^53

@@ -747,8 +747,10 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             uint32_t drel = 0, smask = 0;
             int produced;
             // ---- A: draw the batch's candidates ----
-            if (PRNG == ZIG_L64X128MIX && DT == ZIG_F64 && __all_sync(kFull, rem >= (uint64_t)B)) {
-                // LXM: nextInt and nextDouble are both cut from nextLong, so a deferred
+            if ((PRNG == ZIG_L64X128MIX || PRNG == ZIG_XOROSHIRO128PP) && DT == ZIG_F64 &&
+                __all_sync(kFull, rem >= (uint64_t)B)) {
+                // LXM and Xoroshiro128PlusPlus: nextInt and nextDouble are both cut from
+                // nextLong, so a deferred
                 // wedge's uniform is simply the next output.  Every iteration takes one
                 // output: a candidate, or the record of the wedge deferred just before.
                 // No lane ever steps its generator in a divergent branch for a wedge;
@@ -804,10 +806,11 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                     S val = z128_value<DT>(t, i, j, neg, lane);
                     const bool slow = j >= t.K[i][lane];
                     bool other = slow;   // what needs the divergent slow handler
-                    if constexpr (PRNG != ZIG_L64X128MIX) {
+                    if constexpr (PRNG == ZIG_LCG48 || PRNG == ZIG_SPLITMIX64) {
                         // a wedge is deferred without a branch: recording its uniform
                         // and stepping past it cost a few predicated instructions
-                        // (LXM's step is too long to run predicated on every candidate)
+                        // (the 64-bit generators' steps are too long to run predicated
+                        // on every candidate)
                         const int nw = __popc(smask);
                         const bool wedge = slow && i < 127 && nw < kZRec;
                         if (wedge) {
@@ -1025,49 +1028,58 @@ size_t g_ws_bytes[kMaxDevices];
 struct Affine { uint64_t A, C; };
 static Affine compose(Affine o, Affine i) { return {o.A * i.A, o.A * i.C + o.C}; }
 
-// xoroshiro128 one step on a (x0, x1) pair
-static void xoro_step(uint64_t& x0, uint64_t& x1) {
-    uint64_t q1 = x1 ^ x0;
-    x0 = ((x0 << 24) | (x0 >> 40)) ^ q1 ^ (q1 << 16);
-    x1 = (q1 << 37) | (q1 >> 27);
+// One step of a xoroshiro128 linear engine with constants (a, b, c) on (x0, x1).
+static void xoro_step(uint64_t& x0, uint64_t& x1, int a, int b, int c) {
+    const uint64_t q1 = x1 ^ x0;
+    x0 = ((x0 << a) | (x0 >> (64 - a))) ^ q1 ^ (q1 << b);
+    x1 = (q1 << c) | (q1 >> (64 - c));
+}
+
+// T^(2^k), k = 0..63, of the engine (a, b, c) as GF(2) matrices stored by
+// columns: column d of T^(2^k) at dst[k][2d], dst[k][2d + 1].
+static void fill_gf2_powers(uint64_t (*dst)[256], int a, int b, int cc) {
+    static uint64_t col[128][2], nxt[128][2];
+    for (int d = 0; d < 128; ++d) {
+        uint64_t x0 = d < 64 ? (1ull << d) : 0, x1 = d < 64 ? 0 : (1ull << (d - 64));
+        xoro_step(x0, x1, a, b, cc);
+        col[d][0] = x0;
+        col[d][1] = x1;
+    }
+    for (int k = 0; k < 64; ++k) {
+        for (int d = 0; d < 128; ++d) {
+            dst[k][2 * d] = col[d][0];
+            dst[k][2 * d + 1] = col[d][1];
+        }
+        // square the map: column d of T^2 = T applied to column d of T
+        for (int d = 0; d < 128; ++d) {
+            uint64_t r0 = 0, r1 = 0;
+            for (int e = 0; e < 128; ++e) {
+                const uint64_t bit = e < 64 ? (col[d][0] >> e) & 1 : (col[d][1] >> (e - 64)) & 1;
+                if (bit) {
+                    r0 ^= col[e][0];
+                    r1 ^= col[e][1];
+                }
+            }
+            nxt[d][0] = r0;
+            nxt[d][1] = r1;
+        }
+        std::memcpy(col, nxt, sizeof(col));
+    }
 }
 
 static void fill_jump(JumpTab& jt) {
     Affine l48 = {kLcgA, kLcgC};
     Affine lxm = {kLxmM, 1};
-    static uint64_t col[128][2], nxt[128][2];
-    for (int c = 0; c < 128; ++c) {
-        uint64_t x0 = c < 64 ? (1ull << c) : 0, x1 = c < 64 ? 0 : (1ull << (c - 64));
-        xoro_step(x0, x1);
-        col[c][0] = x0;
-        col[c][1] = x1;
-    }
     for (int b = 0; b < 64; ++b) {
         jt.lcg48_A[b] = l48.A & kMask48;
         jt.lcg48_C[b] = l48.C & kMask48;
         jt.lxm_A[b] = lxm.A;
         jt.lxm_G[b] = lxm.C;
-        for (int c = 0; c < 128; ++c) {
-            jt.xoro[b][2 * c] = col[c][0];
-            jt.xoro[b][2 * c + 1] = col[c][1];
-        }
         l48 = compose(l48, l48);
         lxm = compose(lxm, lxm);
-        // square the GF(2) map: column c of T^2 = T applied to column c of T
-        for (int c = 0; c < 128; ++c) {
-            uint64_t r0 = 0, r1 = 0;
-            for (int d = 0; d < 128; ++d) {
-                uint64_t bit = d < 64 ? (col[c][0] >> d) & 1 : (col[c][1] >> (d - 64)) & 1;
-                if (bit) {
-                    r0 ^= col[d][0];
-                    r1 ^= col[d][1];
-                }
-            }
-            nxt[c][0] = r0;
-            nxt[c][1] = r1;
-        }
-        std::memcpy(col, nxt, sizeof(col));
     }
+    fill_gf2_powers(jt.xoro, 24, 16, 37);   // LXM's xoroshiro128
+    fill_gf2_powers(jt.xpp, 49, 21, 28);    // Xoroshiro128PlusPlus
 }
 
 #define ZIG_CUDA(call)                               \
@@ -1152,7 +1164,8 @@ static GenFn pick_prng(int prng, int dt, bool half_batch) {
     switch (prng) {
     case ZIG_LCG48: return pick_dt<ALG, 0>(dt, half_batch);
     case ZIG_SPLITMIX64: return pick_dt<ALG, 1>(dt, half_batch);
-    default: return pick_dt<ALG, 2>(dt, half_batch);
+    case ZIG_L64X128MIX: return pick_dt<ALG, 2>(dt, half_batch);
+    default: return pick_dt<ALG, 3>(dt, half_batch);
     }
 }
 static GenFn pick(int alg, int prng, int dt, bool half_batch = false) {
@@ -1173,7 +1186,8 @@ static_assert(z128_fits<GenLcg48, ZIG_F64>() && z128_fits<GenLcg48, ZIG_F32>() &
                   z128_fits<GenLcg48, ZIG_BF16>() && z128_fits<GenSplitMix64, ZIG_F64>() &&
                   z128_fits<GenSplitMix64, ZIG_F32>() && z128_fits<GenSplitMix64, ZIG_BF16>() &&
                   z128_fits<GenL64X128Mix, ZIG_F64>() && z128_fits<GenL64X128Mix, ZIG_F32>() &&
-                  z128_fits<GenL64X128Mix, ZIG_BF16>(),
+                  z128_fits<GenL64X128Mix, ZIG_BF16>() && z128_fits<GenXoroshiro128PP, ZIG_F64>() &&
+                  z128_fits<GenXoroshiro128PP, ZIG_F32>() && z128_fits<GenXoroshiro128PP, ZIG_BF16>(),
               "z128_kernel shared memory exceeds 227 KB per block");
 
 // Exactly the per-warp bytes the kernel instantiation for (G, dt, batch width)
@@ -1194,7 +1208,8 @@ static size_t dyn_smem_of(int alg, int dt, int prng, bool half_batch = false, in
     const int warps = block / 32;
     return prng == ZIG_LCG48 ? z128_dyn_for<GenLcg48>(dt, half_batch, warps)
          : prng == ZIG_SPLITMIX64 ? z128_dyn_for<GenSplitMix64>(dt, half_batch, warps)
-                                  : z128_dyn_for<GenL64X128Mix>(dt, half_batch, warps);
+         : prng == ZIG_L64X128MIX ? z128_dyn_for<GenL64X128Mix>(dt, half_batch, warps)
+                                  : z128_dyn_for<GenXoroshiro128PP>(dt, half_batch, warps);
 }
 
 // ---- launch configuration of the 128-level generation kernel ----
@@ -1204,8 +1219,8 @@ static size_t dyn_smem_of(int alg, int dt, int prng, bool half_batch = false, in
 struct LaunchCfg {
     uint32_t block, batch, store_bytes;
 };
-static LaunchCfg g_cfg[kMaxDevices][3][3][2];
-static bool g_cfg_set[kMaxDevices][3][3][2];
+static LaunchCfg g_cfg[kMaxDevices][4][3][2];
+static bool g_cfg_set[kMaxDevices][4][3][2];
 
 static uint32_t default_batch(int dt) { return dt == ZIG_F64 ? 16u : 32u; }
 static LaunchCfg default_cfg(int dt) { return LaunchCfg{(uint32_t)kZBlock, default_batch(dt), 0u}; }
@@ -1335,7 +1350,7 @@ static zig_status generate_impl(zig_prng prng, zig_alg alg, const uint64_t* seed
                                 const uint64_t* lengths_dev, uint64_t uniform_len, uint64_t n_streams,
                                 uint32_t chunk_log2, zig_dtype dtype, void* out_dev, void* workspace_dev,
                                 size_t workspace_bytes, void* stream, const LaunchCfg* force) {
-    if ((unsigned)prng > 2u || (unsigned)alg > 2u || (unsigned)dtype > 2u) return ZIG_ERR_INVALID_ARG;
+    if ((unsigned)prng > 3u || (unsigned)alg > 2u || (unsigned)dtype > 2u) return ZIG_ERR_INVALID_ARG;
     if (chunk_log2 != 0 && (chunk_log2 < 4 || chunk_log2 > 24)) return ZIG_ERR_INVALID_ARG;
     if (n_streams == 0) return ZIG_OK;
     // out_dev may be NULL only with lengths_dev (an all-zero batch); the kernel
@@ -1409,7 +1424,7 @@ zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
 
 zig_status zig_launch_config_get(int device, zig_prng prng, zig_dtype dtype, int variable_lengths,
                                  zig_launch_config* cfg) {
-    if (device < 0 || device >= host::kMaxDevices || (unsigned)prng > 2u || (unsigned)dtype > 2u || !cfg)
+    if (device < 0 || device >= host::kMaxDevices || (unsigned)prng > 3u || (unsigned)dtype > 2u || !cfg)
         return ZIG_ERR_INVALID_ARG;
     const host::LaunchCfg c = host::cfg_of(device, prng, dtype, variable_lengths != 0);
     cfg->block = c.block;
@@ -1421,7 +1436,7 @@ zig_status zig_launch_config_get(int device, zig_prng prng, zig_dtype dtype, int
 
 zig_status zig_launch_config_set(int device, zig_prng prng, zig_dtype dtype, int variable_lengths,
                                  const zig_launch_config* cfg) {
-    if (device < 0 || device >= host::kMaxDevices || (unsigned)prng > 2u || (unsigned)dtype > 2u)
+    if (device < 0 || device >= host::kMaxDevices || (unsigned)prng > 3u || (unsigned)dtype > 2u)
         return ZIG_ERR_INVALID_ARG;
     const int v = variable_lengths ? 1 : 0;
     std::lock_guard<std::mutex> lk(host::g_mu);
@@ -1453,7 +1468,7 @@ zig_status zig_autotune(zig_prng prng, const uint64_t* seeds_dev, const uint64_t
                         uint64_t uniform_len, uint64_t n_streams, uint32_t chunk_log2, zig_dtype dtype,
                         void* out_dev, void* workspace_dev, size_t workspace_bytes, uint32_t reps,
                         zig_launch_config* best, float* best_ms, void* stream) {
-    if ((unsigned)prng > 2u || (unsigned)dtype > 2u || reps == 0 || reps > 1000) return ZIG_ERR_INVALID_ARG;
+    if ((unsigned)prng > 3u || (unsigned)dtype > 2u || reps == 0 || reps > 1000) return ZIG_ERR_INVALID_ARG;
     int dev;
     zig_status st = host::current_device(dev);
     if (st != ZIG_OK) return st;
@@ -1502,7 +1517,7 @@ zig_status zig_autotune(zig_prng prng, const uint64_t* seeds_dev, const uint64_t
 
 zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_t seed,
                       zig_prng prng, void* stream) {
-    if ((unsigned)prng > 2u || !std::isfinite(sigma)) return ZIG_ERR_INVALID_ARG;
+    if ((unsigned)prng > 3u || !std::isfinite(sigma)) return ZIG_ERR_INVALID_ARG;
     if (P == 0 || L == 0) return ZIG_OK;
     if (!x_dev || ((uintptr_t)x_dev) % 4 || L > (1ull << 40) || P > (1ull << 40) / L)
         return ZIG_ERR_INVALID_ARG;
@@ -1525,7 +1540,8 @@ zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_
     GenArgs am = a;
     host::GenFn fn = prng == ZIG_LCG48 ? z128_kernel<0, ZIG_F32, 1>
                    : prng == ZIG_SPLITMIX64 ? z128_kernel<1, ZIG_F32, 1>
-                                            : z128_kernel<2, ZIG_F32, 1>;
+                   : prng == ZIG_L64X128MIX ? z128_kernel<2, ZIG_F32, 1>
+                                            : z128_kernel<3, ZIG_F32, 1>;
     am.mut_seed = seed;
     const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32, prng);
     if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
@@ -1538,7 +1554,7 @@ size_t zig_mutate_batch_desc_bytes(uint32_t n_req) { return (size_t)n_req * size
 
 zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_prng prng, void* desc_dev,
                             size_t desc_bytes, void* stream) {
-    if ((unsigned)prng > 2u) return ZIG_ERR_INVALID_ARG;
+    if ((unsigned)prng > 3u) return ZIG_ERR_INVALID_ARG;
     if (n_req == 0) return ZIG_OK;
     if (!reqs_host || !desc_dev || desc_bytes < zig_mutate_batch_desc_bytes(n_req) ||
         ((uintptr_t)desc_dev) % 16)
@@ -1578,7 +1594,8 @@ zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_p
     a.chunk_log2 = 10;
     host::GenFn fn = prng == ZIG_LCG48 ? z128_kernel<0, ZIG_F32, 2>
                    : prng == ZIG_SPLITMIX64 ? z128_kernel<1, ZIG_F32, 2>
-                                            : z128_kernel<2, ZIG_F32, 2>;
+                   : prng == ZIG_L64X128MIX ? z128_kernel<2, ZIG_F32, 2>
+                                            : z128_kernel<3, ZIG_F32, 2>;
     const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32, prng);
     if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
     int grid = host::grid_for((const void*)fn, dev, (units + 31) / 32, dyn, kZBlock);
@@ -1588,7 +1605,7 @@ zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_p
 
 zig_status zig_prng_fill(zig_prng prng, const uint64_t* seeds_dev, uint64_t n_streams, uint64_t n,
                          uint64_t skip, int kind, uint64_t* out_dev, void* stream) {
-    if ((unsigned)prng > 2u || kind < 0 || kind > 2) return ZIG_ERR_INVALID_ARG;
+    if ((unsigned)prng > 3u || kind < 0 || kind > 2) return ZIG_ERR_INVALID_ARG;
     if (n_streams == 0 || n == 0) return ZIG_OK;
     if (!seeds_dev || !out_dev || n_streams > (1ull << 40) / n) return ZIG_ERR_INVALID_ARG;
     int dev;
@@ -1598,7 +1615,8 @@ zig_status zig_prng_fill(zig_prng prng, const uint64_t* seeds_dev, uint64_t n_st
     unsigned grid = (unsigned)((n_streams + 255) / 256);
     if (prng == ZIG_LCG48) prng_fill_kernel<0><<<grid, 256, 0, s>>>(seeds_dev, n_streams, n, skip, kind, out_dev);
     else if (prng == ZIG_SPLITMIX64) prng_fill_kernel<1><<<grid, 256, 0, s>>>(seeds_dev, n_streams, n, skip, kind, out_dev);
-    else prng_fill_kernel<2><<<grid, 256, 0, s>>>(seeds_dev, n_streams, n, skip, kind, out_dev);
+    else if (prng == ZIG_L64X128MIX) prng_fill_kernel<2><<<grid, 256, 0, s>>>(seeds_dev, n_streams, n, skip, kind, out_dev);
+    else prng_fill_kernel<3><<<grid, 256, 0, s>>>(seeds_dev, n_streams, n, skip, kind, out_dev);
     return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
 }
 
@@ -1680,7 +1698,7 @@ extern "C" zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uin
                                            const uint64_t* lengths_dev, uint64_t n_streams,
                                            uint32_t chunk_log2, zig_dtype dtype, void* out_dev,
                                            void* stream) {
-    if ((unsigned)prng > 2u || (unsigned)alg > 2u || (unsigned)dtype > 2u) return ZIG_ERR_INVALID_ARG;
+    if ((unsigned)prng > 3u || (unsigned)alg > 2u || (unsigned)dtype > 2u) return ZIG_ERR_INVALID_ARG;
     if (chunk_log2 != 0 && (chunk_log2 < 4 || chunk_log2 > 24)) return ZIG_ERR_INVALID_ARG;
     if (n_streams == 0) return ZIG_OK;
     if (n_streams > ZIG_NOALLOC_MAX_STREAMS) return ZIG_ERR_TOO_LARGE;

@@ -183,7 +183,7 @@ extern "C" {
 
 zig_status zig_server_create(int device, zig_prng prng, uint64_t budget_bytes, uint32_t n_slots,
                              uint32_t max_batch, zig_server** out) {
-    if (!out || (unsigned)prng > 2u || budget_bytes == 0 || n_slots == 0 || n_slots > 64 ||
+    if (!out || (unsigned)prng > 3u || budget_bytes == 0 || n_slots == 0 || n_slots > 64 ||
         max_batch == 0 || max_batch > (1u << 20))
         return ZIG_ERR_INVALID_ARG;
     *out = nullptr;

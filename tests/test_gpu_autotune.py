@@ -48,7 +48,7 @@ def run(Z, prng, dtype, seeds, lengths, uniform_len, chunk_log2, cfg):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
-@pytest.mark.parametrize("prng", ["lcg48", "splitmix64", "l64x128mix"])
+@pytest.mark.parametrize("prng", ["lcg48", "splitmix64", "l64x128mix", "xoroshiro128pp"])
 def test_every_candidate_gives_the_default_outputs(Z, prng, dtype):
     L = W.batched_lengths(400, seed=7, max_log2=13)
     L[::11] = 0

@@ -16,7 +16,7 @@ from tests.parity import compare_streams, offsets_of
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PRNGS = ["lcg48", "splitmix64", "l64x128mix"]
+PRNGS = ["lcg48", "splitmix64", "l64x128mix", "xoroshiro128pp"]
 
 
 @pytest.fixture(scope="module")

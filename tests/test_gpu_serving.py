@@ -37,7 +37,7 @@ def _alone(Z, reqs, pops, prng):
     return outs
 
 
-@pytest.mark.parametrize("prng", ["lcg48", "splitmix64", "l64x128mix"])
+@pytest.mark.parametrize("prng", ["lcg48", "splitmix64", "l64x128mix", "xoroshiro128pp"])
 def test_mutate_batch_equals_alone(Z, prng):
     reqs, pops = _requests(37, 5)
     alone = _alone(Z, reqs, pops, prng)

@@ -209,6 +209,46 @@ def test_xoroshiro128_primitive():
         assert _pmod_pow_x(order // q, p, 128) != 1
 
 
+def test_xoroshiro128pp_engine_primitive():
+    # the (49, 21, 28) engine has a primitive degree-128 characteristic
+    # polynomial (full period 2^128 - 1); a wrong rotation or shift constant
+    # almost surely breaks this
+    g = O.Generator("xoroshiro128pp", 2024)
+    seq = []
+    for _ in range(400):
+        g.next_u64()
+        seq.append(g.state()[2] & 1)  # bit 0 of x0
+    L, c = _berlekamp_massey(seq)
+    assert L == 128
+    p = 0
+    for i in range(L + 1):
+        if (c >> i) & 1:
+            p |= 1 << (L - i)
+    order = (1 << 128) - 1
+    factors = [3, 5, 17, 257, 641, 65537, 274177, 6700417, 67280421310721]
+    assert _pmod_pow_x(order, p, 128) == 1
+    for q in factors:
+        assert _pmod_pow_x(order // q, p, 128) != 1
+
+
+def test_xoroshiro128pp_output_is_a_function_of_the_state_before_the_step():
+    # nextLong's ++ scrambler reads (x0, x1) before the linear step: two
+    # generators with equal states give equal outputs, and the output is not
+    # a linear function of the state (its lowest bit is x0 + x1 + x0 with carries)
+    g = O.Generator("xoroshiro128pp", 5)
+    st = g.state()
+    a = g.next_u64()
+    h = O.Generator("xoroshiro128pp", 5)
+    assert h.state() == st and h.next_u64() == a
+    # bit 0 of rotl(x0 + x1, 17) + x0 is bit 47 of (x0 + x1) xor bit 0 of x0
+    bits = []
+    for _ in range(2000):
+        x0, x1 = g.state()[2], g.state()[3]
+        out = g.next_u64()
+        bits.append(((((x0 + x1) % (1 << 64)) >> 47) ^ x0) & 1 == out & 1)
+    assert all(bits)
+
+
 def test_lxm_lcg_low_bit_periods():
     # LXM's LCG s <- M s + a (mod 2^64), a odd: state bit b has period 2^(b+1)
     g = O.Generator("l64x128mix", 77)
