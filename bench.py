@@ -303,6 +303,7 @@ def run_gpu(args):
     line_extra["comparisons"] = compare_variants(Z, torch, seeds, stream, args)
     if rank == 0 and not args.no_precision:
         line_extra["precision"] = measure_precision(Z, torch, stream)
+        line_extra["lcg_low_bits"] = measure_lcg_low_bits(Z, torch, stream)
 
     # end to end through the public call: seeds from pinned host memory, result back to host
     e2e = measure_e2e(Z, torch, seeds_np, stream, args)
@@ -456,6 +457,31 @@ def measure_precision(Z, torch, stream, reps=3):
     return {"workload": "2^31 variates per dtype: 2^21 streams x 1,024, splitmix64, zig128, "
                         "seeds 0x5EED+s; binary32 tables on the fast path of f32/bf16",
             "dtypes": res}
+
+
+def measure_lcg_low_bits(Z, torch, stream):
+    """The modified and the original ziggurat over the 48-bit LCG and over SplitMix64:
+    2^16 streams x 4,096 binary64 variates each (seeds 0x5EED + s); KS against Phi and
+    the serial chi-square within streams at lags 1-3 (16 x 16 equal-probability cells).
+    Both transforms take their slot or layer from low bits of the draw (the modified
+    ziggurat the low byte of nextLong, the GSL form the low 7 bits of nextInt), which
+    for the LCG are state bits 16-23 with periods 2^17 to 2^24."""
+    from paper_2405_19493_gb300 import quality as Q
+    from paper_2405_19493_gb300 import workloads as W
+    n_s, L = 1 << 16, 4096
+    sd = torch.from_numpy(W.seeds(n_s).view(np.int64)).cuda()
+    o = torch.empty(n_s * L, dtype=torch.float64, device="cuda")
+    res = {}
+    for alg in ("zig256", "zig128"):
+        for prng in ("lcg48", "splitmix64"):
+            Z.zig_generate(prng, alg, sd, o, uniform_len=L, stream=stream)
+            torch.cuda.synchronize()
+            res[f"{alg}/{prng}"] = {
+                "ks_p": Q.ks_grid(torch, o, K=1 << 16)["p_value"],
+                "serial_p": [Q.serial_chi2(torch, o, L, lag=g)["p_value"] for g in (1, 2, 3)]}
+    del o
+    torch.cuda.empty_cache()
+    return {"workload": "2^16 streams x 4,096 binary64 variates, seeds 0x5EED+s", "results": res}
 
 
 def measure_serving(Z, torch, rates=(1000, 10000, 50000), n_req=1500, mixed_rate=10000,

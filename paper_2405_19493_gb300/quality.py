@@ -9,6 +9,8 @@ These are measurements of the library's outputs, not part of generation:
     functions on the bfloat16 values), plus the distance to Phi itself, which
     rounding alone keeps near density x half a bfloat16 spacing.
   - tail_mass: the fraction of |x| > t against P(|RN_dtype(Z)| > t).
+  - serial_chi2: independence of outputs `lag` apart within each stream: a chi-square
+    test on the pairs' cells in a k x k grid of equal-probability bins of Phi.
   - error_vs_f64: each narrow output against the binary64 output of the same
     streams: how many representable steps it lies from the nearest value
     RN_dtype(z64), and its distance from z64 in the narrow type's ulps.
@@ -131,3 +133,20 @@ def error_vs_f64(torch, x, z64, dtype: str, chunk: int = CHUNK) -> dict:
     return {"max_steps_from_nearest": max_steps, "max_err_ulp": worst,
             "outputs_not_nearest": not_nearest, "frac_not_nearest": not_nearest / max(n, 1),
             "mean_abs_err": total_abs / n, "max_rel_err": max_rel}
+
+
+def serial_chi2(torch, x, stream_len: int, lag: int = 1, k: int = 16) -> dict:
+    """x: packed stream-major outputs, streams of stream_len; pairs (x_t, x_{t+lag})
+    are taken within streams only."""
+    from scipy.special import ndtri
+    from scipy.stats import chi2 as chi2_dist
+    edges = torch.from_numpy(ndtri(np.arange(1, k, dtype=np.float64) / k)).to(x.device)
+    q = torch.bucketize(x.double().view(-1, stream_len), edges)          # (streams, len)
+    cells = (q[:, :-lag] * k + q[:, lag:]).reshape(-1)
+    counts = torch.bincount(cells, minlength=k * k).double()
+    n = counts.sum()
+    expect = n / (k * k)
+    stat = float(((counts - expect) ** 2 / expect).sum().item())
+    dof = k * k - 1
+    return {"lag": lag, "cells": k * k, "pairs": int(n.item()), "chi2": stat, "dof": dof,
+            "p_value": float(chi2_dist.sf(stat, dof))}

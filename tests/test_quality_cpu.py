@@ -69,3 +69,16 @@ def test_round_to_precision_is_one_rounding():
     got = Q.round_to_precision(torch, z, 8).tolist()
     assert got == [1 + 2.0 ** -7, -(1 + 2.0 ** -7), 1.0, 1 + 4 * 2.0 ** -8, 2.5]
     assert z.float().to(torch.bfloat16)[0].item() == 1.0
+
+
+def test_serial_chi2_sees_dependence_within_streams():
+    x = normals(1 << 20, seed=6)
+    r = Q.serial_chi2(torch, x, stream_len=1 << 10, lag=1)
+    assert r["p_value"] > 1e-4 and r["pairs"] == (1 << 10) * ((1 << 10) - 1)
+    # an AR(1) sequence with correlation 0.05 is flagged
+    a = np.empty(1 << 20)
+    z = np.random.default_rng(7).standard_normal(1 << 20)
+    a[0] = z[0]
+    for t in range(1, len(a)):
+        a[t] = 0.05 * a[t - 1] + np.sqrt(1 - 0.05 ** 2) * z[t]
+    assert Q.serial_chi2(torch, torch.from_numpy(a), stream_len=1 << 10, lag=1)["p_value"] < 1e-10
