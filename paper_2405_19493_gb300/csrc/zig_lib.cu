@@ -1360,10 +1360,13 @@ static zig_status generate_impl(zig_prng prng, zig_alg alg, const uint64_t* seed
     if (((uintptr_t)out_dev) % esz || ((uintptr_t)seeds_dev) % 8) return ZIG_ERR_INVALID_ARG;
     if (lengths_dev == nullptr) {
         if (uniform_len == 0) return ZIG_OK;
-        if (uniform_len > (1ull << 40) || n_streams > (1ull << 40) / uniform_len)
+        if (uniform_len >= (1ull << 40) || n_streams > ((1ull << 40) - 1) / uniform_len)
             return ZIG_ERR_INVALID_ARG;
     } else if (((uintptr_t)lengths_dev) % 8 || n_streams > (1ull << 32)) {
         return ZIG_ERR_INVALID_ARG;
+    } else if (workspace_dev && (workspace_bytes < zig_generate_workspace_bytes(n_streams) ||
+                                 ((uintptr_t)workspace_dev) % 16)) {
+        return ZIG_ERR_INVALID_ARG;   // a caller workspace that cannot hold the scratch
     }
     int dev;
     zig_status st = host::current_device(dev);
@@ -1519,7 +1522,7 @@ zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_
                       zig_prng prng, void* stream) {
     if ((unsigned)prng > 3u || !std::isfinite(sigma)) return ZIG_ERR_INVALID_ARG;
     if (P == 0 || L == 0) return ZIG_OK;
-    if (!x_dev || ((uintptr_t)x_dev) % 4 || L > (1ull << 40) || P > (1ull << 40) / L)
+    if (!x_dev || ((uintptr_t)x_dev) % 4 || L >= (1ull << 40) || P > ((1ull << 40) - 1) / L)
         return ZIG_ERR_INVALID_ARG;
     int dev;
     zig_status st = host::current_device(dev);
@@ -1565,7 +1568,7 @@ zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_p
         const zig_mutation& q = reqs_host[r];
         if (q.kind > ZIG_REQ_GENERATE || (q.kind == ZIG_REQ_MUTATE && !std::isfinite(q.sigma)) ||
             (q.P && q.L && (!q.x_dev || ((uintptr_t)q.x_dev) % 4)) ||
-            q.L > (1ull << 40) || (q.L && q.P > (1ull << 40) / q.L))
+            q.L >= (1ull << 40) || (q.L && q.P > ((1ull << 40) - 1) / q.L))
             return ZIG_ERR_INVALID_ARG;
         d[r].x = q.x_dev;
         d[r].P = q.P;

@@ -226,7 +226,7 @@ namespace {
 zig_status submit(zig_server* S, float* x_dev, uint64_t P, uint64_t L, float sigma, uint32_t kind,
                   uint64_t seed, uint64_t* ticket) {
     if (!S || !ticket || (kind == ZIG_REQ_MUTATE && !std::isfinite(sigma)) || (P && L && !x_dev) ||
-        (L && P > (1ull << 40) / L))
+        (L && P > ((1ull << 40) - 1) / L))
         return ZIG_ERR_INVALID_ARG;
     const uint64_t bytes = P * L * sizeof(float);
     std::lock_guard<std::mutex> lk(S->mu);

@@ -99,3 +99,40 @@ def test_launch_config_validation_and_candidates():
     assert Z.zig_launch_config_get("l64x128mix", "f64", False, device=5)["block"] == 768
     Z.zig_launch_config_set("l64x128mix", "f64", True, None, device=5)
     assert Z.zig_launch_config_get("l64x128mix", "f64", True, device=5)["batch"] == 16
+
+
+def test_more_host_side_argument_errors():
+    """Limits and malformed requests are refused on the host, before any device call."""
+    lib = Z.load()
+    INVALID, TOO_LARGE = 1, 8
+    P = 0x1000   # an aligned non-null stand-in pointer: never dereferenced on these paths
+    # generators beyond the fourth, chunk sizes outside 4..24
+    assert lib.zig_generate(4, 0, P, None, 16, 4, 0, 0, P, None, 0, None) == INVALID
+    assert lib.zig_generate(0, 0, P, None, 16, 4, 3, 0, P, None, 0, None) == INVALID
+    # the output must be aligned to its element size
+    assert lib.zig_generate(0, 0, P, None, 16, 4, 0, 0, P + 4, None, 0, None) == INVALID
+    assert lib.zig_generate(0, 0, P, None, 16, 4, 0, 1, P + 2, None, 0, None) == INVALID
+    # uniform requests of 2^40 elements or more
+    assert lib.zig_generate(0, 0, P, None, 1 << 40, 2, 0, 0, P, None, 0, None) == INVALID
+    assert lib.zig_generate(0, 0, P, None, (1 << 39) + 1, 2, 0, 0, P, None, 0, None) == INVALID
+    # variable-length requests of more than 2^32 streams
+    assert lib.zig_generate(0, 0, P, P, 0, (1 << 32) + 1, 0, 0, P, None, 0, None) == INVALID
+    # a too small or misaligned caller workspace
+    assert lib.zig_generate(0, 0, P, P, 0, 100, 0, 0, P, P, 16, None) == INVALID
+    # the no-allocation path refuses batches beyond its fixed scratch first
+    assert lib.zig_generate_noalloc(0, 0, P, P, B.NOALLOC_MAX_STREAMS + 1, 0, 0, P, None) == TOO_LARGE
+    assert lib.zig_generate_noalloc(0, 0, None, P, 4, 0, 0, P, None) == INVALID
+    # mutation: population of 2^40 elements or more, misaligned rows
+    assert lib.zig_mutate(P, 0.5, 1 << 20, 1 << 20, 1, 0, None) == INVALID
+    assert lib.zig_mutate(P + 2, 0.5, 4, 4, 1, 0, None) == INVALID
+    # batches: an unknown request kind, a NaN sigma on a mutation, a too small descriptor area
+    reqs = (B.Mutation * 2)(B.Mutation(P, 4, 4, 0.5, 0, 1), B.Mutation(P, 4, 4, 0.5, 2, 2))
+    assert lib.zig_mutate_batch(reqs, 2, 0, P, 4096, None) == INVALID
+    reqs[1] = B.Mutation(P, 4, 4, float("nan"), 0, 2)
+    assert lib.zig_mutate_batch(reqs, 2, 0, P, 4096, None) == INVALID
+    reqs[1] = B.Mutation(P, 4, 4, float("nan"), 1, 2)   # generation ignores sigma
+    assert lib.zig_mutate_batch(reqs, 2, 0, P, 16, None) == INVALID   # descriptor area too small
+    # autotuner and self-check arguments
+    assert lib.zig_autotune(0, P, None, 16, 4, 0, 0, P, None, 0, 0, None, None, None) == INVALID
+    assert lib.zig_autotune(0, P, None, 16, 4, 0, 0, P, None, 0, 1001, None, None, None) == INVALID
+    assert lib.zig_selfcheck(None) == INVALID
