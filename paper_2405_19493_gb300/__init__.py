@@ -1,11 +1,13 @@
 """GB300-native bulk N(0,1) generation: the original 128-level ziggurat (GSL
-form) over per-stream java.util.Random / SplitMix64 / L64X128Mix generators, with
-the polar method and a 256-slot modified ziggurat as comparison transforms.
+form) over per-stream java.util.Random / SplitMix64 / L64X128Mix /
+Xoroshiro128PlusPlus generators, with the polar method and a 256-slot modified
+ziggurat as comparison transforms.
 
 The compute lives in libzig_gb300.so (CUDA, sm_103a) behind the C ABI in
 include/zig.h; this package only builds and binds it (``_binding``), plus the
-seeded synthetic workloads (``workloads``) and the request loop for Gaussian
-mutation (``serving``).
+seeded synthetic workloads (``workloads``), the request loop for Gaussian
+mutation and generation (``serving``), and distribution checks of outputs
+(``quality``).
 """
 
 from ._binding import (  # noqa: F401
