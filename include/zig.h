@@ -344,12 +344,14 @@ const char *zig_status_string(zig_status status);
  * the kernel's fused multiply-add construction for every abscissa j < 2^24 of
  * every layer i < 128 and compares it with IEEE multiplication (__dmul_rn), and
  * rounds every finite binary32 bit pattern to bfloat16 by the kernel's routine
- * and compares it with __float2bfloat16_rn.  Writes counts_host[0] = product
- * mismatches, [1] = bfloat16 mismatches, [2] = products checked (2^31),
- * [3] = patterns checked.  Synchronous; allocates 32 bytes of device memory for
- * the call.  ZIG_ERR_NOT_INITIALIZED without zig_tables_init.
+ * and compares it with __float2bfloat16_rn, and compares the tail step's own
+ * binary64 log with CUDA's log on 2^31 uniforms in (0, 1).  Writes
+ * counts_host[0] = product mismatches, [1] = bfloat16 mismatches, [2] = products
+ * checked (2^31), [3] = patterns checked, [4] = logs more than one ulp from
+ * CUDA's, [5] = logs not equal to CUDA's.  Synchronous; allocates 48 bytes of
+ * device memory for the call.  ZIG_ERR_NOT_INITIALIZED without zig_tables_init.
  */
-zig_status zig_selfcheck(uint64_t counts_host[4]);
+zig_status zig_selfcheck(uint64_t counts_host[6]);
 
 int zig_version(void);
 

@@ -318,6 +318,40 @@ def tables256():
             "ODY": ODY, "KIND": KIND, "QA": QA, "THR": THR, "ALIAS": alias}
 
 
+# ---- natural logarithm tables (P. T. P. Tang's table-driven method, 1990) -------------
+# ln x = e ln2 + ln F_k + ln(1 + r) for x = 2^e m, F_k = 1 + k/128 the table point
+# nearest m (k = 0..128) and r = (m - F_k)/F_k.  Stored: G_k = RN(1/F_k), and
+# ln F_k and ln 2 split as hi + lo with hi on the grid 2^-40, so that e * LN2_HI +
+# LOG_THI[k] is exact in binary64 for |e| < 2^10 (at most 50 significant bits).
+
+def _ln(x: Decimal) -> Decimal:
+    return x.ln()
+
+
+def _grid(x: Decimal, step_log2: int) -> Decimal:
+    """x rounded to the nearest multiple of 2^-step_log2 (ties to even multiple)."""
+    q = x * (TWO ** step_log2)
+    n = int(q.to_integral_value(rounding=ROUND_FLOOR))
+    frac = q - n
+    if frac > D("0.5") or (frac == D("0.5") and (n & 1)):
+        n += 1
+    return D(n) / (TWO ** step_log2)
+
+
+def tables_log():
+    ln2 = _ln(TWO)
+    ln2_hi = _grid(ln2, 40)
+    out = {"LN2_HI": rn64(ln2_hi), "LN2_LO": rn64(ln2 - ln2_hi), "G": [], "THI": [], "TLO": []}
+    for k in range(129):
+        F = ONE + D(k) / 128
+        T = _ln(F)
+        t_hi = ln2_hi if k == 128 else _grid(T, 40)   # k = 128: exactly LN2_HI + LN2_LO
+        out["G"].append(rn64(ONE / F))
+        out["THI"].append(rn64(t_hi))
+        out["TLO"].append(rn64(T - t_hi) if k < 128 else out["LN2_LO"])
+    return out
+
+
 # ---- output -------------------------------------------------------------------------
 
 def _arr(ctype, name, vals, fmt, per_line=4):
@@ -331,6 +365,7 @@ def _arr(ctype, name, vals, fmt, per_line=4):
 def render() -> str:
     t = tables128()
     m = tables256()
+    lg = tables_log()
     hx = lambda v: v.hex()
     out = [
         "// Ziggurat tables for the CUDA library.  GENERATED by gen_tables.py "
@@ -338,6 +373,7 @@ def render() -> str:
         "// 128-level original ziggurat: K (u32), W (f64), Y (f64), W32 (f32); "
         "base layer = R f(R) + f(R)/R.",
         "// 256-slot modified ziggurat: rectangle widths, overhang boxes, alias table.",
+        "// Natural-logarithm tables for the tail step's binary64 log.",
         "#pragma once",
         "#include <stdint.h>",
         "namespace zigtab {",
@@ -359,6 +395,12 @@ def render() -> str:
         _arr("uint64_t", "ZIG256_QA", m["QA"], lambda v: f"{v}ull"),
         _arr("uint64_t", "ZIG256_THR", m["THR"], lambda v: f"{v}ull"),
         _arr("int", "ZIG256_ALIAS", m["ALIAS"], str, 16),
+        "// natural logarithm (Tang's table-driven method): F_k = 1 + k/128",
+        f"static const double LN2_HI = {hx(lg['LN2_HI'])};",
+        f"static const double LN2_LO = {hx(lg['LN2_LO'])};",
+        _arr("double", "LOG_G", lg["G"], hx, 3),
+        _arr("double", "LOG_THI", lg["THI"], hx, 3),
+        _arr("double", "LOG_TLO", lg["TLO"], hx, 3),
         "}  // namespace zigtab",
         "",
     ]

@@ -441,35 +441,78 @@ __device__ __forceinline__ bool z128_wedge_accept(const Z128Tab& t, uint32_t i, 
     return y < exp(neg_half_sq(x));
 }
 
+// Natural logarithm of a positive normal binary64 x, by P. T. P. Tang's
+// table-driven method (ACM TOMS 16(4), 1990), all inline (no call):
+// x = 2^e m with m in [1, 2); F = 1 + k/128 is the table point nearest m;
+// r = (m - F)/F from f = m - F (exact) and G = RN(1/F), refined by one fused
+// multiply-add step; ln(1 + r) = r + r^2 q(r) with q the Taylor series to r^7
+// (|r| <= 2^-8, truncation below 2^-59 relative); and
+// ln x = (e ln2_hi + ln F_hi) + (r + (r^2 q + e ln2_lo + ln F_lo)), the first
+// sum exact (hi parts on the grid 2^-40).  Error about half an ulp;
+// zig_selfcheck compares it with CUDA's log.
+__constant__ double c_log_g[129], c_log_thi[129], c_log_tlo[129];
+
+__device__ __forceinline__ double zlog(double x) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const double e = (double)((int)(b >> 52) - 1023);
+    const uint64_t frac = b & ((1ull << 52) - 1);
+    const double m = __longlong_as_double((long long)(frac | (1023ull << 52)));
+    const int k = (int)(((frac >> 44) + 1) >> 1);                  // nearest k/128: 0..128
+    const double F = __dadd_rn(1.0, __dmul_rn((double)k, 0.0078125));   // exact
+    const double f = __dsub_rn(m, F);                               // exact
+    const double G = c_log_g[k];
+    double r = __dmul_rn(f, G);
+    r = __fma_rn(__fma_rn(-r, F, f), G, r);
+    double q = 1.0 / 7;
+    q = __fma_rn(q, r, -1.0 / 6);
+    q = __fma_rn(q, r, 1.0 / 5);
+    q = __fma_rn(q, r, -0.25);
+    q = __fma_rn(q, r, 1.0 / 3);
+    q = __fma_rn(q, r, -0.5);
+    const double hi = __fma_rn(e, zigtab::LN2_HI, c_log_thi[k]);   // exact
+    const double lo = __fma_rn(__dmul_rn(r, r), q, __fma_rn(e, zigtab::LN2_LO, c_log_tlo[k]));
+    return __dadd_rn(hi, __dadd_rn(r, lo));
+}
+
+// RN(z / R) without a division: q = RN(z RN(1/R)) and one fused multiply-add
+// correction, which gives the correctly rounded quotient (Markstein, IBM J. Res.
+// Dev. 34(1), 1990).
+__device__ __forceinline__ double div_by_R(double z) {
+    constexpr double R = zigtab::ZIG128_R;
+    constexpr double Rinv = 1.0 / zigtab::ZIG128_R;
+    const double q = __dmul_rn(z, Rinv);
+    return __fma_rn(__fma_rn(-q, R, z), Rinv, q);
+}
+
 // The tail test for U1 = 1 - m1 2^-53, U2 = m2 2^-53:
 // y = exp(-R (x - R/2)) U2 < exp(-x^2/2) with x = R + s, s = -ln(U1)/R, which is
 // ln U2 < -s^2/2 in exact arithmetic.  Decided in binary32 when that clears a
-// margin of 2^-14 (1 + s^2/2 + |ln U2|), far above the binary32 errors (< 1e-5
-// relative); otherwise the binary64 definition decides.
+// margin of 2^-14 (1 + s^2/2 + |ln U2|), far above the binary32 errors (the
+// hardware log2 within 2^-22.6 absolute on [0.5, 2] and 2 ulp elsewhere:
+// below 1e-5 relative here); otherwise ln U2 < -s^2/2 decides in binary64.  The
+// two tests agree except where the oracle's own rounding could flip its
+// decision (a margin near 1e-16).
 __device__ __forceinline__ bool z128_tail_accept(uint64_t m1, uint64_t m2) {
     if (m2 == 0) return true;                         // U2 = 0: y = 0 < exp(-x^2/2)
     const uint64_t n1 = (1ull << 53) - m1;            // U1 = n1 2^-53 in (0, 1]
-    const float s32 = -logf(m53_to_float(n1)) * (float)(1.0 / zigtab::ZIG128_R);
+    constexpr float kLn2 = 0.693147180559945309f;
+    constexpr float kLn2OverR = (float)(0.693147180559945309 / zigtab::ZIG128_R);
+    const float s32 = -__log2f(m53_to_float(n1)) * kLn2OverR;
     const float h32 = 0.5f * s32 * s32;
-    const float l32 = logf(m53_to_float(m2));
+    const float l32 = __log2f(m53_to_float(m2)) * kLn2;
     const float marg = 0x1p-14f * (1.0f + h32 - l32);
     if (l32 < -h32 - marg) return true;
     if (l32 > -h32 + marg) return false;
-    const double R = zigtab::ZIG128_R;
-    const double U1 = __dsub_rn(1.0, m53_to_double(m1));
-    const double U2 = m53_to_double(m2);
-    const double x = __dsub_rn(R, __ddiv_rn(log(U1), R));
-    const double y = __dmul_rn(exp(__dmul_rn(-R, __dsub_rn(x, __dmul_rn(0.5, R)))), U2);
-    return y < exp(neg_half_sq(x));
+    const double s = -div_by_R(zlog(m53_to_double(n1)));
+    return zlog(m53_to_double(m2)) < __dmul_rn(__dmul_rn(-0.5, s), s);
 }
 
-// The tail step, kept out of line so that its binary64 math does not raise the
-// register pressure of the draw loop: the accepted x, or -1 if rejected.
-__device__ __noinline__ double z128_tail(uint64_t m1, uint64_t m2) {
+// The tail step, inline and free of calls: the accepted x = R - ln(U1)/R, or -1
+// if rejected.
+__device__ __forceinline__ double z128_tail(uint64_t m1, uint64_t m2) {
     if (!z128_tail_accept(m1, m2)) return -1.0;
-    const double R = zigtab::ZIG128_R;
     const double U1 = __dsub_rn(1.0, m53_to_double(m1));
-    return __dsub_rn(R, __ddiv_rn(log(U1), R));
+    return __dsub_rn(zigtab::ZIG128_R, div_by_R(zlog(U1)));
 }
 
 // Staging word per slot: binary64 bits, or binary32 bits (binary32 and bfloat16
@@ -933,16 +976,22 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
 // Exhaustive check of the fast path's arithmetic against CUDA's IEEE operations:
 // RN(j * w[i]) by the fused multiply-add construction against __dmul_rn for all
 // 2^24 abscissae j of all 128 layers, and the bfloat16 rounding of every finite
-// binary32 pattern against __float2bfloat16_rn.  counts: product mismatches,
-// bfloat16 mismatches, products checked, patterns checked.
+// binary32 pattern against __float2bfloat16_rn.  Also the tail step's log
+// against CUDA's log on 2^31 uniforms spread over (0, 1].  counts: product
+// mismatches, bfloat16 mismatches, products checked, patterns checked, logs more
+// than one ulp from CUDA's, logs not equal to CUDA's.
 __global__ void __launch_bounds__(256) selfcheck_kernel(unsigned long long* counts) {
-    unsigned long long bad_p = 0, bad_b = 0, n_p = 0, n_b = 0;
+    unsigned long long bad_p = 0, bad_b = 0, n_p = 0, n_b = 0, far_l = 0, ne_l = 0;
     const uint64_t n = 1ull << 31;
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t i = (uint32_t)(k >> 24), j = (uint32_t)k & 0xFFFFFFu;
         const double w = d_z128_W[i];
         bad_p += mul_j_w_fma(j, w) != (uint64_t)__double_as_longlong(__dmul_rn((double)j, w));
         ++n_p;
+        const double u = m53_to_double(((k * 0x9E3779B97F4A7C15ull) >> 11) | 1u);   // in (0, 1)
+        const long long dl = __double_as_longlong(zlog(u)) - __double_as_longlong(log(u));
+        far_l += dl > 1 || dl < -1;
+        ne_l += dl != 0;
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h) {
             const float f = __uint_as_float((uint32_t)k | (h << 31));
@@ -956,6 +1005,8 @@ __global__ void __launch_bounds__(256) selfcheck_kernel(unsigned long long* coun
     atomicAdd(&counts[1], bad_b);
     atomicAdd(&counts[2], n_p);
     atomicAdd(&counts[3], n_b);
+    atomicAdd(&counts[4], far_l);
+    atomicAdd(&counts[5], ne_l);
 }
 
 // Exclusive prefix sums of lengths and unit counts (one block).
@@ -1110,6 +1161,9 @@ static zig_status init_device(int device) {
         dy32[i] = i < 127 ? (float)(zigtab::ZIG128_Y[i] - zigtab::ZIG128_Y[i + 1]) : 0.0f;
     }
     ZIG_CUDA(cudaMemcpyToSymbol(d_z128_Y32, y32, sizeof(y32)));
+    ZIG_CUDA(cudaMemcpyToSymbol(c_log_g, zigtab::LOG_G, sizeof(zigtab::LOG_G)));
+    ZIG_CUDA(cudaMemcpyToSymbol(c_log_thi, zigtab::LOG_THI, sizeof(zigtab::LOG_THI)));
+    ZIG_CUDA(cudaMemcpyToSymbol(c_log_tlo, zigtab::LOG_TLO, sizeof(zigtab::LOG_TLO)));
     ZIG_CUDA(cudaMemcpyToSymbol(d_z128_DY32, dy32, sizeof(dy32)));
     const int nr = zigtab::ZIG256_NR;
     double xs[256] = {0};
@@ -1660,19 +1714,19 @@ const char* zig_status_string(zig_status status) {
 
 int zig_version(void) { return 100; }
 
-zig_status zig_selfcheck(uint64_t counts_host[4]) {
+zig_status zig_selfcheck(uint64_t counts_host[6]) {
     if (!counts_host) return ZIG_ERR_INVALID_ARG;
     int dev;
     zig_status st = host::current_device(dev);
     if (st != ZIG_OK) return st;
     unsigned long long* d = nullptr;
-    ZIG_CUDA(cudaMalloc(&d, 4 * sizeof(unsigned long long)));
+    ZIG_CUDA(cudaMalloc(&d, 6 * sizeof(unsigned long long)));
     st = ZIG_OK;
-    if (cudaMemset(d, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) st = ZIG_ERR_CUDA;
+    if (cudaMemset(d, 0, 6 * sizeof(unsigned long long)) != cudaSuccess) st = ZIG_ERR_CUDA;
     if (st == ZIG_OK) {
         selfcheck_kernel<<<host::g_sms[dev] * 8, 256>>>(d);
         if (cudaGetLastError() != cudaSuccess ||
-            cudaMemcpy(counts_host, d, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            cudaMemcpy(counts_host, d, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
             st = ZIG_ERR_CUDA;
     }
     cudaFree(d);
