@@ -125,6 +125,39 @@ __device__ __forceinline__ double neg_half_sq(double x) {
 }
 
 // Polar method with the cached second variate.
+// Natural logarithm of a positive normal binary64 x, by P. T. P. Tang's
+// table-driven method (ACM TOMS 16(4), 1990), all inline (no call):
+// x = 2^e m with m in [1, 2); F = 1 + k/128 is the table point nearest m;
+// r = (m - F)/F from f = m - F (exact) and G = RN(1/F), refined by one fused
+// multiply-add step; ln(1 + r) = r + r^2 q(r) with q the Taylor series to r^7
+// (|r| <= 2^-8, truncation below 2^-59 relative); and
+// ln x = (e ln2_hi + ln F_hi) + (r + (r^2 q + e ln2_lo + ln F_lo)), the first
+// sum exact (hi parts on the grid 2^-40).  Error about half an ulp;
+// zig_selfcheck compares it with CUDA's log.
+__constant__ double c_log_g[129], c_log_thi[129], c_log_tlo[129];
+
+__device__ __forceinline__ double zlog(double x) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const double e = (double)((int)(b >> 52) - 1023);
+    const uint64_t frac = b & ((1ull << 52) - 1);
+    const double m = __longlong_as_double((long long)(frac | (1023ull << 52)));
+    const int k = (int)(((frac >> 44) + 1) >> 1);                  // nearest k/128: 0..128
+    const double F = __dadd_rn(1.0, __dmul_rn((double)k, 0.0078125));   // exact
+    const double f = __dsub_rn(m, F);                               // exact
+    const double G = c_log_g[k];
+    double r = __dmul_rn(f, G);
+    r = __fma_rn(__fma_rn(-r, F, f), G, r);
+    double q = 1.0 / 7;
+    q = __fma_rn(q, r, -1.0 / 6);
+    q = __fma_rn(q, r, 1.0 / 5);
+    q = __fma_rn(q, r, -0.25);
+    q = __fma_rn(q, r, 1.0 / 3);
+    q = __fma_rn(q, r, -0.5);
+    const double hi = __fma_rn(e, zigtab::LN2_HI, c_log_thi[k]);   // exact
+    const double lo = __fma_rn(__dmul_rn(r, r), q, __fma_rn(e, zigtab::LN2_LO, c_log_tlo[k]));
+    return __dadd_rn(hi, __dadd_rn(r, lo));
+}
+
 template <class G>
 __device__ __forceinline__ double polar_f64(G& g, bool& have, double& cached, uint32_t& extra) {
     if (have) {
@@ -139,7 +172,7 @@ __device__ __forceinline__ double polar_f64(G& g, bool& have, double& cached, ui
         s = __dadd_rn(__dmul_rn(v1, v1), __dmul_rn(v2, v2));
         extra += 2 * kStepsPerDouble;
     } while (s >= 1.0 || s == 0.0);
-    double mult = __dsqrt_rn(__ddiv_rn(__dmul_rn(-2.0, log(s)), s));
+    double mult = __dsqrt_rn(__ddiv_rn(__dmul_rn(-2.0, zlog(s)), s));
     cached = __dmul_rn(v2, mult);
     have = true;
     return __dmul_rn(v1, mult);
@@ -200,8 +233,8 @@ __device__ __forceinline__ double z256_slow(G& g, const Z256Smem& t, uint32_t& e
             double U1 = __dsub_rn(1.0, m53_to_double(g.next_m53()));
             double U2 = __dsub_rn(1.0, m53_to_double(g.next_m53()));
             extra += 2 * kStepsPerDouble;
-            double x = __ddiv_rn(-log(U1), x0);
-            double y = -log(U2);
+            double x = __ddiv_rn(-zlog(U1), x0);
+            double y = -zlog(U2);
             if (__dadd_rn(y, y) > __dmul_rn(x, x)) return __dadd_rn(x0, x);
         }
     }
@@ -439,39 +472,6 @@ __device__ __forceinline__ bool z128_wedge_accept(const Z128Tab& t, uint32_t i, 
     const double U = m53_to_double(m1);
     const double y = __dadd_rn(t.Y[i + 1], __dmul_rn(__dsub_rn(t.Y[i], t.Y[i + 1]), U));
     return y < exp(neg_half_sq(x));
-}
-
-// Natural logarithm of a positive normal binary64 x, by P. T. P. Tang's
-// table-driven method (ACM TOMS 16(4), 1990), all inline (no call):
-// x = 2^e m with m in [1, 2); F = 1 + k/128 is the table point nearest m;
-// r = (m - F)/F from f = m - F (exact) and G = RN(1/F), refined by one fused
-// multiply-add step; ln(1 + r) = r + r^2 q(r) with q the Taylor series to r^7
-// (|r| <= 2^-8, truncation below 2^-59 relative); and
-// ln x = (e ln2_hi + ln F_hi) + (r + (r^2 q + e ln2_lo + ln F_lo)), the first
-// sum exact (hi parts on the grid 2^-40).  Error about half an ulp;
-// zig_selfcheck compares it with CUDA's log.
-__constant__ double c_log_g[129], c_log_thi[129], c_log_tlo[129];
-
-__device__ __forceinline__ double zlog(double x) {
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const double e = (double)((int)(b >> 52) - 1023);
-    const uint64_t frac = b & ((1ull << 52) - 1);
-    const double m = __longlong_as_double((long long)(frac | (1023ull << 52)));
-    const int k = (int)(((frac >> 44) + 1) >> 1);                  // nearest k/128: 0..128
-    const double F = __dadd_rn(1.0, __dmul_rn((double)k, 0.0078125));   // exact
-    const double f = __dsub_rn(m, F);                               // exact
-    const double G = c_log_g[k];
-    double r = __dmul_rn(f, G);
-    r = __fma_rn(__fma_rn(-r, F, f), G, r);
-    double q = 1.0 / 7;
-    q = __fma_rn(q, r, -1.0 / 6);
-    q = __fma_rn(q, r, 1.0 / 5);
-    q = __fma_rn(q, r, -0.25);
-    q = __fma_rn(q, r, 1.0 / 3);
-    q = __fma_rn(q, r, -0.5);
-    const double hi = __fma_rn(e, zigtab::LN2_HI, c_log_thi[k]);   // exact
-    const double lo = __fma_rn(__dmul_rn(r, r), q, __fma_rn(e, zigtab::LN2_LO, c_log_tlo[k]));
-    return __dadd_rn(hi, __dadd_rn(r, lo));
 }
 
 // RN(z / R) without a division: q = RN(z RN(1/R)) and one fused multiply-add
