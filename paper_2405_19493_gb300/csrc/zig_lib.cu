@@ -937,31 +937,56 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                 // pointer, count, rejections (and sigma, kind) come from its lane
                 constexpr int kRowsPerStep = 32 / B;
                 const int sub = lane / B, c = lane % B;
-#pragma unroll 4
-                for (int k = 0; k < 32 / kRowsPerStep; ++k) {
-                    const int row = kRowsPerStep * k + sub;
-                    OutT* const rd = (OutT*)__shfl_sync(kFull, (unsigned long long)dst, row);
-                    const int rcnt = __shfl_sync(kFull, acc, row);
-                    const uint32_t rrej = __shfl_sync(kFull, rj, row);
-                    float rsig = 0.0f;
-                    uint32_t rkind = ZIG_REQ_MUTATE;
-                    if constexpr (MODE != 0) {
-                        rsig = __shfl_sync(kFull, sigma, row);
-                        rkind = __shfl_sync(kFull, kind, row);
-                    }
-                    if (c < rcnt) {
-                        int src = c;   // slot of the row's c-th accepted candidate
-                        for (uint32_t m = rrej; m; m &= m - 1) {
-                            if (__ffs(m) - 1 <= src) ++src;
-                            else break;
+                if constexpr (MODE != 0) {
+                    // read-modify-write of x, four row-steps at a time: their loads of x
+                    // are issued before any of their stores, so the loads overlap.  Each
+                    // element of x is read once, before this thread writes it, and never
+                    // read again, so the read-only load path is safe.
+                    constexpr int kG = 8;
+#pragma unroll 1
+                    for (int k0 = 0; k0 < 32 / kRowsPerStep; k0 += kG) {
+                        float* rdp[kG];
+                        float zf[kG], xv[kG], sg[kG];
+                        bool ok[kG], gen[kG];
+#pragma unroll
+                        for (int u = 0; u < kG; ++u) {
+                            const int row = kRowsPerStep * (k0 + u) + sub;
+                            rdp[u] = (float*)__shfl_sync(kFull, (unsigned long long)dst, row);
+                            const int rcnt = __shfl_sync(kFull, acc, row);
+                            const uint32_t rrej = __shfl_sync(kFull, rj, row);
+                            sg[u] = __shfl_sync(kFull, sigma, row);
+                            const uint32_t rkind = __shfl_sync(kFull, kind, row);
+                            gen[u] = MODE == 2 && rkind == ZIG_REQ_GENERATE;
+                            ok[u] = c < rcnt;
+                            int src = c;   // slot of the row's c-th accepted candidate
+                            for (uint32_t m = rrej; m; m &= m - 1) {
+                                if (__ffs(m) - 1 <= src) ++src;
+                                else break;
+                            }
+                            if (!ok[u]) src = 0;   // keep the stage read in range
+                            zf[u] = __uint_as_float((uint32_t)ws.stage[zslot<B, S>(row, src)]);
+                            xv[u] = 0.0f;
+                            if (ok[u] && !gen[u]) xv[u] = __ldg(rdp[u] + c);
                         }
-                        const S z = ws.stage[zslot<B, S>(row, src)];
-                        if constexpr (MODE != 0) {
-                            const float zf = __uint_as_float((uint32_t)z);
-                            if (MODE == 2 && rkind == ZIG_REQ_GENERATE) ((float*)rd)[c] = zf;
-                            else ((float*)rd)[c] = fmaf(rsig, zf, ((float*)rd)[c]);
-                        } else {
-                            z128_store1<OutT, S>(rd + c, z);   // write-once output: streaming store
+#pragma unroll
+                        for (int u = 0; u < kG; ++u)
+                            if (ok[u]) rdp[u][c] = gen[u] ? zf[u] : fmaf(sg[u], zf[u], xv[u]);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int k = 0; k < 32 / kRowsPerStep; ++k) {
+                        const int row = kRowsPerStep * k + sub;
+                        OutT* const rd = (OutT*)__shfl_sync(kFull, (unsigned long long)dst, row);
+                        const int rcnt = __shfl_sync(kFull, acc, row);
+                        const uint32_t rrej = __shfl_sync(kFull, rj, row);
+                        if (c < rcnt) {
+                            int src = c;   // slot of the row's c-th accepted candidate
+                            for (uint32_t m = rrej; m; m &= m - 1) {
+                                if (__ffs(m) - 1 <= src) ++src;
+                                else break;
+                            }
+                            // write-once output: streaming store
+                            z128_store1<OutT, S>(rd + c, ws.stage[zslot<B, S>(row, src)]);
                         }
                     }
                 }
