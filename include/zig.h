@@ -181,11 +181,12 @@ zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uint64_t *seed
  *  batch        candidates each lane draws per batch before the warp decides its
  *               deferred wedge tests and writes: 16 (default) or 8 for
  *               ZIG_F64; 32 (default) or 16 for ZIG_F32 and ZIG_BF16.
- *  store_bytes  0: the warp writes each row cooperatively, one element per lane
- *               and store; 32: each lane writes its own row in whole 32-byte
- *               sectors (256-bit stores), carrying a partial sector over to its
- *               next batch, with element stores only at a unit's unaligned
- *               start and at its end.
+ *  store_bytes  0 (default for ZIG_F32, ZIG_BF16): the warp writes each row
+ *               cooperatively, one element per lane and store; 32 (default for
+ *               ZIG_F64): each lane writes its own row in whole 32-byte sectors
+ *               (256-bit stores), carrying a partial sector over to its next
+ *               batch, with element stores only at a unit's unaligned start and
+ *               at its end.
  * One configuration is kept per device, PRNG, dtype and input form
  * (variable_lengths = 1 for calls with a lengths array, 0 for uniform ones);
  * zig_generate and zig_generate_noalloc read it at each call.

@@ -1302,7 +1302,11 @@ static LaunchCfg g_cfg[kMaxDevices][4][3][2];
 static bool g_cfg_set[kMaxDevices][4][3][2];
 
 static uint32_t default_batch(int dt) { return dt == ZIG_F64 ? 16u : 32u; }
-static LaunchCfg default_cfg(int dt) { return LaunchCfg{(uint32_t)kZBlock, default_batch(dt), 0u}; }
+// binary64 rows go out in per-lane 32-byte sectors, the narrower types in
+// warp-cooperative element stores (each measured the faster for its type)
+static LaunchCfg default_cfg(int dt) {
+    return LaunchCfg{(uint32_t)kZBlock, default_batch(dt), dt == ZIG_F64 ? 32u : 0u};
+}
 
 static bool cfg_valid(int dt, const LaunchCfg& c) {
     const uint32_t b = default_batch(dt);

@@ -78,7 +78,7 @@ def test_launch_config_validation_and_candidates():
     """Launch configurations: defaults, validation, set/reset; no CUDA call."""
     for dt, b in (("f64", 16), ("f32", 32), ("bf16", 32)):
         assert Z.zig_launch_config_get("splitmix64", dt, False, device=5) == \
-            {"block": 768, "batch": b, "store_bytes": 0}
+            {"block": 768, "batch": b, "store_bytes": 32 if dt == "f64" else 0}
         cands = Z.zig_autotune_candidates(dt)
         assert len(cands) == 16
         assert {c["batch"] for c in cands} == {b // 2, b}
