@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
 //       narrow binary64 pipe keeps up with one per candidate, and the same
 //       product in integer arithmetic costs far more issue slots.
 //       binary32/bfloat16 use fl32(j * w32[i]).
-//     - wedge (i < 127): deferred.  The slot keeps j | i << 24 | negative << 31,
+//     - wedge (i < 127): deferred.  The slot keeps the draw w,
 //       the generator writes an 8-byte record from which the test's uniform is
 //       rebuilt (G::snap) and moves past that uniform at once.  A lane holds up
 //       to kZRec records per batch; a further wedge is decided on the spot.
@@ -390,9 +390,16 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
 // sequence a one-variate-at-a-time loop produces.
 
 
-struct Z128Tab {
-    uint32_t K[128][32];    // k[i], one copy per lane
-    double W[128][16];      // w[i], 16 copies (a half-warp reads without conflicts)
+// The fast path's table.  Binary64 kernels index it by the draw's low byte
+// ix = w & 0xFF (layer ix & 127, positive when bit 7 is set); one 16-byte entry
+// holds everything a candidate needs: {low, high word of 2^52 w[i], k[i], the
+// output's sign bit}, in 8 copies so that the 8 lanes of a quarter warp
+// reading 16-byte entries hit distinct banks.  The narrower types keep k[i]
+// in one copy per lane.
+struct Z128FastF64 { uint4 T[256][8]; };
+struct Z128FastNarrow { uint32_t K[128][32]; };
+template <int DT>
+struct Z128Tab : std::conditional<DT == ZIG_F64, Z128FastF64, Z128FastNarrow>::type {
     float W32[128];         // RN32(x_{i+1} / 2^24)
     float Y32[128];         // RN32(y[i])
     float DY32[128];        // RN32(y[i] - y[i+1])
@@ -402,11 +409,18 @@ struct Z128Tab {
 __device__ float d_z128_Y32[128];
 __device__ float d_z128_DY32[128];
 
-__device__ __forceinline__ void z128tab_load(Z128Tab& t) {
-    for (int k = threadIdx.x; k < 128 * 32; k += blockDim.x) {
-        const int i = k >> 5, c = k & 31;
-        t.K[i][c] = d_z128_kE[i] & 0xFFFFFFu;
-        if (c < 16) t.W[i][c] = d_z128_W[i];
+template <int DT>
+__device__ __forceinline__ void z128tab_load(Z128Tab<DT>& t) {
+    if constexpr (DT == ZIG_F64) {
+        for (int k = threadIdx.x; k < 256 * 8; k += blockDim.x) {
+            const int ix = k >> 3, i = ix & 127;
+            const double b = __dmul_rn(d_z128_W[i], 0x1p52);   // exact: a power-of-two scaling
+            const long long bb = __double_as_longlong(b);
+            t.T[ix][k & 7] = make_uint4((uint32_t)bb, (uint32_t)(bb >> 32), d_z128_kE[i] & 0xFFFFFFu,
+                                        ix < 128 ? 0x80000000u : 0u);
+        }
+    } else {
+        for (int k = threadIdx.x; k < 128 * 32; k += blockDim.x) t.K[k >> 5][k & 31] = d_z128_kE[k >> 5] & 0xFFFFFFu;
     }
     for (int i = threadIdx.x; i < 128; i += blockDim.x) {
         t.W32[i] = d_z128_W32[i];
@@ -417,13 +431,11 @@ __device__ __forceinline__ void z128tab_load(Z128Tab& t) {
     }
 }
 
-// RN(j * w) with one binary64 fma: (2^52 + j) * w - 2^52 * w = j * w exactly
-// before the single rounding.  2^52 + j and -2^52 * w are built from bits.
-__device__ __forceinline__ uint64_t mul_j_w_fma(uint32_t j, double w) {
-    const uint32_t wh = (uint32_t)__double2hiint(w), wl = (uint32_t)__double2loint(w);
-    const double d = __hiloint2double(0x43300000, (int)j);
-    const double c = __hiloint2double((int)((wh + (52u << 20)) | 0x80000000u), (int)wl);
-    return (uint64_t)__double_as_longlong(__fma_rn(d, w, c));
+// RN(j * w) with one binary64 fma, given b = 2^52 w: a = 1 + j 2^-52 (built
+// from bits; j < 2^24) gives a b - b = j w exactly before the single rounding.
+// (An exact zero comes out as +0; the caller sets the sign.)
+__device__ __forceinline__ double mul_j_w(uint32_t j, double b) {
+    return __fma_rn(__hiloint2double(0x3FF00000, (int)j), b, -b);
 }
 
 // binary32 value of m * 2^-53 for m < 2^53 (relative error < 2^-23).
@@ -432,36 +444,13 @@ __device__ __forceinline__ float m53_to_float(uint64_t m) {
     return hi ? (float)hi * 0x1p-24f : (float)(uint32_t)m * 0x1p-53f;
 }
 
-template <int DT> struct Z128Out;
-template <> struct Z128Out<ZIG_F64> {
-    using T = double;
-    using Pair = double2;
-    static __device__ __forceinline__ double fast(const Z128Tab& t, uint32_t i, uint32_t j,
-                                                  uint32_t neg, int lane) {
-        const uint64_t b = mul_j_w_fma(j, t.W[i][lane & 15]);
-        return __longlong_as_double((long long)(b | ((uint64_t)neg << 63)));
-    }
-    static __device__ __forceinline__ double from64(double x, uint32_t neg) {
-        return __longlong_as_double((long long)((uint64_t)__double_as_longlong(x) | ((uint64_t)neg << 63)));
-    }
-};
-template <> struct Z128Out<ZIG_F32> {
-    using T = float;
-    using Pair = float2;
-    static __device__ __forceinline__ float fast(const Z128Tab& t, uint32_t i, uint32_t j,
-                                                 uint32_t neg, int) {
-        return __uint_as_float(__float_as_uint(__fmul_rn((float)j, t.W32[i])) | (neg << 31));
-    }
-    static __device__ __forceinline__ float from64(double x, uint32_t neg) {
-        return __uint_as_float(__float_as_uint(__double2float_rn(x)) | (neg << 31));
-    }
-};
 // The wedge test for layer i, abscissa j and uniform U = m1 2^-53:
 // y = y[i+1] + (y[i] - y[i+1]) U < exp(-x^2/2) with x = RN(j w[i]).  Decided in
 // binary32 when |y32 - e32| clears 2^-16 e32 (the binary32 errors are
 // |y32/y - 1| + |e32/e - 1| <= 2.6e-6, expf within 2 ulp); inside the margin
 // the binary64 definition decides.
-__device__ __forceinline__ bool z128_wedge_accept(const Z128Tab& t, uint32_t i, uint32_t j, uint64_t m1) {
+template <class Tab>
+__device__ __forceinline__ bool z128_wedge_accept(const Tab& t, uint32_t i, uint32_t j, uint64_t m1) {
     const float x32 = __fmul_rn((float)j, t.W32[i]);
     const float e32 = expf(__fmul_rn(__fmul_rn(-0.5f, x32), x32));
     const float u32 = (float)(uint32_t)(m1 >> 29) * 0x1p-24f;
@@ -517,25 +506,42 @@ __device__ __forceinline__ double z128_tail(uint64_t m1, uint64_t m2) {
 
 // Staging word per slot: binary64 bits, or binary32 bits (binary32 and bfloat16
 // outputs; bfloat16 is rounded at the store).  A deferred wedge's slot holds
-// j | i << 24 | negative << 31 until it is decided.
+// its 32-bit draw w until it is decided.
 template <int DT> struct ZStage { using T = uint32_t; };
 template <> struct ZStage<ZIG_F64> { using T = uint64_t; };
 
 
+// The candidate of the 32-bit draw w (layer i = w & 127, positive when bit 7
+// is set, abscissa j = w >> 8): its staging word sign RN(j w[i]) and whether
+// it leaves the fast path (j >= k[i]).
 template <int DT>
-__device__ __forceinline__ typename ZStage<DT>::T z128_value(const Z128Tab& t, uint32_t i, uint32_t j,
-                                                              uint32_t neg, int lane) {
+__device__ __forceinline__ typename ZStage<DT>::T z128_fast(const Z128Tab<DT>& t, uint32_t w, int lane,
+                                                             bool& slow) {
+    const uint32_t j = w >> 8;
     if constexpr (DT == ZIG_F64) {
-        return (uint64_t)__double_as_longlong(Z128Out<ZIG_F64>::fast(t, i, j, neg, lane));
+        const uint4 e = t.T[w & 0xFFu][lane & 7];
+        slow = j >= e.z;
+        const double b = __hiloint2double((int)e.y, (int)e.x);
+        return (uint64_t)__double_as_longlong(mul_j_w(j, b)) | ((uint64_t)e.w << 32);
     } else {
-        return __float_as_uint(Z128Out<ZIG_F32>::fast(t, i, j, neg, lane));
+        const uint32_t i = w & 0x7Fu;
+        slow = j >= t.K[i][lane];
+        return __float_as_uint(__fmul_rn((float)j, t.W32[i])) | ((~w << 24) & 0x80000000u);
     }
 }
 
 template <int DT>
-__device__ __forceinline__ typename ZStage<DT>::T z128_from64(double x, uint32_t neg) {
-    if constexpr (DT == ZIG_F64) return (uint64_t)__double_as_longlong(Z128Out<ZIG_F64>::from64(x, neg));
-    else return __float_as_uint(Z128Out<ZIG_F32>::from64(x, neg));
+__device__ __forceinline__ typename ZStage<DT>::T z128_value(const Z128Tab<DT>& t, uint32_t w, int lane) {
+    bool slow;
+    return z128_fast<DT>(t, w, lane, slow);
+}
+
+// A tail's staging word: x with the sign of the draw w.
+template <int DT>
+__device__ __forceinline__ typename ZStage<DT>::T z128_from64(double x, uint32_t w) {
+    const uint32_t neg = (~w >> 7) & 1u;
+    if constexpr (DT == ZIG_F64) return (uint64_t)__double_as_longlong(x) | ((uint64_t)neg << 63);
+    else return __float_as_uint(__double2float_rn(x)) | (neg << 31);
 }
 
 
@@ -677,42 +683,42 @@ __device__ __forceinline__ void z128_flush_lane(const S* stage, S* carry, int la
     nc = unit_end ? 0 : tail;
 }
 
-// Resolve a slow draw (j >= k[i]) of slot v.  A wedge is deferred to phase B
-// (its slot keeps j | i << 24 | negative << 31 and the generator's record of
+// Resolve a slow draw w (j >= k[i]) of slot v.  A wedge is deferred to phase B
+// (its slot keeps w and the generator's record of
 // the test's uniform goes to rec) unless the lane already holds kZRec records
 // in this batch; a tail, or a wedge that is not deferred, is decided here, and
 // a rejected one draws again for the same slot.  Returns the slot's word.
 template <class G, int DT, class W>
-__device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab& t, W& ws,
-                                                             int lane, int v, uint32_t i, uint32_t j,
-                                                             uint32_t neg, uint32_t& drel, uint32_t& smask) {
+__device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab<DT>& t, W& ws,
+                                                             int lane, int v, uint32_t w,
+                                                             uint32_t& drel, uint32_t& smask) {
     using S = typename ZStage<DT>::T;
     for (;;) {
+        const uint32_t i = w & 0x7Fu;
         if (i < 127) {
             const int nw = __popc(smask);
             if (nw < kZRec) {
                 ws.rec[lane][nw] = g.template snap<kRecOut<G, DT>>();   // record the uniform, move past it
                 drel += G::kStepsPerDouble;
                 smask |= 1u << v;
-                return (S)(j | (i << 24) | (neg << 31));
+                return (S)w;
             }
             const uint64_t mu = g.next_m53();
             drel += G::kStepsPerDouble;
-            if (z128_wedge_accept(t, i, j, mu)) return z128_value<DT>(t, i, j, neg, lane);
+            if (z128_wedge_accept(t, i, w >> 8, mu)) return z128_value<DT>(t, w, lane);
         } else {
             const uint64_t m1 = g.next_m53();
             const uint64_t m2 = g.next_m53();
             drel += 2 * G::kStepsPerDouble;
             const double x = z128_tail(m1, m2);
-            if (x >= 0.0) return z128_from64<DT>(x, neg);
+            if (x >= 0.0) return z128_from64<DT>(x, w);
         }
         // rejected: the next draw is for the same slot
-        const uint32_t w = g.next_u32();
+        w = g.next_u32();
         ++drel;
-        i = w & 0x7Fu;
-        neg = (~w >> 7) & 1u;
-        j = w >> 8;
-        if (j < t.K[i][lane]) return z128_value<DT>(t, i, j, neg, lane);
+        bool slow;
+        const S val = z128_fast<DT>(t, w, lane, slow);
+        if (!slow) return val;
     }
 }
 
@@ -727,7 +733,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
     using OutT = typename OutOf<DT>::T;
     using W = ZWarp<G, DT, BW>;
     constexpr int B = W::B;
-    __shared__ Z128Tab t;
+    __shared__ Z128Tab<DT> t;
     extern __shared__ __align__(16) unsigned char z128_dsm[];
     z128tab_load(t);
     __syncthreads();
@@ -800,38 +806,41 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                 // a lane ends the batch with B minus its deferred wedges candidates.
                 // (Measured faster for binary64 only; the 32-wide binary32 batches
                 // keep the candidate loop below.)
-                int slot = 0;
+                // The iteration after a deferral runs the candidate code too, with
+                // its results discarded, so that the loop has no divergent branch
+                // but the rare slow draws'.
+                int slot = 0, nw = 0;
                 bool pend = false;
 #pragma unroll 2
                 for (int it = 0; it < B; ++it) {
                     const uint64_t r = g.next_u64();   // this output is its own record
-                    ++drel;
-                    if (pend) {
-                        ws.rec[lane][__popc(smask) - 1] = r;
-                        pend = false;
-                    } else {
-                        const uint32_t w = (uint32_t)(r >> 32);   // nextInt
-                        const uint32_t i = w & 0x7Fu;
-                        const uint32_t neg = (~w >> 7) & 1u;   // bit 7 set -> positive
-                        const uint32_t j = w >> 8;
-                        S val = z128_value<DT>(t, i, j, neg, lane);
-                        const bool slow = j >= t.K[i][lane];
-                        const bool wedge = slow && i < 127 && __popc(smask) < kZRec;
-                        if (wedge) {
-                            smask |= 1u << slot;
-                            val = (S)(j | (i << 24) | (neg << 31));
-                            pend = true;
-                        }
-                        const bool other = slow && !wedge;   // a tail, or no record left
-                        if (__any_sync(__activemask(), other)) {
-                            if (other) val = z128_slow<G, DT>(g, t, ws, lane, slot, i, j, neg, drel, smask);
-                        }
-                        ws.stage[zslot<B, S>(lane, slot)] = val;
-                        ++slot;
+                    if (pend) ws.rec[lane][nw - 1] = r;   // the uniform of the wedge just deferred
+                    const uint32_t w = (uint32_t)(r >> 32);   // nextInt
+                    bool slow;
+                    S val = z128_fast<DT>(t, w, lane, slow);
+                    slow = slow && !pend;
+                    const bool wedge = slow && (w & 0x7Fu) != 0x7Fu && nw < kZRec;
+                    if (wedge) {
+                        smask |= 1u << slot;
+                        val = (S)w;
                     }
+                    const bool other = slow && !wedge;   // a tail, or no record left
+                    if (__any_sync(kFull, other)) {
+                        if (other) {
+                            val = z128_slow<G, DT>(g, t, ws, lane, slot, w, drel, smask);
+                            nw = __popc(smask);
+                        }
+                    }
+                    // a discarded iteration's word goes to the next free slot (in
+                    // range: slot <= it) and is overwritten or never read
+                    ws.stage[zslot<B, S>(lane, slot)] = val;
+                    slot += pend ? 0 : 1;
+                    nw += wedge ? 1 : 0;
+                    pend = wedge;
                 }
+                drel += B;
                 if (pend) {   // the last candidate was a deferred wedge: its uniform is next
-                    ws.rec[lane][__popc(smask) - 1] = g.next_u64();
+                    ws.rec[lane][nw - 1] = g.next_u64();
                     ++drel;
                 }
                 produced = slot;
@@ -839,36 +848,37 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                 // full batch: B candidates per lane, one warp vote per candidate guarding
                 // the rare slow draws (unrolled by two: deeper unrolling copies the slow
                 // handler into the instruction stream and costs more than it saves)
+                int nw = 0;
 #pragma unroll 2
                 for (int v = 0; v < B; ++v) {
                     const uint32_t w = g.next_u32();
-                    ++drel;
-                    const uint32_t i = w & 0x7Fu;
-                    const uint32_t neg = (~w >> 7) & 1u;   // bit 7 set -> positive
-                    const uint32_t j = w >> 8;
-                    S val = z128_value<DT>(t, i, j, neg, lane);
-                    const bool slow = j >= t.K[i][lane];
+                    bool slow;
+                    S val = z128_fast<DT>(t, w, lane, slow);
                     bool other = slow;   // what needs the divergent slow handler
                     if constexpr (PRNG == ZIG_LCG48 || PRNG == ZIG_SPLITMIX64) {
                         // a wedge is deferred without a branch: recording its uniform
                         // and stepping past it cost a few predicated instructions
                         // (the 64-bit generators' steps are too long to run predicated
                         // on every candidate)
-                        const int nw = __popc(smask);
-                        const bool wedge = slow && i < 127 && nw < kZRec;
+                        const bool wedge = slow && (w & 0x7Fu) != 0x7Fu && nw < kZRec;
                         if (wedge) {
                             ws.rec[lane][nw] = g.template snap<kRecOut<G, DT>>();
                             drel += G::kStepsPerDouble;
                             smask |= 1u << v;
-                            val = (S)(j | (i << 24) | (neg << 31));
+                            val = (S)w;
                         }
+                        nw += wedge ? 1 : 0;
                         other = slow && !wedge;
                     }
                     if (__any_sync(kFull, other)) {
-                        if (other) val = z128_slow<G, DT>(g, t, ws, lane, v, i, j, neg, drel, smask);
+                        if (other) {
+                            val = z128_slow<G, DT>(g, t, ws, lane, v, w, drel, smask);
+                            nw = __popc(smask);
+                        }
                     }
                     ws.stage[zslot<B, S>(lane, v)] = val;
                 }
+                drel += B;
                 produced = B;
             } else {
                 // the end of some streams: up to min(rem, B) candidates per lane
@@ -879,11 +889,9 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                     if (v < cnt) {
                         const uint32_t w = g.next_u32();
                         ++drel;
-                        const uint32_t i = w & 0x7Fu;
-                        const uint32_t neg = (~w >> 7) & 1u;
-                        const uint32_t j = w >> 8;
-                        S val = z128_value<DT>(t, i, j, neg, lane);
-                        if (j >= t.K[i][lane]) val = z128_slow<G, DT>(g, t, ws, lane, v, i, j, neg, drel, smask);
+                        bool slow;
+                        S val = z128_fast<DT>(t, w, lane, slow);
+                        if (slow) val = z128_slow<G, DT>(g, t, ws, lane, v, w, drel, smask);
                         ws.stage[zslot<B, S>(lane, v)] = val;
                         produced = v + 1;
                     }
@@ -916,10 +924,9 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                         uint32_t m = ws.smask[o];
                         for (int k = kr; k > 0; --k) m &= m - 1;
                         const int slot = __ffs(m) - 1;
-                        const uint32_t meta = (uint32_t)ws.stage[zslot<B, S>(o, slot)];
-                        const uint32_t j = meta & 0xFFFFFFu, i = (meta >> 24) & 0x7Fu, neg = meta >> 31;
-                        if (z128_wedge_accept(t, i, j, G::template m53_of<kRecOut<G, DT>>(ws.rec[o][kr])))
-                            ws.stage[zslot<B, S>(o, slot)] = z128_value<DT>(t, i, j, neg, lane);
+                        const uint32_t w = (uint32_t)ws.stage[zslot<B, S>(o, slot)];   // the deferred draw
+                        if (z128_wedge_accept(t, w & 0x7Fu, w >> 8, G::template m53_of<kRecOut<G, DT>>(ws.rec[o][kr])))
+                            ws.stage[zslot<B, S>(o, slot)] = z128_value<DT>(t, w, lane);
                         else
                             atomicOr(&ws.rej[o], 1u << slot);
                     }
@@ -1011,7 +1018,7 @@ __global__ void __launch_bounds__(256) selfcheck_kernel(unsigned long long* coun
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t i = (uint32_t)(k >> 24), j = (uint32_t)k & 0xFFFFFFu;
         const double w = d_z128_W[i];
-        bad_p += mul_j_w_fma(j, w) != (uint64_t)__double_as_longlong(__dmul_rn((double)j, w));
+        bad_p += __double_as_longlong(mul_j_w(j, __dmul_rn(w, 0x1p52))) != __double_as_longlong(__dmul_rn((double)j, w));
         ++n_p;
         const double u = m53_to_double(((k * 0x9E3779B97F4A7C15ull) >> 11) | 1u);   // in (0, 1)
         const long long dl = __double_as_longlong(zlog(u)) - __double_as_longlong(log(u));
@@ -1259,7 +1266,7 @@ static GenFn pick(int alg, int prng, int dt, bool half_batch = false) {
 // Every instantiation must fit one SM's shared memory (227 KB per block).
 template <class G, int DT>
 constexpr bool z128_fits() {   // the default batch width is the larger one
-    return z128_warp_bytes<G, DT>() * kZWarps + sizeof(Z128Tab) <= 227 * 1024;
+    return z128_warp_bytes<G, DT>() * kZWarps + sizeof(Z128Tab<DT>) <= 227 * 1024;
 }
 static_assert(z128_fits<GenLcg48, ZIG_F64>() && z128_fits<GenLcg48, ZIG_F32>() &&
                   z128_fits<GenLcg48, ZIG_BF16>() && z128_fits<GenSplitMix64, ZIG_F64>() &&
