@@ -568,23 +568,27 @@ struct ZWarp {
     using S = typename ZStage<DT>::T;
     using OutT = typename OutOf<DT>::T;
     static constexpr int EPS = 32 / (int)sizeof(OutT);   // output elements per 32-byte sector
-    // carry row width: at least EPS - 1 values, with a stride that spreads the
-    // 32 lanes' rows over distinct banks
-    static constexpr int CW = sizeof(S) == 8 ? 5 : (EPS == 8 ? 9 : 17);
-    S stage[32 * B];
-    S carry[32 * CW];                     // values a lane has not written yet (lane-per-row flush)
+    // Row stride of the stage: binary64 rows hold the lane's carried values in
+    // columns 1..3 and the batch's slots from column 4, at an odd stride of
+    // 8-byte words (the 32 lanes' rows start on distinct banks); 4-byte rows
+    // are B wide and swizzled, with the carry kept apart (CW wide).
+    static constexpr int RS = sizeof(S) == 8 ? B + 5 : B;
+    static constexpr int CW = sizeof(S) == 8 ? 1 : (EPS == 8 ? 9 : 17);
+    S stage[32 * RS];
+    S carry[sizeof(S) == 8 ? 1 : 32 * CW];   // values a lane has not written yet (4-byte rows)
     uint64_t rec[32][kZRec];              // each deferred wedge's uniform record (G::snap)
     uint32_t smask[32], rej[32], excl[32];
 };
 
-// Slot (row, col) of a B-wide stage, swizzled so that the 32 lanes writing
-// column col of their own rows, and the lanes of a row reading it, hit distinct banks.
+// Slot (row, col) of the stage, laid out so that the 32 lanes writing column
+// col of their own rows, and the lanes of a row reading it, hit distinct
+// banks: 8-byte rows at an odd stride (B + 5 words, slots from column 4),
+// 4-byte rows swizzled.
 template <int B, typename S>
 __device__ __forceinline__ int zslot(int row, int col) {
     static_assert(B == 32 || B == 16 || (B == 8 && sizeof(S) == 8), "unsupported batch width");
-    if constexpr (B == 32) return row * 32 + (col ^ row);              // 4-byte words
-    else if constexpr (B == 8) return row * 8 + (col ^ ((row >> 1) & 7));
-    else if constexpr (sizeof(S) == 8) return row * 16 + (col ^ (row & 15));
+    if constexpr (sizeof(S) == 8) return row * (B + 5) + 4 + col;
+    else if constexpr (B == 32) return row * 32 + (col ^ row);
     else return row * 16 + (col ^ ((row >> 1) & 15));
 }
 
@@ -681,6 +685,76 @@ __device__ __forceinline__ void z128_flush_lane(const S* stage, S* carry, int la
     }
     dst = unit_end ? p + tail : p;
     nc = unit_end ? 0 : tail;
+}
+
+// Phase C for binary64 rows, lane-per-row form.  The lane's row holds the nc
+// values carried over from its previous batch in columns 4 - nc .. 3 and the
+// batch's slots from column 4, so its output sequence (the carry, then the
+// accepted slots) is contiguous but for rejected slots.  A lane with one
+// rejected slot reads around it; one with more first closes them up.  The
+// lane writes whole 32-byte sectors, one 256-bit store each; element stores
+// remain only before the first sector boundary of a unit and at its end;
+// the rest (at most 3 values) moves to columns 4 - nc' .. 3 for the next batch
+// (each value moves left or stays, in ascending order, so none is overwritten
+// before it is read).
+template <int B, bool kAligned>
+__device__ __forceinline__ void z128_flush_f64_body(uint64_t* row, int t, int total, bool unit_end,
+                                                    double*& dst, int& nc) {
+    const uint64_t* const s0 = row + 4 - nc;   // sequence element e: s0[e], or s0[e + 1] from e >= t
+    const uint64_t* const s1 = s0 + 1;
+    int e0 = 0;
+    if constexpr (!kAligned) {   // a unit's first batch may start inside a sector
+        const int mis = (int)(((uintptr_t)dst & 31) >> 3);
+        e0 = umin64(mis ? 4 - mis : 0, total);
+        for (int k = 0; k < e0; ++k) __stcs((unsigned long long*)dst + k, (k >= t ? s1 : s0)[k]);
+        dst += e0;
+    }
+    const int nsec = (total - e0) >> 2;
+    constexpr int kMaxSec = (B + 3) / 4;
+#pragma unroll
+    for (int q = 0; q < kMaxSec; ++q) {
+        if (q < nsec) {
+            uint64_t v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = e0 + 4 * q + k;
+                v[k] = (e >= t ? s1 : s0)[e];
+            }
+            z128_store_sector<double, uint64_t, 4>(dst + 4 * q, v);
+        }
+    }
+    const int rest = total - e0 - 4 * nsec;
+    const int eb = e0 + 4 * nsec;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k < rest) {
+            const int e = eb + k;
+            const uint64_t z = (e >= t ? s1 : s0)[e];
+            if (unit_end) __stcs((unsigned long long*)dst + 4 * nsec + k, z);
+            else row[4 - rest + k] = z;
+        }
+    }
+    dst += 4 * nsec + (unit_end ? rest : 0);
+    nc = unit_end ? 0 : rest;
+}
+
+template <int B>
+__device__ __forceinline__ void z128_flush_f64(uint64_t* row, uint32_t rj, int produced, int acc,
+                                               bool unit_end, double*& dst, int& nc) {
+    if (__any_sync(kFull, (rj & (rj - 1)) != 0)) {
+        if (rj & (rj - 1)) {   // two or more rejected slots: close them up in place
+            int d = __ffs(rj) - 1;
+            for (int c = d + 1; c < produced; ++c)
+                if (!((rj >> c) & 1u)) row[4 + d++] = row[4 + c];
+            rj = 0;
+        }
+    }
+    const int t = rj ? nc + __ffs(rj) - 1 : 1 << 30;   // the one rejected slot's sequence index
+    const int total = nc + acc;
+    if (__any_sync(kFull, ((uintptr_t)dst & 31) != 0))
+        z128_flush_f64_body<B, false>(row, t, total, unit_end, dst, nc);
+    else
+        z128_flush_f64_body<B, true>(row, t, total, unit_end, dst, nc);
 }
 
 // Resolve a slow draw w (j >= k[i]) of slot v.  A wedge is deferred to phase B
@@ -938,7 +1012,10 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             const int acc = produced - __popc(rj);
             rem -= (uint64_t)acc;
             if (MODE == 0 && a.lane_sectors) {
-                z128_flush_lane<B, W::EPS, W::CW, S, OutT>(ws.stage, ws.carry, lane, rj, acc, rem == 0, dst, nc);
+                if constexpr (sizeof(S) == 8)
+                    z128_flush_f64<B>(ws.stage + lane * W::RS, rj, produced, acc, rem == 0, dst, nc);
+                else
+                    z128_flush_lane<B, W::EPS, W::CW, S, OutT>(ws.stage, ws.carry, lane, rj, acc, rem == 0, dst, nc);
             } else {
                 // warp-cooperative: B lanes per row, one element each; the row's
                 // pointer, count, rejections (and sigma, kind) come from its lane
