@@ -577,7 +577,8 @@ struct ZWarp {
     S stage[32 * RS];
     S carry[sizeof(S) == 8 ? 1 : 32 * CW];   // values a lane has not written yet (4-byte rows)
     uint64_t rec[32][kZRec];              // each deferred wedge's uniform record (G::snap)
-    uint32_t smask[32], rej[32], excl[32];
+    uint32_t list[32 * kZRec];            // the batch's deferred wedges: row | slot << 5 | record << 10
+    uint32_t rej[32];
 };
 
 // Slot (row, col) of the stage, laid out so that the 32 lanes writing column
@@ -813,6 +814,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;   // the lanes below this one
     const int wib = threadIdx.x >> 5;
     const int n_warps = blockDim.x >> 5;
     W& ws = *(W*)(z128_dsm + (size_t)wib * z128_warp_bytes<G, DT, BW>());
@@ -973,31 +975,31 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             }
             draws += drel;
             // ---- B: decide the deferred wedges, 32 at a time ----
-            const int ns = __popc(smask);
-            int incl = ns;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += y;
+            // List them (row, slot, the row's record index), the k-th of every
+            // row in round k, one warp vote per round; then lane r decides entry r.
+            int total = 0;
+            {
+                uint32_t m = smask;
+                int k = 0;
+                for (;;) {
+                    const uint32_t bal = __ballot_sync(kFull, m != 0);
+                    if (bal == 0) break;
+                    if (m) {
+                        ws.list[total + __popc(bal & lt_mask)] = (uint32_t)lane | (uint32_t)(__ffs(m) - 1) << 5 |
+                                                                 (uint32_t)k << 10;
+                        m &= m - 1;
+                    }
+                    total += __popc(bal);
+                    ++k;
+                }
             }
-            const int total = __shfl_sync(kFull, incl, 31);
             if (total) {
-                ws.smask[lane] = smask;
-                ws.excl[lane] = (uint32_t)(incl - ns);
                 __syncwarp();
                 for (int base = 0; base < total; base += 32) {
                     const int r = base + lane;
                     if (r < total) {
-                        // the row holding record r: the last o with excl[o] <= r (excl[0] = 0;
-                        // o + step never exceeds 31)
-                        int o = 0;
-#pragma unroll
-                        for (int step = 16; step; step >>= 1)
-                            if (ws.excl[o + step] <= (uint32_t)r) o += step;
-                        const int kr = r - (int)ws.excl[o];   // the row's kr-th deferred wedge
-                        uint32_t m = ws.smask[o];
-                        for (int k = kr; k > 0; --k) m &= m - 1;
-                        const int slot = __ffs(m) - 1;
+                        const uint32_t en = ws.list[r];
+                        const int o = (int)(en & 31u), slot = (int)((en >> 5) & 31u), kr = (int)(en >> 10);
                         const uint32_t w = (uint32_t)ws.stage[zslot<B, S>(o, slot)];   // the deferred draw
                         if (z128_wedge_accept(t, w & 0x7Fu, w >> 8, G::template m53_of<kRecOut<G, DT>>(ws.rec[o][kr])))
                             ws.stage[zslot<B, S>(o, slot)] = z128_value<DT>(t, w, lane);
