@@ -179,7 +179,7 @@ zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uint64_t *seed
  * change how the same work is laid out on the GPU, never the values:
  *  block        threads per block, a multiple of 32 in [64, 768] (default 768).
  *  batch        candidates each lane draws per batch before the warp decides its
- *               deferred wedge tests and writes: 16 (default) or 8 for
+ *               deferred wedge tests and writes: 20 (default) or 10 for
  *               ZIG_F64; 32 (default) or 16 for ZIG_F32 and ZIG_BF16.
  *  store_bytes  0 (default for ZIG_F32, ZIG_BF16): the warp writes each row
  *               cooperatively, one element per lane and store; 32 (default for

@@ -546,15 +546,17 @@ __device__ __forceinline__ typename ZStage<DT>::T z128_from64(double x, uint32_t
 
 
 // Batch width (candidates per lane per batch): by default 32 slots with 4-byte
-// staging words and 16 with 8-byte words (a 2 KB stage per warp); half that is
-// the other choice a launch configuration can make.
-template <int DT> struct ZBatch { static constexpr int B = (DT == ZIG_F64) ? 16 : 32; };
+// staging words and 20 with 8-byte words (the most that fits 24 warps' stages
+// in one SM's shared memory); half that is the other choice a launch
+// configuration can make.
+template <int DT> struct ZBatch { static constexpr int B = (DT == ZIG_F64) ? 20 : 32; };
 
-// The kind of wedge record a kernel instantiation keeps: L64X128Mix binary64
-// batches draw every output with nextLong anyway and record that output; the
-// other instantiations record the generator's cheaper snapshot (G::snap).
+// The kind of wedge record a kernel instantiation keeps: L64X128Mix batches
+// draw every output with nextLong anyway and record that output; the other
+// generators record their cheaper snapshot (G::snap; Xoroshiro128PlusPlus's is
+// its output too).
 template <class G, int DT>
-constexpr bool kRecOut = std::is_same<G, GenL64X128Mix>::value && DT == ZIG_F64;
+constexpr bool kRecOut = std::is_same<G, GenL64X128Mix>::value;
 
 // Deferred wedges a lane may hold per batch (one 8-byte record each); a lane's
 // next wedge in the same batch is decided on the spot.  With 2.7 % wedges a
@@ -587,7 +589,7 @@ struct ZWarp {
 // 4-byte rows swizzled.
 template <int B, typename S>
 __device__ __forceinline__ int zslot(int row, int col) {
-    static_assert(B == 32 || B == 16 || (B == 8 && sizeof(S) == 8), "unsupported batch width");
+    static_assert(sizeof(S) == 8 ? (B == 20 || B == 10) : (B == 32 || B == 16), "unsupported batch width");
     if constexpr (sizeof(S) == 8) return row * (B + 5) + 4 + col;
     else if constexpr (B == 32) return row * 32 + (col ^ row);
     else return row * 16 + (col ^ ((row >> 1) & 15));
@@ -872,19 +874,16 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             uint32_t drel = 0, smask = 0;
             int produced;
             // ---- A: draw the batch's candidates ----
-            if ((PRNG == ZIG_L64X128MIX || PRNG == ZIG_XOROSHIRO128PP) && DT == ZIG_F64 &&
+            if ((PRNG == ZIG_L64X128MIX || PRNG == ZIG_XOROSHIRO128PP) &&
                 __all_sync(kFull, rem >= (uint64_t)B)) {
-                // LXM and Xoroshiro128PlusPlus: nextInt and nextDouble are both cut from
-                // nextLong, so a deferred
-                // wedge's uniform is simply the next output.  Every iteration takes one
-                // output: a candidate, or the record of the wedge deferred just before.
-                // No lane ever steps its generator in a divergent branch for a wedge;
-                // a lane ends the batch with B minus its deferred wedges candidates.
-                // (Measured faster for binary64 only; the 32-wide binary32 batches
-                // keep the candidate loop below.)
-                // The iteration after a deferral runs the candidate code too, with
-                // its results discarded, so that the loop has no divergent branch
-                // but the rare slow draws'.
+                // L64X128Mix and Xoroshiro128PlusPlus: nextInt and nextDouble are both
+                // cut from nextLong, so a deferred wedge's uniform is simply the next
+                // output.  Every iteration takes one output: a candidate, or the record
+                // of the wedge deferred just before.  No lane ever steps its generator
+                // in a divergent branch for a wedge; a lane ends the batch with B minus
+                // its deferred wedges candidates.  The iteration after a deferral runs
+                // the candidate code too, with its results discarded, so that the loop
+                // has no divergent branch but the rare slow draws'.
                 int slot = 0, nw = 0;
                 bool pend = false;
 #pragma unroll 2
@@ -1020,10 +1019,14 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                     z128_flush_lane<B, W::EPS, W::CW, S, OutT>(ws.stage, ws.carry, lane, rj, acc, rem == 0, dst, nc);
             } else {
                 // warp-cooperative: B lanes per row, one element each; the row's
-                // pointer, count, rejections (and sigma, kind) come from its lane
+                // pointer, count, rejections (and sigma, kind) come from its lane.
+                // kRowsPerStep rows per step; when B does not divide 32 the lanes
+                // past kRowsPerStep * B idle, and so do the rows past 31 in the last step.
                 constexpr int kRowsPerStep = 32 / B;
+                constexpr int kSteps = (32 + kRowsPerStep - 1) / kRowsPerStep;
                 const int sub = lane / B, c = lane % B;
                 if constexpr (MODE != 0) {
+                    static_assert(32 % B == 0, "mutation batches are 32 or 16 wide");
                     // read-modify-write of x, four row-steps at a time: their loads of x
                     // are issued before any of their stores, so the loads overlap.  Each
                     // element of x is read once, before this thread writes it, and never
@@ -1060,12 +1063,14 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                     }
                 } else {
 #pragma unroll 4
-                    for (int k = 0; k < 32 / kRowsPerStep; ++k) {
-                        const int row = kRowsPerStep * k + sub;
+                    for (int k = 0; k < kSteps; ++k) {
+                        const int rw = kRowsPerStep * k + sub;
+                        const bool in = sub < kRowsPerStep && rw < 32;
+                        const int row = in ? rw : 0;   // every lane takes part in the shuffles
                         OutT* const rd = (OutT*)__shfl_sync(kFull, (unsigned long long)dst, row);
                         const int rcnt = __shfl_sync(kFull, acc, row);
                         const uint32_t rrej = __shfl_sync(kFull, rj, row);
-                        if (c < rcnt) {
+                        if (in && c < rcnt) {
                             int src = c;   // slot of the row's c-th accepted candidate
                             for (uint32_t m = rrej; m; m &= m - 1) {
                                 if (__ffs(m) - 1 <= src) ++src;
@@ -1312,7 +1317,7 @@ template <int ALG, int PRNG>
 static GenFn pick_dt(int dt, bool half_batch) {
     if constexpr (ALG == ZIG_ZIG128) {
         switch (dt) {
-        case ZIG_F64: return half_batch ? z128_kernel<PRNG, ZIG_F64, 0, 8> : z128_kernel<PRNG, ZIG_F64, 0>;
+        case ZIG_F64: return half_batch ? z128_kernel<PRNG, ZIG_F64, 0, 10> : z128_kernel<PRNG, ZIG_F64, 0>;
         case ZIG_F32: return half_batch ? z128_kernel<PRNG, ZIG_F32, 0, 16> : z128_kernel<PRNG, ZIG_F32, 0>;
         default: return half_batch ? z128_kernel<PRNG, ZIG_BF16, 0, 16> : z128_kernel<PRNG, ZIG_BF16, 0>;
         }
@@ -1361,7 +1366,7 @@ template <class G>
 static size_t z128_dyn_for(int dt, bool half_batch, int warps) {
     size_t per;
     switch (dt) {
-    case ZIG_F64: per = half_batch ? z128_warp_bytes<G, ZIG_F64, 8>() : z128_warp_bytes<G, ZIG_F64>(); break;
+    case ZIG_F64: per = half_batch ? z128_warp_bytes<G, ZIG_F64, 10>() : z128_warp_bytes<G, ZIG_F64>(); break;
     case ZIG_F32: per = half_batch ? z128_warp_bytes<G, ZIG_F32, 16>() : z128_warp_bytes<G, ZIG_F32>(); break;
     default: per = half_batch ? z128_warp_bytes<G, ZIG_BF16, 16>() : z128_warp_bytes<G, ZIG_BF16>(); break;
     }
@@ -1387,7 +1392,7 @@ struct LaunchCfg {
 static LaunchCfg g_cfg[kMaxDevices][4][3][2];
 static bool g_cfg_set[kMaxDevices][4][3][2];
 
-static uint32_t default_batch(int dt) { return dt == ZIG_F64 ? 16u : 32u; }
+static uint32_t default_batch(int dt) { return dt == ZIG_F64 ? 20u : 32u; }
 // binary64 rows go out in per-lane 32-byte sectors, the narrower types in
 // warp-cooperative element stores (each measured the faster for its type)
 static LaunchCfg default_cfg(int dt) {

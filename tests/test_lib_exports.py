@@ -76,7 +76,7 @@ def test_host_side_argument_errors():
 
 def test_launch_config_validation_and_candidates():
     """Launch configurations: defaults, validation, set/reset; no CUDA call."""
-    for dt, b in (("f64", 16), ("f32", 32), ("bf16", 32)):
+    for dt, b in (("f64", 20), ("f32", 32), ("bf16", 32)):
         assert Z.zig_launch_config_get("splitmix64", dt, False, device=5) == \
             {"block": 768, "batch": b, "store_bytes": 32 if dt == "f64" else 0}
         cands = Z.zig_autotune_candidates(dt)
@@ -93,12 +93,12 @@ def test_launch_config_validation_and_candidates():
                 raise AssertionError(f"accepted {bad}")
             except Z.ZigError as e:
                 assert e.status == 1
-    cfg = {"block": 384, "batch": 8, "store_bytes": 32}
+    cfg = {"block": 384, "batch": 10, "store_bytes": 32}
     Z.zig_launch_config_set("l64x128mix", "f64", True, cfg, device=5)
     assert Z.zig_launch_config_get("l64x128mix", "f64", True, device=5) == cfg
     assert Z.zig_launch_config_get("l64x128mix", "f64", False, device=5)["block"] == 768
     Z.zig_launch_config_set("l64x128mix", "f64", True, None, device=5)
-    assert Z.zig_launch_config_get("l64x128mix", "f64", True, device=5)["batch"] == 16
+    assert Z.zig_launch_config_get("l64x128mix", "f64", True, device=5)["batch"] == 20
 
 
 def test_more_host_side_argument_errors():
