@@ -109,6 +109,15 @@ def test_bulk_full_size_sampled(Z, prng):
     compare_streams(rows, o, m, offsets_of(Ls), Ls)
 
 
+@pytest.mark.parametrize("prng", PRNGS)
+def test_zig128_f64_16m_full(Z, prng):
+    """2^14 streams x 1,024 (2^24 binary64) compared in full: enough lane batches that
+    the rare paths all occur (tails in the last slots of a batch, rows with more than
+    three rejected slots, deferred wedges beyond a lane's records)."""
+    rep = check(Z, prng, "zig128", W.seeds(1 << 14), uniform_len=1024)
+    assert rep.max_ulp <= 4
+
+
 # ---- variable lengths, chunks, ragged and degenerate inputs -------------------------------
 
 @pytest.mark.parametrize("prng", PRNGS)
