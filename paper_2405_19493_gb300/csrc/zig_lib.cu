@@ -164,7 +164,7 @@ __device__ __forceinline__ double polar_f64(G& g, bool& have, double& cached, ui
         have = false;
         return cached;
     }
-    constexpr uint32_t kStepsPerDouble = (sizeof(G) == sizeof(GenLcg48)) ? 2u : 1u;
+    constexpr uint32_t kStepsPerDouble = std::is_same<G, GenLcg48>::value ? 2u : 1u;
     double v1, v2, s;
     do {
         v1 = __dsub_rn(__dmul_rn(2.0, m53_to_double(g.next_m53())), 1.0);
@@ -220,7 +220,7 @@ __device__ __forceinline__ int z256_overhang_filter(float ox, float odx, float o
 
 template <class G>
 __device__ __forceinline__ double z256_slow(G& g, const Z256Smem& t, uint32_t& extra) {
-    constexpr uint32_t kSteps64 = (sizeof(G) == sizeof(GenLcg48)) ? 2u : 1u;
+    constexpr uint32_t kSteps64 = std::is_same<G, GenLcg48>::value ? 2u : 1u;
     constexpr uint32_t kStepsPerDouble = kSteps64;
     const uint64_t two53 = 1ull << 53;
     uint64_t V = g.next_u64();
@@ -366,25 +366,26 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
 // 128-level ziggurat (GSL form): one launch per bulk request
 // ---------------------------------------------------------------------------
 // Each lane owns one unit (stream or chunk) with its generator in registers.
-// A warp works in batches of B candidates per lane (B = 16 for binary64, 32
+// A warp works in batches of B candidates per lane (B = 20 for binary64, 32
 // otherwise, or half that by launch configuration), staged in shared memory:
 //  A. the lanes draw their candidates in lockstep; one warp vote per candidate
 //     guards the rare slow draws.
 //     - fast path (j < k[i]): x = RN(j * w[i]) on the spot.  For binary64 this
-//       is one fused multiply-add, fma(2^52 + j, w, -2^52 w) = RN(j w) exactly
-//       (2^52 + j is built from j's bits; -2^52 w from w's bits); GB300's
-//       narrow binary64 pipe keeps up with one per candidate, and the same
-//       product in integer arithmetic costs far more issue slots.
+//       is one fused multiply-add, fma(1 + j 2^-52, 2^52 w, -2^52 w) = RN(j w)
+//       exactly (1 + j 2^-52 is built from j's bits, 2^52 w is in the table);
+//       GB300's narrow binary64 pipe keeps up with one per candidate, and the
+//       same product in integer arithmetic costs far more issue slots.
 //       binary32/bfloat16 use fl32(j * w32[i]).
 //     - wedge (i < 127): deferred.  The slot keeps the draw w,
 //       the generator writes an 8-byte record from which the test's uniform is
 //       rebuilt (G::snap) and moves past that uniform at once.  A lane holds up
 //       to kZRec records per batch; a further wedge is decided on the spot.
 //     - tail (i = 127, j >= k[127]; 0.06 % of draws): decided in the lane.
-//  B. at the end of the batch the warp's deferred wedges are tested 32 at a
-//     time, in binary32 with a proven margin (binary64 only inside it); an
-//     accepted slot gets RN(j w[i]), a rejected one is flagged.
-//  C. the rows are written with B lanes per row, skipping rejected slots; the
+//  B. at the end of the batch the warp's deferred wedges are listed and tested
+//     32 at a time, in binary32 with a proven margin (binary64 only inside it);
+//     an accepted slot gets RN(j w[i]), a rejected one is flagged.
+//  C. the rows are written, skipping rejected slots: binary64 rows by their own
+//     lanes in whole 32-byte sectors, the narrower types B lanes per row; the
 //     unit continues in the next batch.
 // The outputs of a unit are its accepted candidates in draw order: exactly the
 // sequence a one-variate-at-a-time loop produces.
@@ -1089,6 +1090,115 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// modified ziggurat (McFarland), binary64, batched
+// ---------------------------------------------------------------------------
+// The batch layout of z128_kernel: each lane owns a unit and writes its row of
+// B values (the carry in front) with the binary64 lane flush.  In phase A a lane
+// takes one nextLong U per iteration.  A fast draw (j = U & 255 < 253) gives
+// XS[j] m with m = U >> 11 < 2^53 (XS[j] = X[j] 2^-53), in one fused multiply-add:
+// with X' = XS[j] 2^52, m = h 2^52 + l and a = 1 + l 2^-52 (built from bits),
+// fma(a, X', h ? 0 : -X') = X' (l 2^-52 + h) = XS[j] m exactly before its one
+// rounding.  The table holds -X', so that both the addend and the multiplicand
+// come without a separate negation (a binary64 add on the narrow FP64 pipe).  A slow draw (an overhang or the tail, 1.2 % of draws) stops the
+// lane for the rest of the batch, its generator standing just after the draw;
+// after the loop each stopped lane finishes that draw's slow path, one divergent
+// pass per batch (inline, a warp would run it in about every third iteration).
+// No slot is rejected afterwards, so the rows have no holes.
+struct Z256Fast {
+    double XN[256][16];   // -XS[j] 2^52, 16 copies (a half warp reads without conflicts)
+};
+constexpr int kZ256Row = ZBatch<ZIG_F64>::B + 5;   // row stride in 8-byte words: carry in 1..3, slots from 4
+
+__host__ __device__ constexpr size_t z256_warp_bytes() { return (size_t)32 * kZ256Row * sizeof(uint64_t); }
+
+template <int PRNG>
+__global__ void __launch_bounds__(kZBlock, 1) z256_kernel(GenArgs a) {
+    using G = typename GenOf<PRNG>::T;
+    constexpr int B = ZBatch<ZIG_F64>::B;
+    constexpr uint32_t kSteps64 = PRNG == ZIG_LCG48 ? 2u : 1u;   // raw steps of one nextLong
+    __shared__ Z256Smem t;
+    __shared__ Z256Fast f;
+    extern __shared__ __align__(16) unsigned char z256_dsm[];
+    z256_load(t);
+    for (int k = threadIdx.x; k < 256 * 16; k += blockDim.x) f.XN[k >> 4][k & 15] = __dmul_rn(d_z256_XS[k >> 4], -0x1p52);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int n_warps = blockDim.x >> 5;
+    uint64_t* const row = (uint64_t*)(z256_dsm + (size_t)wib * z256_warp_bytes()) + lane * kZ256Row;
+    if (a.out == nullptr) {   // only legal when every length is zero
+        if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0)
+            atomicOr(&d_err, kErrNullOutput);
+        return;
+    }
+    const uint64_t n_units = units_total(a);
+    const uint64_t n_groups = (n_units + 31) >> 5;
+    const uint64_t warp_id = (uint64_t)blockIdx.x * n_warps + wib;
+    const uint64_t warp_stride = (uint64_t)gridDim.x * n_warps;
+    double* const out = (double*)a.out;
+
+    for (uint64_t grp = warp_id; grp < n_groups; grp += warp_stride) {
+        const uint64_t u = grp * 32 + lane;
+        uint64_t rem = 0;
+        double* dst = out;
+        G g;
+        g.seed(0);
+        if (u < n_units) {
+            uint64_t s, q, off, n;
+            unit_info(a, u, s, q, off, n);
+            g.seed(a.seeds[s]);
+            if (q) g.jump(q * kChunkDraws, &d_jump);
+            rem = n;
+            dst = out + off;
+        }
+        const bool check_chunk = a.chunk_log2 != 0 && rem != 0;
+        uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
+        int nc = 0;           // values carried to the next batch
+        while (__any_sync(kFull, rem > 0)) {
+            const int cnt = (int)umin64(rem, (uint64_t)B);
+            int slot = 0;
+            bool stopped = false;
+            uint64_t pend = 0;   // a stopped lane's slow draw
+#pragma unroll 2
+            for (int it = 0; it < B; ++it) {
+                // a lane draws while it has not stopped and still needs values
+                const bool act = !stopped && slot < cnt;
+                G gn = g;
+                const uint64_t U = gn.next_u64();
+                if (act) g = gn;
+                const uint32_t j = (uint32_t)U & 0xFFu;
+                const uint64_t m = U >> 11;
+                const uint32_t mh = (uint32_t)(m >> 32);
+                const double xn = f.XN[j][lane & 15];
+                const double av = __hiloint2double((int)(0x3FF00000u | (mh & 0xFFFFFu)), (int)(uint32_t)m);
+                const double x = __fma_rn(av, -xn, (mh >> 20) ? 0.0 : xn);
+                const bool fast = j < (uint32_t)zigtab::ZIG256_NR;
+                if (act && fast) row[4 + slot] = (uint64_t)__double_as_longlong(x) | ((U >> 8) & 1u) << 63;
+                slot += (act && fast) ? 1 : 0;
+                if (act && !fast) {
+                    stopped = true;
+                    pend = U;
+                }
+                draws += act ? kSteps64 : 0u;
+            }
+            if (__any_sync(kFull, stopped)) {
+                if (stopped) {
+                    uint32_t extra = 0;
+                    const double x = z256_slow(g, t, extra);   // x >= 0
+                    draws += extra;
+                    row[4 + slot] = (uint64_t)__double_as_longlong(x) | ((pend >> 8) & 1u) << 63;
+                    ++slot;
+                }
+            }
+            rem -= (uint64_t)slot;
+            z128_flush_f64<B>(row, 0u, slot, slot, rem == 0, dst, nc);
+        }
+        if (check_chunk && draws > kChunkDraws) atomicOr(&d_err, kErrChunkOverflow);
+    }
+}
+
 // Exhaustive check of the fast path's arithmetic against CUDA's IEEE operations:
 // RN(j * w[i]) by the fused multiply-add construction against __dmul_rn for all
 // 2^24 abscissae j of all 128 layers, and the bfloat16 rounding of every finite
@@ -1323,7 +1433,7 @@ static GenFn pick_dt(int dt, bool half_batch) {
         }
     } else {
         switch (dt) {
-        case ZIG_F64: return gen_kernel<ALG, PRNG, ZIG_F64>;
+        case ZIG_F64: return ALG == ZIG_ZIG256 ? z256_kernel<PRNG> : gen_kernel<ALG, PRNG, ZIG_F64>;
         case ZIG_F32: return gen_kernel<ALG, PRNG, ZIG_F32>;
         default: return gen_kernel<ALG, PRNG, ZIG_BF16>;
         }
@@ -1359,6 +1469,8 @@ static_assert(z128_fits<GenLcg48, ZIG_F64>() && z128_fits<GenLcg48, ZIG_F32>() &
                   z128_fits<GenL64X128Mix, ZIG_BF16>() && z128_fits<GenXoroshiro128PP, ZIG_F64>() &&
                   z128_fits<GenXoroshiro128PP, ZIG_F32>() && z128_fits<GenXoroshiro128PP, ZIG_BF16>(),
               "z128_kernel shared memory exceeds 227 KB per block");
+static_assert(sizeof(Z256Smem) + sizeof(Z256Fast) + z256_warp_bytes() * kZWarps <= 227 * 1024,
+              "z256_kernel shared memory exceeds 227 KB per block");
 
 // Exactly the per-warp bytes the kernel instantiation for (G, dt, batch width)
 // indexes (its carry rows depend on the output type, not only the staging word).
@@ -1374,6 +1486,7 @@ static size_t z128_dyn_for(int dt, bool half_batch, int warps) {
 }
 
 static size_t dyn_smem_of(int alg, int dt, int prng, bool half_batch = false, int block = kZBlock) {
+    if (alg == ZIG_ZIG256 && dt == ZIG_F64) return z256_warp_bytes() * (size_t)(block / 32);
     if (alg != ZIG_ZIG128) return 0;
     const int warps = block / 32;
     return prng == ZIG_LCG48 ? z128_dyn_for<GenLcg48>(dt, half_batch, warps)
@@ -1474,7 +1587,7 @@ static zig_status launch_gen(int alg, int prng, int dt, int dev, bool variable, 
     const bool z128 = alg == ZIG_ZIG128;
     const LaunchCfg c = force ? *force : z128 ? cfg_of(dev, prng, dt, variable) : default_cfg(dt);
     const bool half = z128 && c.batch != default_batch(dt);
-    const int block = z128 ? (int)c.block : kBlock;
+    const int block = z128 ? (int)c.block : (alg == ZIG_ZIG256 && dt == ZIG_F64) ? kZBlock : kBlock;
     a.lane_sectors = (z128 && c.store_bytes == 32) ? 1u : 0u;
     GenFn fn = pick(alg, prng, dt, half);
     const size_t dyn = dyn_smem_of(alg, dt, prng, half, block);
