@@ -1181,8 +1181,8 @@ __global__ void __launch_bounds__(kZBlock, 1) z256_kernel(GenArgs a) {
                     stopped = true;
                     pend = U;
                 }
-                draws += act ? kSteps64 : 0u;
             }
+            draws += (uint64_t)kSteps64 * (uint64_t)(slot + (stopped ? 1 : 0));   // one nextLong per active iteration
             if (__any_sync(kFull, stopped)) {
                 if (stopped) {
                     uint32_t extra = 0;
