@@ -140,6 +140,18 @@ def test_ragged_uniform(Z, n, L):
     check(Z, "splitmix64", "zig128", W.seeds(n), uniform_len=L)
 
 
+@pytest.mark.parametrize("prng", PRNGS)
+@pytest.mark.parametrize("chunk_log2", [0, 10])
+def test_zig256_f64_variable_and_ragged(Z, prng, chunk_log2):
+    """The batched modified-ziggurat kernel on rows that start inside a 32-byte sector,
+    end mid-batch, or are empty."""
+    L = W.batched_lengths(300, seed=11, max_log2=13)
+    L[::13] = 0
+    L[1::7] = 17
+    check(Z, prng, "zig256", W.seeds(300), lengths=L, chunk_log2=chunk_log2)
+    check(Z, prng, "zig256", W.seeds(33), uniform_len=17)
+
+
 def test_degenerate_lengths(Z):
     L = np.zeros(50, dtype=np.uint64)
     assert gen(Z, "lcg48", "zig128", W.seeds(50), lengths=L).size == 0
