@@ -158,6 +158,25 @@ __device__ __forceinline__ double zlog(double x) {
     return __dadd_rn(hi, __dadd_rn(r, lo));
 }
 
+// binary64 value of an integer m < 2^53 (exact), scaled by 2^-k, built with
+// integer operations: GB300's conversion to binary64 runs on the narrow binary64 pipe.
+__device__ __forceinline__ double u53_to_double(uint64_t m, int k = 0) {
+    const int lz = __clzll((long long)m);   // 11..63 (64 for m = 0)
+    const uint64_t frac = ((m << (lz & 63)) >> 11) & ((1ull << 52) - 1);
+    const uint64_t bits = ((uint64_t)(1086 - lz - k) << 52) | frac;
+    return m ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+// 2 u - 1 for u = m 2^-53 (m < 2^53): the two roundings of RN(RN(2 u) - 1) are
+// exact, and the value is (m - 2^52) 2^-52, built here with integer operations
+// (GB300's binary64 pipe is narrow; the polar method spends it on log, division
+// and square root).
+__device__ __forceinline__ double polar_v(uint64_t m) {
+    const int64_t d = (int64_t)m - (1ll << 52);   // |d| < 2^52
+    const double r = u53_to_double((uint64_t)(d < 0 ? -d : d), 52);
+    return d < 0 ? __longlong_as_double(__double_as_longlong(r) ^ (long long)(1ull << 63)) : r;
+}
+
 template <class G>
 __device__ __forceinline__ double polar_f64(G& g, bool& have, double& cached, uint32_t& extra) {
     if (have) {
@@ -167,8 +186,8 @@ __device__ __forceinline__ double polar_f64(G& g, bool& have, double& cached, ui
     constexpr uint32_t kStepsPerDouble = std::is_same<G, GenLcg48>::value ? 2u : 1u;
     double v1, v2, s;
     do {
-        v1 = __dsub_rn(__dmul_rn(2.0, m53_to_double(g.next_m53())), 1.0);
-        v2 = __dsub_rn(__dmul_rn(2.0, m53_to_double(g.next_m53())), 1.0);
+        v1 = polar_v(g.next_m53());
+        v2 = polar_v(g.next_m53());
         s = __dadd_rn(__dmul_rn(v1, v1), __dmul_rn(v2, v2));
         extra += 2 * kStepsPerDouble;
     } while (s >= 1.0 || s == 0.0);
@@ -191,15 +210,6 @@ __device__ __forceinline__ void z256_load(Z256Smem& t) {
         t.THR[i] = d_z256_THR[i];
         t.ALIAS[i] = d_z256_ALIAS[i];
     }
-}
-
-// binary64 value of an integer m < 2^53 (exact), scaled by 2^-k, built with
-// integer operations: GB300's conversion to binary64 runs on the narrow binary64 pipe.
-__device__ __forceinline__ double u53_to_double(uint64_t m, int k = 0) {
-    const int lz = __clzll((long long)m);   // 11..63 (64 for m = 0)
-    const uint64_t frac = ((m << (lz & 63)) >> 11) & ((1ull << 52) - 1);
-    const uint64_t bits = ((uint64_t)(1086 - lz - k) << 52) | frac;
-    return m ? __longlong_as_double((long long)bits) : 0.0;
 }
 
 // binary32 filter for an overhang test y < exp(-x^2/2): x = ox + odx u, y = oy + ody v
