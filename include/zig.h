@@ -338,7 +338,6 @@ zig_status zig_device_status(int device, int clear);
 /* Human-readable name of a status code (static storage). */
 const char *zig_status_string(zig_status status);
 
-/* Library version as major * 10000 + minor * 100 + patch. */
 /*
  * zig_selfcheck -- exhaustive check of the fast path's arithmetic on the current
  * device (test support; the paper has no counterpart).  Computes RN(j * w[i]) by
@@ -354,6 +353,7 @@ const char *zig_status_string(zig_status status);
  */
 zig_status zig_selfcheck(uint64_t counts_host[6]);
 
+/* Library version as major * 10000 + minor * 100 + patch. */
 int zig_version(void);
 
 #ifdef __cplusplus
