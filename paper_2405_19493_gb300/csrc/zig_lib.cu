@@ -1110,11 +1110,12 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
 // with X' = XS[j] 2^52, m = h 2^52 + l and a = 1 + l 2^-52 (built from bits),
 // fma(a, X', h ? 0 : -X') = X' (l 2^-52 + h) = XS[j] m exactly before its one
 // rounding.  The table holds -X', so that both the addend and the multiplicand
-// come without a separate negation (a binary64 add on the narrow FP64 pipe).  A slow draw (an overhang or the tail, 1.2 % of draws) stops the
-// lane for the rest of the batch, its generator standing just after the draw;
-// after the loop each stopped lane finishes that draw's slow path, one divergent
-// pass per batch (inline, a warp would run it in about every third iteration).
-// No slot is rejected afterwards, so the rows have no holes.
+// come without a separate negation (a binary64 add on the narrow FP64 pipe).
+// A slow draw (an overhang or the tail, 1.2 % of draws) stops the lane for the
+// rest of the batch, its generator standing just after the draw; after the loop
+// each stopped lane finishes that draw's slow path, one divergent pass per batch
+// (inline, a warp would run it in about every third iteration).  No slot is
+// rejected afterwards, so the rows have no holes.
 struct Z256Fast {
     double XN[256][16];   // -XS[j] 2^52, 16 copies (a half warp reads without conflicts)
 };
