@@ -5,6 +5,8 @@ population larger than the budget, batching of requests that queue up, and the
 latency statistics.
 """
 
+import time
+
 import pytest
 
 from paper_2405_19493_gb300 import _binding as B
@@ -14,9 +16,11 @@ FAKE = 1 << 20   # a non-null pointer; dry runs never dereference it
 
 
 def test_dry_run_admission_and_batching():
-    budget = 64 << 20   # 64 MiB
+    # 256 MiB requests: a dry launch lasts about 0.27 ms, long enough that requests
+    # submitted meanwhile queue up and are batched however the submitting loop runs
+    budget = 2 << 30   # 2 GiB: eight requests in flight
     with MutationServer(device=-1, budget_bytes=budget, n_slots=2, max_batch=8) as srv:
-        tickets = [srv.submit(None, 0.5, k, P=64, L=32768, x_ptr=FAKE) for k in range(40)]   # 8 MiB each
+        tickets = [srv.submit(None, 0.5, k, P=2048, L=32768, x_ptr=FAKE) for k in range(40)]
         srv.drain(timeout_s=30)
         st = srv.stats()
         assert st["completed"] == 40 and st["failed"] == 0
@@ -44,16 +48,22 @@ def test_dry_run_budget_refusal_and_invalid():
 
 
 def test_dry_run_fifo_under_memory_pressure():
-    # each request needs the whole budget: they must run one at a time, in order
-    budget = 4 << 20
+    # each request needs the whole budget: they must run one at a time, in order.  A dry
+    # launch of 2 GiB lasts about 2 ms, so consecutive starts are 2 ms apart however the
+    # submitting loop is scheduled.
+    P, L = 32768, 16384                       # 2 GiB of binary32
+    budget = P * L * 4
     with MutationServer(device=-1, budget_bytes=budget, n_slots=4, max_batch=16) as srv:
-        tickets = [srv.submit(None, 0.3, k, P=1024, L=1024, x_ptr=FAKE) for k in range(6)]
+        tickets, t_sub = [], []
+        for k in range(6):
+            t_sub.append(time.perf_counter())
+            tickets.append(srv.submit(None, 0.3, k, P=P, L=L, x_ptr=FAKE))
         srv.drain(timeout_s=30)
         st = srv.stats()
         assert st["peak_busy_slots"] == 1 and st["batches"] == 6
-        # one at a time in arrival order: each waits at least as long as the one before
-        q = [srv.query(t)["queue_us"] for t in tickets]
-        assert all(q[k] <= q[k + 1] + 1e-6 for k in range(5))
+        # start = submit + queue time (the submit stamp is taken just before the call)
+        start = [t_sub[k] + srv.query(t)["queue_us"] * 1e-6 for k, t in enumerate(tickets)]
+        assert all(start[k] < start[k + 1] + 2e-4 for k in range(5)), start
         assert all(srv.query(t)["latency_us"] > 0 for t in tickets)
 
 
