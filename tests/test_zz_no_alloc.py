@@ -53,9 +53,11 @@ def _case(n, max_log2, seed, base):
 def test_noalloc_matches_generate_on_two_calls_in_a_row(Z):
     lib = Z.load()
     # call 1: a large batch (chunked); call 2: a smaller one (sequential streams,
-    # binary32), which must not see anything call 1 left in the shared array
+    # binary32), which must not see anything call 1 left in the shared array; call 3:
+    # the batched modified-ziggurat kernel (binary64, chunked)
     cases = [("l64x128mix", "zig128", 10, "f64", _case(3000, 16, 7, 0x5EED)),
-             ("lcg48", "zig256", 0, "f32", _case(700, 12, 8, 0xABC))]
+             ("lcg48", "zig256", 0, "f32", _case(700, 12, 8, 0xABC)),
+             ("splitmix64", "zig256", 10, "f64", _case(900, 13, 9, 0x123))]
     refs, outs = [], []
     for prng, alg, c, dt, (s, ln, total) in cases:
         tdt = torch.float64 if dt == "f64" else torch.float32
