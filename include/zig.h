@@ -195,7 +195,7 @@ typedef struct {
     uint32_t block;
     uint32_t batch;
     uint32_t store_bytes;
-    uint32_t reserved; /* 0 */
+    uint32_t fma_of_4;
 } zig_launch_config;
 
 /* The recorded configuration (the default if none was set). No CUDA call. */

@@ -50,12 +50,13 @@ class Mutation(C.Structure):
 
 
 class LaunchConfig(C.Structure):
-    """zig_launch_config: block size, batch width and store width of the 128-level kernel."""
+    """zig_launch_config: block size, batch width, store width and (binary64) fma share of the 128-level kernel."""
     _fields_ = [("block", C.c_uint32), ("batch", C.c_uint32), ("store_bytes", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("fma_of_4", C.c_uint32)]
 
     def as_dict(self):
-        return {"block": self.block, "batch": self.batch, "store_bytes": self.store_bytes}
+        return {"block": self.block, "batch": self.batch, "store_bytes": self.store_bytes,
+                "fma_of_4": self.fma_of_4}
 
 
 class ServingStats(C.Structure):
@@ -243,10 +244,11 @@ def zig_launch_config_get(prng: str, dtype: str, variable_lengths: bool, device:
 
 def zig_launch_config_set(prng: str, dtype: str, variable_lengths: bool, cfg=None,
                           device: int = 0) -> None:
-    """cfg: a dict with block, batch and store_bytes, or None for the default."""
+    """cfg: a dict with block, batch, store_bytes (and fma_of_4 for f64), or None for the default."""
     ptr = None
     if cfg is not None:
-        ptr = C.byref(LaunchConfig(int(cfg["block"]), int(cfg["batch"]), int(cfg["store_bytes"]), 0))
+        ptr = C.byref(LaunchConfig(int(cfg["block"]), int(cfg["batch"]), int(cfg["store_bytes"]),
+                                   int(cfg.get("fma_of_4", 0))))
     _check(load().zig_launch_config_set(device, PRNG[prng], DTYPE[dtype], int(bool(variable_lengths)),
                                         ptr), "zig_launch_config_set")
 

@@ -1,0 +1,420 @@
+// 128-level ziggurat with binary64 output: the speculative batch kernel.
+// Included by zig_lib.cu after the samplers, the unit helpers and z256_kernel.
+//
+// Each lane owns one unit (a stream, or a 2^c chunk of one) with its generator
+// in registers; a warp works on its 32 units in batches of B draws per lane,
+// B = 32 - 2 kU (kU = raw steps per nextDouble), so that a batch with the
+// draws a tail may need past it fills exactly 32 slots of the lane's row.
+//  A. Every lane takes B draws in lockstep and keeps each in its row, with no
+//     branch and no vote: the fast test j < k[i] (Sec. 1; the GSL form's first
+//     comparison) only sets a bit of the lane's mask nf.  A slot holds the
+//     32-bit draw w, or for the generators whose draws are nextLong outputs the
+//     whole output (a wedge or tail test may read it as its uniform).
+//  B. Each lane walks its nf bits in draw order.  A slow candidate at draw p
+//     (j >= k[i]) consumes the next kU (wedge, i < 127) or 2 kU (tail) draws as
+//     its uniforms; a consumed draw is not a candidate, whatever its bit says.
+//     A lane whose last slow candidate needs draws past the batch takes them
+//     now.  The warp lists its slow candidates and decides them 32 at a time,
+//     the wedge and tail tests first in binary32 with proven margins.  A
+//     rejected candidate and every consumed draw are dropped; an accepted
+//     tail's value is written over its first uniform's slot(s).
+//  C. The warp writes its rows one at a time, all 32 lanes on one row, lane c
+//     on slot c: a kept slot's output index is the number of kept slots below
+//     it, so one store instruction writes the row's batch as one contiguous
+//     run (about 240 bytes) at any alignment, with no close-up of the row and
+//     no carry between batches.  Each lane rebuilds its value x = sign RN(j w[i])
+//     from the draw: one binary64 fma, or for every fourth row the same
+//     correctly rounded product in 32-bit integer arithmetic (the narrow
+//     binary64 pipe and the integer pipes share the work).
+// A unit's outputs are its accepted candidates in draw order: the sequence a
+// one-variate-at-a-time loop produces (Sec. 2, Listing 2, repeated).
+#pragma once
+
+namespace zf {
+
+// ---- per-generator draws ----
+// SW: 32-bit words per slot.  draw(): one raw step, stored at the slot; the
+// candidate w is the slot's last word.  m53(st, d, s0): the 53-bit integer of
+// the nextDouble that starts at batch draw d, from the row's slots (and, for
+// SplitMix64, the batch's first state s0).
+template <int PRNG> struct Gen;
+template <> struct Gen<ZIG_LCG48> {
+    using G = GenLcg48;
+    static constexpr int kU = 2, SW = 1;   // nextDouble = next(26), next(27)
+    static __device__ __forceinline__ void draw(G& g, uint32_t* slot, uint32_t& w) { w = g.step(32); slot[0] = w; }
+    static __device__ __forceinline__ uint64_t m53(const uint32_t* st, int d, uint64_t) {
+        // next(26) = s1 >> 22 = w1 >> 6, next(27) = s2 >> 21 = w2 >> 5 (w = s >> 16)
+        return ((uint64_t)(st[d] >> 6) << 27) + (st[d + 1] >> 5);
+    }
+    static __device__ __forceinline__ uint64_t first_state(const G& g) { return g.s; }
+};
+template <> struct Gen<ZIG_SPLITMIX64> {
+    using G = GenSplitMix64;
+    static constexpr int kU = 1, SW = 1;
+    static __device__ __forceinline__ void draw(G& g, uint32_t* slot, uint32_t& w) { w = g.next_u32(); slot[0] = w; }
+    static __device__ __forceinline__ uint64_t m53(const uint32_t*, int d, uint64_t s0) {
+        return mix64(s0 + (uint64_t)(d + 1) * kGamma) >> 11;   // the state of draw d
+    }
+    static __device__ __forceinline__ uint64_t first_state(const G& g) { return g.s; }
+};
+template <> struct Gen<ZIG_L64X128MIX> {
+    using G = GenL64X128Mix;
+    static constexpr int kU = 1, SW = 2;
+    // nextLong without the mixer's last z ^= z >> 32, which changes only the
+    // low word (the candidate is the high word); m53 applies it.
+    static __device__ __forceinline__ void draw(G& g, uint32_t* slot, uint32_t& w) {
+        uint64_t z = g.s + g.x0;
+        z = (z ^ (z >> 32)) * kLeaM;
+        z = (z ^ (z >> 32)) * kLeaM;
+        g.advance();
+        *(uint64_t*)slot = z;
+        w = (uint32_t)(z >> 32);
+    }
+    static __device__ __forceinline__ uint64_t m53(const uint32_t* st, int d, uint64_t) {
+        const uint64_t z = *(const uint64_t*)(st + 2 * d);
+        return (z ^ (z >> 32)) >> 11;
+    }
+    static __device__ __forceinline__ uint64_t first_state(const G&) { return 0; }
+};
+template <> struct Gen<ZIG_XOROSHIRO128PP> {
+    using G = GenXoroshiro128PP;
+    static constexpr int kU = 1, SW = 2;
+    static __device__ __forceinline__ void draw(G& g, uint32_t* slot, uint32_t& w) {
+        const uint64_t r = g.next_u64();
+        *(uint64_t*)slot = r;
+        w = (uint32_t)(r >> 32);
+    }
+    static __device__ __forceinline__ uint64_t m53(const uint32_t* st, int d, uint64_t) {
+        return *(const uint64_t*)(st + 2 * d) >> 11;
+    }
+    static __device__ __forceinline__ uint64_t first_state(const G&) { return 0; }
+};
+
+// ---- shared memory ----
+// The fast table: one 256-byte block per signed layer ix = w & 0xFF (layer
+// ix & 127, positive when bit 7 is set).  Words 0..31: 8 copies of the entry
+// {low, high word of b = 2^52 w[i], eh | sign, K}, one per lane & 7, so that
+// the 8 lanes of a quarter warp reading 16-byte entries of random layers hit
+// distinct banks; words 32..63: 32 copies of K, one per lane.  K = k[i] << 8,
+// so j >= k[i] is w >= K; eh = (E(w[i]) + 30) << 20 is the exponent field of
+// the integer product; sign is bit 31 of the output's high word.  The block
+// stride of 256 bytes makes each address one byte permute of w.
+struct Tab {
+    uint32_t blk[256][64];
+};
+struct SlowTab {   // the wedge test's tables (z128_wedge_accept)
+    float W32[128], Y32[128], DY32[128];
+    double Wd[128], Y[128];
+};
+
+constexpr int kMaxThreads = 640;   // 20 warps: the register budget is 65536 / 640 = 102
+
+template <int PRNG>
+struct Warp {
+    static constexpr int kU = Gen<PRNG>::kU, SW = Gen<PRNG>::SW;
+    static constexpr int B = 32 - 2 * kU;                  // draws per batch
+    static constexpr int RS = SW == 1 ? 33 : 66;            // row stride in words
+    uint32_t stage[32 * RS];   // row r, slot d: words r RS + SW d ..
+    uint4 info[32];            // per row: output address (low, high), dropped slots, accepted tails
+    uint64_t s0[32];           // per row: the state before the batch's first draw (SplitMix64)
+    uint32_t drop[32];         // per row: candidates rejected in the decision pass
+    uint32_t lit[32];          // per row: accepted tails
+    uint32_t list[64];         // slow candidates: row | draw << 5 | tail << 10
+};
+template <int PRNG>
+__host__ __device__ constexpr size_t warp_bytes() {
+    return (sizeof(Warp<PRNG>) + 15) & ~(size_t)15;
+}
+__host__ __device__ constexpr size_t head_bytes() { return sizeof(Tab) + ((sizeof(SlowTab) + 15) & ~(size_t)15); }
+template <int PRNG>
+__host__ __device__ constexpr size_t smem_bytes(int warps) {
+    return head_bytes() + warp_bytes<PRNG>() * (size_t)warps;
+}
+
+__device__ __forceinline__ void tab_load(Tab& t, SlowTab& s) {
+    for (int k = threadIdx.x; k < 256 * 64; k += blockDim.x) {
+        const int ix = k >> 6, wd = k & 63, i = ix & 127;
+        const double wi = d_z128_W[i];
+        const uint32_t K = (d_z128_kE[i] & 0xFFFFFFu) << 8;
+        uint32_t v;
+        if (wd >= 32) {
+            v = K;
+        } else {
+            const long long b = __double_as_longlong(__dmul_rn(wi, 0x1p52));   // exact scaling
+            const uint32_t ew = (uint32_t)(__double_as_longlong(wi) >> 52) & 0x7FFu;
+            const uint32_t sign = ix < 128 ? 0x80000000u : 0u;
+            switch (wd & 3) {
+            case 0: v = (uint32_t)b; break;
+            case 1: v = (uint32_t)(b >> 32); break;
+            case 2: v = ((ew + 30u) << 20) | sign; break;
+            default: v = K; break;
+            }
+        }
+        t.blk[ix][wd] = v;
+    }
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+        s.W32[i] = d_z128_W32[i];
+        s.Y32[i] = d_z128_Y32[i];
+        s.DY32[i] = d_z128_DY32[i];
+        s.Wd[i] = d_z128_W[i];
+        s.Y[i] = d_z128_Y[i];
+    }
+}
+
+// RN(j w) for j < 2^24 and a 53-bit significand m (mlo, mhi: m << 11) in
+// 32-bit integer arithmetic, returned as binary64 bits with eh's sign: the
+// 77-bit product of j normalized (its top bit at bit 31) and m << 11 has its
+// top bit at bit 95 or 94; its high 64 bits, shifted left when bit 95 is clear
+// and with a sticky bit for the 32 bits below, round to 53 bits by adding
+// 2^10 - 1 plus the last kept bit; the carry of a round-up into 2^53 moves
+// into the exponent field.  j = 0 gives the signed zero.
+__device__ __forceinline__ uint64_t int_mul_jw(uint32_t j, uint32_t mlo, uint32_t mhi, uint32_t eh) {
+    const uint32_t s = __clz(j);
+    const uint32_t jn = __funnelshift_l(0u, j, s);   // j << s, 0 for s = 32
+    const uint64_t A = (uint64_t)jn * mlo;
+    const uint64_t Bp = (uint64_t)jn * mhi;
+    uint64_t H = Bp + (A >> 32);                      // product bits 32..95
+    const uint32_t t = (uint32_t)(H >> 63);
+    H <<= (1u - t);
+    H |= (uint32_t)A != 0u ? 1u : 0u;                 // sticky
+    const uint64_t M = (H + 0x3FFu + ((H >> 11) & 1u)) >> 11;   // in [2^52, 2^53]
+    const uint32_t hi = (uint32_t)(M >> 32) + eh + ((t - s) << 20);
+    return j ? ((uint64_t)hi << 32 | (uint32_t)M) : ((uint64_t)(eh & 0x80000000u) << 32);
+}
+
+// x = sign RN(j w[i]) for the draw w, as binary64 bits: one binary64 fma
+// fma(1 + j 2^-52, b, -b) with b = 2^52 w[i] (exact before its one rounding;
+// 1 + j 2^-52 is built from j's bits), or (kInt) int_mul_jw.
+template <bool kInt>
+__device__ __forceinline__ uint64_t x_of(const unsigned char* tab, uint32_t w, uint32_t copy16) {
+    const uint4 e = *(const uint4*)(tab + __byte_perm(w, copy16, 0x5504));   // block ix, copy
+    const uint32_t j = w >> 8;
+    if constexpr (kInt) {
+        const uint32_t mhi = __funnelshift_l(e.x, (e.y & 0xFFFFFu) | 0x100000u, 11);
+        return int_mul_jw(j, e.x << 11, mhi, e.z);
+    } else {
+        const double b = __hiloint2double((int)e.y, (int)e.x);
+        const double x = __fma_rn(__hiloint2double(0x3FF00000, (int)j), b, -b);
+        return (uint64_t)__double_as_longlong(x) | ((uint64_t)(e.z & 0x80000000u) << 32);
+    }
+}
+
+// Decide listed slow candidate `it` (row | draw << 5 | tail << 10), for the
+// lanes with has set (all 32 lanes call this): a rejected candidate is marked
+// in drop[row]; an accepted tail's value goes to the words of its first
+// uniform (the next slot, or two for 4-byte slots) and its slot is marked in
+// lit[row].  The binary64 wedge test and the tail step run only when some lane
+// needs them.
+template <int PRNG, class W>
+__device__ __forceinline__ void decide(W& ws, const SlowTab& slow, uint32_t it, bool has) {
+    using GT = Gen<PRNG>;
+    const int o = (int)(it & 31u), p = (int)((it >> 5) & 31u);
+    uint32_t* st = ws.stage + o * W::RS;
+    const bool wedge = has && !(it >> 10), tail = has && (it >> 10);
+    uint32_t w = 0;
+    uint64_t m1 = 0;
+    if (has) {
+        w = st[GT::SW * p + GT::SW - 1];
+        m1 = GT::m53(st, p + 1, ws.s0[o]);
+    }
+    int f = 1;
+    if (wedge) f = z128_wedge_filter(slow, w & 0x7Fu, w >> 8, m1);
+    if (__any_sync(kFull, f < 0)) {
+        if (f < 0) f = z128_wedge_exact(slow, w & 0x7Fu, w >> 8, m1) ? 1 : 0;
+    }
+    if (wedge && f == 0) atomicOr(&ws.drop[o], 1u << p);
+    if (__any_sync(kFull, tail)) {
+        if (tail) {
+            const double x = z128_tail(m1, GT::m53(st, p + 1 + GT::kU, ws.s0[o]));
+            if (x < 0.0) {
+                atomicOr(&ws.drop[o], 1u << p);
+            } else {
+                const uint64_t v = (uint64_t)__double_as_longlong(x) | (uint64_t)((~w >> 7) & 1u) << 63;
+                st[GT::SW * (p + 1)] = (uint32_t)v;   // the uniforms' words (dropped slots)
+                st[GT::SW * (p + 1) + 1] = (uint32_t)(v >> 32);
+                atomicOr(&ws.lit[o], 1u << p);
+            }
+        }
+    }
+}
+
+// Write row r of the warp's batch: lane c takes slot c (kInt: the integer
+// product).  An accepted tail's slot gets a value rebuilt from its draw here
+// and is rewritten afterwards by its row's lane.
+template <int PRNG, bool kInt, class W>
+__device__ __forceinline__ void write_row(const W& ws, const unsigned char* tb, int r, int lane, uint32_t lane_bit,
+                                          uint32_t lt_mask, uint32_t copy16) {
+    using GT = Gen<PRNG>;
+    const uint4 inf = ws.info[r];
+    const uint32_t w = ws.stage[r * W::RS + GT::SW * lane + GT::SW - 1];
+    const uint64_t v = x_of<kInt>(tb, w, copy16);
+    const uint32_t e = __popc(~inf.z & lt_mask);   // kept slots below this one
+    const uint64_t addr = ((uint64_t)inf.x | (uint64_t)inf.y << 32) + 8ull * e;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %2, 0;\n\t@p st.global.cs.b64 [%0], %1;\n\t}" ::"l"(addr), "l"(v),
+        "r"(inf.z & lane_bit)
+        : "memory");
+}
+
+template <int PRNG, int NDF>
+__global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
+    using GT = Gen<PRNG>;
+    using G = typename GT::G;
+    using W = Warp<PRNG>;
+    constexpr int kU = GT::kU, SW = GT::SW, B = W::B;
+    static_assert(NDF >= 2 && NDF <= 4, "rows per 4 with the binary64 fma");
+    extern __shared__ __align__(16) unsigned char zf_dsm[];
+    Tab& tab = *(Tab*)zf_dsm;
+    SlowTab& slow = *(SlowTab*)(zf_dsm + sizeof(Tab));
+    tab_load(tab, slow);
+    __syncthreads();
+    const unsigned char* const tb = zf_dsm;
+
+    const int lane = threadIdx.x & 31;
+    const uint32_t lane_bit = 1u << lane, lt_mask = lane_bit - 1u;
+    const int wib = threadIdx.x >> 5;
+    const int n_warps = blockDim.x >> 5;
+    W& ws = *(W*)(zf_dsm + head_bytes() + (size_t)wib * warp_bytes<PRNG>());
+    uint32_t* const row = ws.stage + lane * W::RS;
+    const uint32_t copy16 = (uint32_t)(lane & 7) << 4;    // this lane's copy of a fast entry
+    const uint32_t kcopy = 0x80u + ((uint32_t)lane << 2);  // this lane's copy of K
+
+    if (a.out == nullptr) {   // only legal when every length is zero
+        if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&d_err, kErrNullOutput);
+        return;
+    }
+    const uint64_t n_units = units_total(a);
+    const uint64_t n_groups = (n_units + 31) >> 5;
+    const uint64_t warp_id = (uint64_t)blockIdx.x * n_warps + wib;
+    const uint64_t warp_stride = (uint64_t)gridDim.x * n_warps;
+    double* const out = (double*)a.out;
+
+    for (uint64_t grp = warp_id; grp < n_groups; grp += warp_stride) {
+        const uint64_t u = grp * 32 + lane;
+        uint64_t rem = 0;
+        double* dst = out;
+        G g;
+        g.seed(0);
+        if (u < n_units) {
+            uint64_t s, q, off, n;
+            unit_info(a, u, s, q, off, n);
+            g.seed(a.seeds[s]);
+            if (q) g.jump(q * kChunkDraws, &d_jump);
+            rem = n;
+            dst = out + off;
+        }
+        const bool check_chunk = a.chunk_log2 != 0 && rem != 0;
+        uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
+        ws.drop[lane] = 0;
+        ws.lit[lane] = 0;
+
+        while (__any_sync(kFull, rem > 0)) {
+            // ---- A: B draws per lane, lockstep; nf marks the slow candidates ----
+            if constexpr (PRNG == ZIG_SPLITMIX64) ws.s0[lane] = GT::first_state(g);
+            uint32_t nf = 0;
+#pragma unroll
+            for (int d = 0; d < B; ++d) {
+                uint32_t w;
+                GT::draw(g, row + SW * d, w);
+                const uint32_t K = *(const uint32_t*)(tb + __byte_perm(w, kcopy, 0x5504));
+                nf |= (w >= K ? 1u : 0u) << d;
+            }
+            // ---- B: the slow candidates, in draw order; list, then decide ----
+            // Each lane walks its nf bits once: a bit not consumed by an earlier
+            // slow candidate is one (R; tails also in T), and consumes the next kU
+            // or 2 kU draws (du).  Draws past the batch for the last one are taken now.
+            uint32_t R = 0, T = 0, du = 0;
+            int ne = 0;
+            if (rem > 0) {
+                uint32_t m = nf;
+                while (m) {
+                    const int p = __ffs(m) - 1;
+                    const uint32_t w = row[SW * p + SW - 1];
+                    const bool tail = (w & 0x7Fu) == 0x7Fu;
+                    const int need = tail ? 2 * kU : kU;
+                    const int last = p + need;   // the last draw it consumes (< 32)
+                    R |= 1u << p;
+                    T |= tail ? 1u << p : 0u;
+                    du |= ((1u << need) - 1u) << (p + 1);
+                    m &= last >= 31 ? 0u : ~0u << (last + 1);
+                }
+                const int lastU = du ? 31 - __clz(du) : -1;
+                while (B + ne <= lastU) {   // past the batch (rare)
+                    uint32_t wx;
+                    GT::draw(g, row + SW * (B + ne), wx);
+                    ++ne;
+                }
+            }
+            // list them in lane order: this lane's first at the exclusive prefix sum of the counts
+            const int cnt = __popc(R);
+            int incl = cnt;
+#pragma unroll
+            for (int dd = 1; dd < 32; dd <<= 1) {
+                const int t = __shfl_up_sync(kFull, incl, dd);
+                if (lane >= dd) incl += t;
+            }
+            const int n_items = __shfl_sync(kFull, incl, 31);
+            for (int b0 = 0; b0 < n_items; b0 += 64) {   // 64 at a time (more is rare)
+                int idx = incl - cnt;
+                for (uint32_t m = R; m; m &= m - 1u, ++idx) {
+                    if (idx >= b0 && idx < b0 + 64) {
+                        const int p = __ffs(m) - 1;
+                        ws.list[idx - b0] = (uint32_t)lane | (uint32_t)p << 5 | ((T >> p) & 1u) << 10;
+                    }
+                }
+                __syncwarp();
+                decide<PRNG>(ws, slow, ws.list[lane], b0 + lane < n_items);
+                if (b0 + 32 < n_items) decide<PRNG>(ws, slow, ws.list[32 + lane], b0 + 32 + lane < n_items);
+                __syncwarp();
+            }
+            // ---- C: drops, the unit's end, then the rows ----
+            const int n = B + ne;   // slots drawn
+            uint32_t D = du | ws.drop[lane] | (n >= 32 ? 0u : (~0u << n));
+            const uint32_t L = ws.lit[lane];
+            ws.drop[lane] = 0;
+            ws.lit[lane] = 0;
+            const int kept = 32 - __popc(D);
+            int k_out = kept;
+            if ((uint64_t)kept >= rem) {   // the unit ends in this batch: keep rem outputs
+                k_out = (int)rem;
+                uint32_t keepm = ~D;
+                for (int m = 0; m < k_out; ++m) keepm &= keepm - 1u;   // the slots past the rem-th kept one
+                D |= keepm;
+                if (check_chunk && k_out > 0) {
+                    // the draws up to the last output and its uniforms
+                    const int c = 31 - __clz(~D);   // slot of the last output
+                    int used = c + 1;
+                    while (used < n && ((du >> used) & 1u)) ++used;
+                    draws += (uint64_t)used;
+                }
+            } else if (check_chunk) {
+                draws += (uint64_t)n;
+            }
+            ws.info[lane] = make_uint4((uint32_t)(uintptr_t)dst, (uint32_t)((uintptr_t)dst >> 32), D, L);
+            __syncwarp();
+#pragma unroll 2
+            for (int r = 0; r < 32; r += 4) {
+                write_row<PRNG, (0 >= NDF)>(ws, tb, r + 0, lane, lane_bit, lt_mask, copy16);
+                write_row<PRNG, (1 >= NDF)>(ws, tb, r + 1, lane, lane_bit, lt_mask, copy16);
+                write_row<PRNG, (2 >= NDF)>(ws, tb, r + 2, lane, lane_bit, lt_mask, copy16);
+                write_row<PRNG, (3 >= NDF)>(ws, tb, r + 3, lane, lane_bit, lt_mask, copy16);
+            }
+            // accepted tails: the row's lane rewrites each kept one's output
+            const uint32_t Lk = L & ~D;
+            if (__any_sync(kFull, Lk != 0)) {
+                __syncwarp();
+                for (uint32_t m = Lk; m; m &= m - 1u) {
+                    const int p = __ffs(m) - 1;
+                    const uint64_t v = (uint64_t)row[SW * (p + 1)] | (uint64_t)row[SW * (p + 1) + 1] << 32;
+                    __stcs((unsigned long long*)dst + __popc(~D & ((1u << p) - 1u)), (unsigned long long)v);
+                }
+            }
+            dst += k_out;
+            rem -= (uint64_t)k_out;
+            __syncwarp();
+        }
+        if (check_chunk && draws > kChunkDraws) atomicOr(&d_err, kErrChunkOverflow);
+    }
+}
+
+}  // namespace zf

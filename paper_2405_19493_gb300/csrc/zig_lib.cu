@@ -460,18 +460,29 @@ __device__ __forceinline__ float m53_to_float(uint64_t m) {
 // binary32 when |y32 - e32| clears 2^-16 e32 (the binary32 errors are
 // |y32/y - 1| + |e32/e - 1| <= 2.6e-6, expf within 2 ulp); inside the margin
 // the binary64 definition decides.
+// z128_wedge_filter: 1 accept, 0 reject, -1 inside the margin;
+// z128_wedge_exact: the binary64 definition.
 template <class Tab>
-__device__ __forceinline__ bool z128_wedge_accept(const Tab& t, uint32_t i, uint32_t j, uint64_t m1) {
+__device__ __forceinline__ int z128_wedge_filter(const Tab& t, uint32_t i, uint32_t j, uint64_t m1) {
     const float x32 = __fmul_rn((float)j, t.W32[i]);
     const float e32 = expf(__fmul_rn(__fmul_rn(-0.5f, x32), x32));
     const float u32 = (float)(uint32_t)(m1 >> 29) * 0x1p-24f;
     const float y32 = __fadd_rn(t.Y32[i + 1], __fmul_rn(t.DY32[i], u32));
-    if (y32 < e32 * (1.0f - 0x1p-16f)) return true;
-    if (y32 > e32 * (1.0f + 0x1p-16f)) return false;
+    if (y32 < e32 * (1.0f - 0x1p-16f)) return 1;
+    if (y32 > e32 * (1.0f + 0x1p-16f)) return 0;
+    return -1;
+}
+template <class Tab>
+__device__ __forceinline__ bool z128_wedge_exact(const Tab& t, uint32_t i, uint32_t j, uint64_t m1) {
     const double x = __dmul_rn((double)j, t.Wd[i]);
     const double U = m53_to_double(m1);
     const double y = __dadd_rn(t.Y[i + 1], __dmul_rn(__dsub_rn(t.Y[i], t.Y[i + 1]), U));
     return y < exp(neg_half_sq(x));
+}
+template <class Tab>
+__device__ __forceinline__ bool z128_wedge_accept(const Tab& t, uint32_t i, uint32_t j, uint64_t m1) {
+    const int f = z128_wedge_filter(t, i, j, m1);
+    return f >= 0 ? f == 1 : z128_wedge_exact(t, i, j, m1);
 }
 
 // RN(z / R) without a division: q = RN(z RN(1/R)) and one fused multiply-add
@@ -1210,6 +1221,8 @@ __global__ void __launch_bounds__(kZBlock, 1) z256_kernel(GenArgs a) {
     }
 }
 
+#include "z128_f64.cuh"
+
 // Exhaustive check of the fast path's arithmetic against CUDA's IEEE operations:
 // RN(j * w[i]) by the fused multiply-add construction against __dmul_rn for all
 // 2^24 abscissae j of all 128 layers, and the bfloat16 rounding of every finite
@@ -1434,11 +1447,22 @@ static zig_status current_device(int& dev) {
 
 typedef void (*GenFn)(GenArgs);
 
+// The binary64 128-level kernel with fma share `fma`: rows of every 4 whose
+// products use the binary64 fma (the others use the integer product).
+template <int PRNG>
+static GenFn pick_zf(int fma) {
+    switch (fma) {
+    case 2: return zf::z128f_kernel<PRNG, 2>;
+    case 3: return zf::z128f_kernel<PRNG, 3>;
+    default: return zf::z128f_kernel<PRNG, 4>;
+    }
+}
+
 template <int ALG, int PRNG>
-static GenFn pick_dt(int dt, bool half_batch) {
+static GenFn pick_dt(int dt, bool half_batch, int fma) {
     if constexpr (ALG == ZIG_ZIG128) {
         switch (dt) {
-        case ZIG_F64: return half_batch ? z128_kernel<PRNG, ZIG_F64, 0, 10> : z128_kernel<PRNG, ZIG_F64, 0>;
+        case ZIG_F64: return pick_zf<PRNG>(fma);
         case ZIG_F32: return half_batch ? z128_kernel<PRNG, ZIG_F32, 0, 16> : z128_kernel<PRNG, ZIG_F32, 0>;
         default: return half_batch ? z128_kernel<PRNG, ZIG_BF16, 0, 16> : z128_kernel<PRNG, ZIG_BF16, 0>;
         }
@@ -1451,19 +1475,19 @@ static GenFn pick_dt(int dt, bool half_batch) {
     }
 }
 template <int ALG>
-static GenFn pick_prng(int prng, int dt, bool half_batch) {
+static GenFn pick_prng(int prng, int dt, bool half_batch, int fma) {
     switch (prng) {
-    case ZIG_LCG48: return pick_dt<ALG, 0>(dt, half_batch);
-    case ZIG_SPLITMIX64: return pick_dt<ALG, 1>(dt, half_batch);
-    case ZIG_L64X128MIX: return pick_dt<ALG, 2>(dt, half_batch);
-    default: return pick_dt<ALG, 3>(dt, half_batch);
+    case ZIG_LCG48: return pick_dt<ALG, 0>(dt, half_batch, fma);
+    case ZIG_SPLITMIX64: return pick_dt<ALG, 1>(dt, half_batch, fma);
+    case ZIG_L64X128MIX: return pick_dt<ALG, 2>(dt, half_batch, fma);
+    default: return pick_dt<ALG, 3>(dt, half_batch, fma);
     }
 }
-static GenFn pick(int alg, int prng, int dt, bool half_batch = false) {
+static GenFn pick(int alg, int prng, int dt, bool half_batch = false, int fma = 4) {
     switch (alg) {
-    case ZIG_ZIG128: return pick_prng<ZIG_ZIG128>(prng, dt, half_batch);
-    case ZIG_POLAR: return pick_prng<ZIG_POLAR>(prng, dt, false);
-    default: return pick_prng<ZIG_ZIG256>(prng, dt, false);
+    case ZIG_ZIG128: return pick_prng<ZIG_ZIG128>(prng, dt, half_batch, fma);
+    case ZIG_POLAR: return pick_prng<ZIG_POLAR>(prng, dt, false, fma);
+    default: return pick_prng<ZIG_ZIG256>(prng, dt, false, fma);
     }
 }
 
@@ -1496,10 +1520,28 @@ static size_t z128_dyn_for(int dt, bool half_batch, int warps) {
     return per * (size_t)warps;
 }
 
+// Shared memory of the binary64 128-level kernel: tables plus one warp area per warp.
+static size_t zf_smem(int prng, int warps) {
+    switch (prng) {
+    case ZIG_LCG48: return zf::smem_bytes<0>(warps);
+    case ZIG_SPLITMIX64: return zf::smem_bytes<1>(warps);
+    case ZIG_L64X128MIX: return zf::smem_bytes<2>(warps);
+    default: return zf::smem_bytes<3>(warps);
+    }
+}
+// The most threads a block of that kernel can have: as many warps as one SM's
+// shared memory holds (227 KB per block), at most zf::kMaxThreads.
+static int zf_max_block(int prng) {
+    int w = zf::kMaxThreads / 32;
+    while (w > 1 && zf_smem(prng, w) > 227 * 1024) --w;
+    return 32 * w;
+}
+
 static size_t dyn_smem_of(int alg, int dt, int prng, bool half_batch = false, int block = kZBlock) {
     if (alg == ZIG_ZIG256 && dt == ZIG_F64) return z256_warp_bytes() * (size_t)(block / 32);
     if (alg != ZIG_ZIG128) return 0;
     const int warps = block / 32;
+    if (dt == ZIG_F64) return zf_smem(prng, warps);
     return prng == ZIG_LCG48 ? z128_dyn_for<GenLcg48>(dt, half_batch, warps)
          : prng == ZIG_SPLITMIX64 ? z128_dyn_for<GenSplitMix64>(dt, half_batch, warps)
          : prng == ZIG_L64X128MIX ? z128_dyn_for<GenL64X128Mix>(dt, half_batch, warps)
@@ -1511,22 +1553,29 @@ static size_t dyn_smem_of(int alg, int dt, int prng, bool half_batch = false, in
 // array): threads per block, batch width and store width.  Any choice gives
 // the same outputs; zig_autotune times the candidates and keeps the fastest.
 struct LaunchCfg {
-    uint32_t block, batch, store_bytes;
+    uint32_t block, batch, store_bytes, fma;
 };
 static LaunchCfg g_cfg[kMaxDevices][4][3][2];
 static bool g_cfg_set[kMaxDevices][4][3][2];
 
-static uint32_t default_batch(int dt) { return dt == ZIG_F64 ? 20u : 32u; }
-// binary64 rows go out in per-lane 32-byte sectors, the narrower types in
-// warp-cooperative element stores (each measured the faster for its type)
+static uint32_t default_batch(int dt) { (void)dt; return 32u; }
+// binary64: values of every 4 whose exact product uses the binary64 fma (the
+// rest use the integer product), by generator
+static uint32_t default_fma(int prng) { return prng == ZIG_L64X128MIX ? 3u : 2u; }
+// binary64 rows go out as warp-wide runs, one row per store (the kernel's only
+// form); the narrower types in warp-cooperative element stores
 static LaunchCfg default_cfg(int dt) {
-    return LaunchCfg{(uint32_t)kZBlock, default_batch(dt), dt == ZIG_F64 ? 32u : 0u};
+    if (dt == ZIG_F64) return LaunchCfg{(uint32_t)zf::kMaxThreads, 32u, 0u, 0u};
+    return LaunchCfg{(uint32_t)kZBlock, default_batch(dt), 0u, 0u};
 }
 
 static bool cfg_valid(int dt, const LaunchCfg& c) {
     const uint32_t b = default_batch(dt);
-    return c.block >= 64 && c.block <= (uint32_t)kZBlock && c.block % 32 == 0 &&
-           (c.batch == b || c.batch == b / 2) && (c.store_bytes == 0 || c.store_bytes == 32);
+    if (!(c.block >= 64 && c.block % 32 == 0 && (c.batch == b || c.batch == b / 2))) return false;
+    if (dt == ZIG_F64)
+        return c.block <= (uint32_t)zf::kMaxThreads && c.batch == b && c.store_bytes == 0 &&
+               (c.fma == 0 || (c.fma >= 2 && c.fma <= 4));
+    return c.block <= (uint32_t)kZBlock && (c.store_bytes == 0 || c.store_bytes == 32) && c.fma == 0;
 }
 
 static LaunchCfg cfg_of(int dev, int prng, int dt, bool variable) {
@@ -1598,9 +1647,11 @@ static zig_status launch_gen(int alg, int prng, int dt, int dev, bool variable, 
     const bool z128 = alg == ZIG_ZIG128;
     const LaunchCfg c = force ? *force : z128 ? cfg_of(dev, prng, dt, variable) : default_cfg(dt);
     const bool half = z128 && c.batch != default_batch(dt);
-    const int block = z128 ? (int)c.block : (alg == ZIG_ZIG256 && dt == ZIG_F64) ? kZBlock : kBlock;
+    int block = z128 ? (int)c.block : (alg == ZIG_ZIG256 && dt == ZIG_F64) ? kZBlock : kBlock;
+    if (z128 && dt == ZIG_F64) block = std::min(block, zf_max_block(prng));
     a.lane_sectors = (z128 && c.store_bytes == 32) ? 1u : 0u;
-    GenFn fn = pick(alg, prng, dt, half);
+    const int fma = c.fma ? (int)c.fma : (int)default_fma(prng);
+    GenFn fn = pick(alg, prng, dt, half, fma);
     const size_t dyn = dyn_smem_of(alg, dt, prng, half, block);
     if (!allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
     const int grid = grid_for((const void*)fn, dev, n_groups_hint, dyn, block);
@@ -1731,7 +1782,7 @@ zig_status zig_launch_config_get(int device, zig_prng prng, zig_dtype dtype, int
     cfg->block = c.block;
     cfg->batch = c.batch;
     cfg->store_bytes = c.store_bytes;
-    cfg->reserved = 0;
+    cfg->fma_of_4 = c.fma;
     return ZIG_OK;
 }
 
@@ -1745,7 +1796,7 @@ zig_status zig_launch_config_set(int device, zig_prng prng, zig_dtype dtype, int
         host::g_cfg_set[device][prng][dtype][v] = false;
         return ZIG_OK;
     }
-    const host::LaunchCfg c{cfg->block, cfg->batch, cfg->store_bytes};
+    const host::LaunchCfg c{cfg->block, cfg->batch, cfg->store_bytes, cfg->fma_of_4};
     if (!host::cfg_valid(dtype, c)) return ZIG_ERR_INVALID_ARG;
     host::g_cfg[device][prng][dtype][v] = c;
     host::g_cfg_set[device][prng][dtype][v] = true;
@@ -1753,9 +1804,19 @@ zig_status zig_launch_config_set(int device, zig_prng prng, zig_dtype dtype, int
 }
 
 uint32_t zig_autotune_candidates(zig_dtype dtype, zig_launch_config* cands, uint32_t max_cands) {
-    static const uint32_t blocks[] = {256, 384, 512, 768};
     const uint32_t b = host::default_batch((unsigned)dtype > 2u ? ZIG_F64 : dtype);
     uint32_t n = 0;
+    if (dtype == ZIG_F64) {
+        // blocks are clamped to what one SM's shared memory holds for the generator
+        static const uint32_t blocks[] = {256, 384, 512, 640};
+        for (uint32_t bl : blocks)
+            for (uint32_t fm : {2u, 3u, 4u}) {
+                if (cands && n < max_cands) cands[n] = zig_launch_config{bl, b, 0u, fm};
+                ++n;
+            }
+        return n;
+    }
+    static const uint32_t blocks[] = {256, 384, 512, 768};
     for (uint32_t bl : blocks)
         for (uint32_t bw : {b / 2, b})
             for (uint32_t sb : {0u, 32u}) {
@@ -1788,7 +1849,7 @@ zig_status zig_autotune(zig_prng prng, const uint64_t* seeds_dev, const uint64_t
     float best_t = -1.0f;
     uint32_t best_k = 0;
     for (uint32_t k = 0; k < nc && st == ZIG_OK; ++k) {
-        const host::LaunchCfg c{cands[k].block, cands[k].batch, cands[k].store_bytes};
+        const host::LaunchCfg c{cands[k].block, cands[k].batch, cands[k].store_bytes, cands[k].fma_of_4};
         // one untimed launch, then `reps` timed back to back on the caller's stream
         for (uint32_t r = 0; r <= reps && st == ZIG_OK; ++r) {
             if (r == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = ZIG_ERR_CUDA;
