@@ -16,16 +16,17 @@
 //     A lane whose last slow candidate needs draws past the batch takes them
 //     now.  The warp lists its slow candidates and decides them 32 at a time,
 //     the wedge and tail tests first in binary32 with proven margins.  A
-//     rejected candidate and every consumed draw are dropped; an accepted
-//     tail's value is written over its first uniform's slot(s).
+//     rejected candidate and every consumed draw are dropped.  An accepted
+//     tail's value, R - ln(U1)/R in binary64, is not computed here: its U1 and
+//     output address join a per-warp queue that is evaluated 32 at a time.
 //  C. The warp writes its rows one at a time, all 32 lanes on one row, lane c
 //     on slot c: a kept slot's output index is the number of kept slots below
 //     it, so one store instruction writes the row's batch as one contiguous
 //     run (about 240 bytes) at any alignment, with no close-up of the row and
 //     no carry between batches.  Each lane rebuilds its value x = sign RN(j w[i])
-//     from the draw: one binary64 fma, or for every fourth row the same
-//     correctly rounded product in 32-bit integer arithmetic (the narrow
-//     binary64 pipe and the integer pipes share the work).
+//     from the draw: one binary64 fma, or for some rows the same correctly
+//     rounded product in 32-bit integer arithmetic (the narrow binary64 pipe
+//     and the integer pipes share the work).
 // A unit's outputs are its accepted candidates in draw order: the sequence a
 // one-variate-at-a-time loop produces (Sec. 2, Listing 2, repeated).
 #pragma once
@@ -37,11 +38,31 @@ namespace zf {
 // candidate w is the slot's last word.  m53(st, d, s0): the 53-bit integer of
 // the nextDouble that starts at batch draw d, from the row's slots (and, for
 // SplitMix64, the batch's first state s0).
+// n raw steps of java.util.Random's LCG: s -> (lcg_A(n) s + lcg_C(n)) mod 2^48
+__host__ __device__ constexpr uint64_t lcg_A(int n) {
+    uint64_t A = 1;
+    for (int k = 0; k < n; ++k) A = (A * kLcgA) & kMask48;
+    return A;
+}
+__host__ __device__ constexpr uint64_t lcg_C(int n) {
+    uint64_t C = 0;
+    for (int k = 0; k < n; ++k) C = (C * kLcgA + kLcgC) & kMask48;
+    return C;
+}
+
 template <int PRNG> struct Gen;
 template <> struct Gen<ZIG_LCG48> {
     using G = GenLcg48;
     static constexpr int kU = 2, SW = 1;   // nextDouble = next(26), next(27)
     static __device__ __forceinline__ void draw(G& g, uint32_t* slot, uint32_t& w) { w = g.step(32); slot[0] = w; }
+    // batch draw D straight from the batch's first state s0 (all draws of a batch
+    // are independent of one another this way)
+    template <int D>
+    static __device__ __forceinline__ uint32_t draw_at(uint64_t s0) {
+        return (uint32_t)(((lcg_A(D + 1) * s0 + lcg_C(D + 1)) & kMask48) >> 16);
+    }
+    template <int N>
+    static __device__ __forceinline__ void skip(G& g) { g.s = (lcg_A(N) * g.s + lcg_C(N)) & kMask48; }
     static __device__ __forceinline__ uint64_t m53(const uint32_t* st, int d, uint64_t) {
         // next(26) = s1 >> 22 = w1 >> 6, next(27) = s2 >> 21 = w2 >> 5 (w = s >> 16)
         return ((uint64_t)(st[d] >> 6) << 27) + (st[d + 1] >> 5);
@@ -90,6 +111,20 @@ template <> struct Gen<ZIG_XOROSHIRO128PP> {
     static __device__ __forceinline__ uint64_t first_state(const G&) { return 0; }
 };
 
+// f(integral_constant<int, d>) for d = 0 .. N - 1, unrolled at compile time
+template <int N, int D = 0, class F>
+__device__ __forceinline__ void unroll(F& f) {
+    if constexpr (D < N) {
+        f(std::integral_constant<int, D>{});
+        unroll<N, D + 1>(f);
+    }
+}
+template <class G>
+__device__ __forceinline__ uint64_t first_state_of(const G& g) {
+    if constexpr (std::is_same<G, GenLcg48>::value || std::is_same<G, GenSplitMix64>::value) return g.s;
+    else return 0;
+}
+
 // ---- shared memory ----
 // The fast table: one 256-byte block per signed layer ix = w & 0xFF (layer
 // ix & 127, positive when bit 7 is set).  Words 0..31: 8 copies of the entry
@@ -120,6 +155,9 @@ struct Warp {
     uint32_t drop[32];         // per row: candidates rejected in the decision pass
     uint32_t lit[32];          // per row: accepted tails
     uint32_t list[64];         // slow candidates: row | draw << 5 | tail << 10
+    uint64_t tq_addr[64];      // accepted tails waiting for their value: output address | negative
+    uint64_t tq_m1[64];        // and their uniform m1 (U1 = 1 - m1 2^-53)
+    uint32_t tq_n;
 };
 template <int PRNG>
 __host__ __device__ constexpr size_t warp_bytes() {
@@ -201,10 +239,9 @@ __device__ __forceinline__ uint64_t x_of(const unsigned char* tab, uint32_t w, u
 
 // Decide listed slow candidate `it` (row | draw << 5 | tail << 10), for the
 // lanes with has set (all 32 lanes call this): a rejected candidate is marked
-// in drop[row]; an accepted tail's value goes to the words of its first
-// uniform (the next slot, or two for 4-byte slots) and its slot is marked in
-// lit[row].  The binary64 wedge test and the tail step run only when some lane
-// needs them.
+// in drop[row]; an accepted tail's m1 goes to the words of its first uniform
+// (the next slot, or two for 4-byte slots) and its slot is marked in lit[row].
+// The binary64 wedge test and the tail test run only when some lane needs them.
 template <int PRNG, class W>
 __device__ __forceinline__ void decide(W& ws, const SlowTab& slow, uint32_t it, bool has) {
     using GT = Gen<PRNG>;
@@ -224,23 +261,28 @@ __device__ __forceinline__ void decide(W& ws, const SlowTab& slow, uint32_t it, 
     }
     if (wedge && f == 0) atomicOr(&ws.drop[o], 1u << p);
     if (__any_sync(kFull, tail)) {
+        uint64_t m2 = 0;
+        int ft = 1;
         if (tail) {
-            const double x = z128_tail(m1, GT::m53(st, p + 1 + GT::kU, ws.s0[o]));
-            if (x < 0.0) {
+            m2 = GT::m53(st, p + 1 + GT::kU, ws.s0[o]);
+            ft = z128_tail_filter(m1, m2);
+        }
+        if (__any_sync(kFull, ft < 0)) {
+            if (ft < 0) ft = z128_tail_exact(m1, m2) ? 1 : 0;
+        }
+        if (tail) {
+            if (ft == 0) {
                 atomicOr(&ws.drop[o], 1u << p);
-            } else {
-                const uint64_t v = (uint64_t)__double_as_longlong(x) | (uint64_t)((~w >> 7) & 1u) << 63;
-                st[GT::SW * (p + 1)] = (uint32_t)v;   // the uniforms' words (dropped slots)
-                st[GT::SW * (p + 1) + 1] = (uint32_t)(v >> 32);
+            } else {   // m1 goes to the uniforms' words (dropped slots) for the value pass
+                st[GT::SW * (p + 1)] = (uint32_t)m1;
+                st[GT::SW * (p + 1) + 1] = (uint32_t)(m1 >> 32);
                 atomicOr(&ws.lit[o], 1u << p);
             }
         }
     }
 }
 
-// Write row r of the warp's batch: lane c takes slot c (kInt: the integer
-// product).  An accepted tail's slot gets a value rebuilt from its draw here
-// and is rewritten afterwards by its row's lane.
+// Write row r of the warp's batch: lane c takes slot c.
 template <int PRNG, bool kInt, class W>
 __device__ __forceinline__ void write_row(const W& ws, const unsigned char* tb, int r, int lane, uint32_t lane_bit,
                                           uint32_t lt_mask, uint32_t copy16) {
@@ -248,12 +290,28 @@ __device__ __forceinline__ void write_row(const W& ws, const unsigned char* tb, 
     const uint4 inf = ws.info[r];
     const uint32_t w = ws.stage[r * W::RS + GT::SW * lane + GT::SW - 1];
     const uint64_t v = x_of<kInt>(tb, w, copy16);
-    const uint32_t e = __popc(~inf.z & lt_mask);   // kept slots below this one
+    const uint32_t e = __popc(~inf.z & lt_mask);
     const uint64_t addr = ((uint64_t)inf.x | (uint64_t)inf.y << 32) + 8ull * e;
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %2, 0;\n\t@p st.global.cs.b64 [%0], %1;\n\t}" ::"l"(addr), "l"(v),
-        "r"(inf.z & lane_bit)
-        : "memory");
+        "r"(inf.z & lane_bit));
+}
+
+// The values of queued accepted tails, 32 at a time (all 32 lanes call this).
+template <class W>
+__device__ __forceinline__ void drain_tails(W& ws, int lane) {
+    const uint32_t n = ws.tq_n;
+    for (uint32_t b = 0; b < n; b += 32) {
+        if (b + lane < n) {
+            const uint64_t ad = ws.tq_addr[b + lane];
+            const double x = z128_tail_value(ws.tq_m1[b + lane]);
+            __stcs((unsigned long long*)(ad & ~7ull),
+                   (unsigned long long)__double_as_longlong(x) | (unsigned long long)(ad & 1u) << 63);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) ws.tq_n = 0;
+    __syncwarp();
 }
 
 template <int PRNG, int NDF>
@@ -279,6 +337,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
     const uint32_t copy16 = (uint32_t)(lane & 7) << 4;    // this lane's copy of a fast entry
     const uint32_t kcopy = 0x80u + ((uint32_t)lane << 2);  // this lane's copy of K
 
+    if (lane == 0) ws.tq_n = 0;
+    __syncwarp();
     if (a.out == nullptr) {   // only legal when every length is zero
         if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&d_err, kErrNullOutput);
         return;
@@ -312,13 +372,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
             // ---- A: B draws per lane, lockstep; nf marks the slow candidates ----
             if constexpr (PRNG == ZIG_SPLITMIX64) ws.s0[lane] = GT::first_state(g);
             uint32_t nf = 0;
-#pragma unroll
-            for (int d = 0; d < B; ++d) {
+            const uint64_t sb = first_state_of(g);
+            auto step = [&](auto dc) {
+                constexpr int d = decltype(dc)::value;
                 uint32_t w;
-                GT::draw(g, row + SW * d, w);
+                if constexpr (PRNG == ZIG_LCG48) {
+                    w = GT::template draw_at<d>(sb);
+                    row[d] = w;
+                } else {
+                    GT::draw(g, row + SW * d, w);
+                }
                 const uint32_t K = *(const uint32_t*)(tb + __byte_perm(w, kcopy, 0x5504));
                 nf |= (w >= K ? 1u : 0u) << d;
-            }
+            };
+            unroll<B>(step);
+            if constexpr (PRNG == ZIG_LCG48) GT::template skip<B>(g);
             // ---- B: the slow candidates, in draw order; list, then decide ----
             // Each lane walks its nf bits once: a bit not consumed by an earlier
             // slow candidate is one (R; tails also in T), and consumes the next kU
@@ -326,17 +394,41 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
             uint32_t R = 0, T = 0, du = 0;
             int ne = 0;
             if (rem > 0) {
-                uint32_t m = nf;
-                while (m) {
-                    const int p = __ffs(m) - 1;
-                    const uint32_t w = row[SW * p + SW - 1];
-                    const bool tail = (w & 0x7Fu) == 0x7Fu;
-                    const int need = tail ? 2 * kU : kU;
-                    const int last = p + need;   // the last draw it consumes (< 32)
-                    R |= 1u << p;
-                    T |= tail ? 1u << p : 0u;
-                    du |= ((1u << need) - 1u) << (p + 1);
-                    m &= last >= 31 ? 0u : ~0u << (last + 1);
+                if constexpr (kU == 1) {
+                    // As if every slow candidate were a wedge (one uniform): in each run
+                    // of consecutive nf bits the candidates are the bits at even
+                    // distance from the run's start.  A tail consumes one more draw:
+                    // the candidates after it are found again from its second uniform on.
+                    auto cands = [](uint32_t f) {
+                        const uint32_t S = f & ~(f << 1);                      // run starts
+                        const uint32_t re = f & ~(f + (S & 0x55555555u));      // runs starting at even bits
+                        return (re & 0x55555555u) | (f & ~re & 0xAAAAAAAAu);
+                    };
+                    R = cands(nf);
+                    for (uint32_t m = R; m; m &= m - 1u) {
+                        const int p = __ffs(m) - 1;
+                        const uint32_t w = row[SW * p + SW - 1];
+                        if ((w & 0x7Fu) == 0x7Fu) {   // a tail: draws p + 1 and p + 2 are its uniforms
+                            T |= 1u << p;
+                            const uint32_t Rn = cands(p + 3 >= 32 ? 0u : nf & (~0u << (p + 3)));
+                            R = (R & ((2u << p) - 1u)) | Rn;
+                            m = Rn | (1u << p);   // the loop clears bit p, then continues with Rn
+                        }
+                    }
+                    du = (R << 1) | (T << 2);
+                } else {
+                    uint32_t m = nf;
+                    while (m) {
+                        const int p = __ffs(m) - 1;
+                        const uint32_t w = row[SW * p + SW - 1];
+                        const bool tail = (w & 0x7Fu) == 0x7Fu;
+                        const int need = tail ? 2 * kU : kU;
+                        const int last = p + need;   // the last draw it consumes (< 32)
+                        R |= 1u << p;
+                        T |= tail ? 1u << p : 0u;
+                        du |= ((1u << need) - 1u) << (p + 1);
+                        m &= last >= 31 ? 0u : ~0u << (last + 1);
+                    }
                 }
                 const int lastU = du ? 31 - __clz(du) : -1;
                 while (B + ne <= lastU) {   // past the batch (rare)
@@ -390,8 +482,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
             } else if (check_chunk) {
                 draws += (uint64_t)n;
             }
-            ws.info[lane] = make_uint4((uint32_t)(uintptr_t)dst, (uint32_t)((uintptr_t)dst >> 32), D, L);
+            ws.info[lane] = make_uint4((uint32_t)(uintptr_t)dst, (uint32_t)((uintptr_t)dst >> 32), D, 0u);
             __syncwarp();
+            // products q = 0..3 of every two steps: the binary64 fma for q < NDF
 #pragma unroll 2
             for (int r = 0; r < 32; r += 4) {
                 write_row<PRNG, (0 >= NDF)>(ws, tb, r + 0, lane, lane_bit, lt_mask, copy16);
@@ -399,15 +492,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
                 write_row<PRNG, (2 >= NDF)>(ws, tb, r + 2, lane, lane_bit, lt_mask, copy16);
                 write_row<PRNG, (3 >= NDF)>(ws, tb, r + 3, lane, lane_bit, lt_mask, copy16);
             }
-            // accepted tails: the row's lane rewrites each kept one's output
-            const uint32_t Lk = L & ~D;
-            if (__any_sync(kFull, Lk != 0)) {
-                __syncwarp();
-                for (uint32_t m = Lk; m; m &= m - 1u) {
-                    const int p = __ffs(m) - 1;
-                    const uint64_t v = (uint64_t)row[SW * (p + 1)] | (uint64_t)row[SW * (p + 1) + 1] << 32;
-                    __stcs((unsigned long long*)dst + __popc(~D & ((1u << p) - 1u)), (unsigned long long)v);
+            // accepted tails join the queue (one per lane per round), evaluated 32 at a time
+            uint32_t Lk = L & ~D;
+            for (;;) {
+                const uint32_t bal = __ballot_sync(kFull, Lk != 0);
+                if (bal == 0) break;
+                if (Lk) {
+                    const int p = __ffs(Lk) - 1;
+                    Lk &= Lk - 1u;
+                    const uint32_t idx = ws.tq_n + __popc(bal & lt_mask);
+                    const uint32_t w = row[SW * p + SW - 1];
+                    ws.tq_addr[idx] = (uint64_t)(uintptr_t)(dst + __popc(~D & ((1u << p) - 1u))) | ((~w >> 7) & 1u);
+                    ws.tq_m1[idx] = (uint64_t)row[SW * (p + 1)] | (uint64_t)row[SW * (p + 1) + 1] << 32;
                 }
+                __syncwarp();
+                if (lane == 0) ws.tq_n += __popc(bal);
+                __syncwarp();
+                if (ws.tq_n >= 32) drain_tails(ws, lane);
             }
             dst += k_out;
             rem -= (uint64_t)k_out;
@@ -415,6 +516,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
         }
         if (check_chunk && draws > kChunkDraws) atomicOr(&d_err, kErrChunkOverflow);
     }
+    drain_tails(ws, lane);
 }
 
 }  // namespace zf

@@ -503,8 +503,10 @@ __device__ __forceinline__ double div_by_R(double z) {
 // below 1e-5 relative here); otherwise ln U2 < -s^2/2 decides in binary64.  The
 // two tests agree except where the oracle's own rounding could flip its
 // decision (a margin near 1e-16).
-__device__ __forceinline__ bool z128_tail_accept(uint64_t m1, uint64_t m2) {
-    if (m2 == 0) return true;                         // U2 = 0: y = 0 < exp(-x^2/2)
+// z128_tail_filter: 1 accept, 0 reject, -1 inside the margin;
+// z128_tail_exact: the binary64 decision.
+__device__ __forceinline__ int z128_tail_filter(uint64_t m1, uint64_t m2) {
+    if (m2 == 0) return 1;                            // U2 = 0: y = 0 < exp(-x^2/2)
     const uint64_t n1 = (1ull << 53) - m1;            // U1 = n1 2^-53 in (0, 1]
     constexpr float kLn2 = 0.693147180559945309f;
     constexpr float kLn2OverR = (float)(0.693147180559945309 / zigtab::ZIG128_R);
@@ -512,18 +514,31 @@ __device__ __forceinline__ bool z128_tail_accept(uint64_t m1, uint64_t m2) {
     const float h32 = 0.5f * s32 * s32;
     const float l32 = __log2f(m53_to_float(m2)) * kLn2;
     const float marg = 0x1p-14f * (1.0f + h32 - l32);
-    if (l32 < -h32 - marg) return true;
-    if (l32 > -h32 + marg) return false;
+    if (l32 < -h32 - marg) return 1;
+    if (l32 > -h32 + marg) return 0;
+    return -1;
+}
+__device__ __forceinline__ bool z128_tail_exact(uint64_t m1, uint64_t m2) {
+    const uint64_t n1 = (1ull << 53) - m1;
     const double s = -div_by_R(zlog(m53_to_double(n1)));
     return zlog(m53_to_double(m2)) < __dmul_rn(__dmul_rn(-0.5, s), s);
+}
+__device__ __forceinline__ bool z128_tail_accept(uint64_t m1, uint64_t m2) {
+    const int f = z128_tail_filter(m1, m2);
+    return f >= 0 ? f == 1 : z128_tail_exact(m1, m2);
+}
+
+// The tail step's value for an accepted U1 = 1 - m1 2^-53: x = R - ln(U1)/R.
+__device__ __forceinline__ double z128_tail_value(uint64_t m1) {
+    const double U1 = __dsub_rn(1.0, m53_to_double(m1));
+    return __dsub_rn(zigtab::ZIG128_R, div_by_R(zlog(U1)));
 }
 
 // The tail step, inline and free of calls: the accepted x = R - ln(U1)/R, or -1
 // if rejected.
 __device__ __forceinline__ double z128_tail(uint64_t m1, uint64_t m2) {
     if (!z128_tail_accept(m1, m2)) return -1.0;
-    const double U1 = __dsub_rn(1.0, m53_to_double(m1));
-    return __dsub_rn(zigtab::ZIG128_R, div_by_R(zlog(U1)));
+    return z128_tail_value(m1);
 }
 
 // Staging word per slot: binary64 bits, or binary32 bits (binary32 and bfloat16
@@ -1561,7 +1576,7 @@ static bool g_cfg_set[kMaxDevices][4][3][2];
 static uint32_t default_batch(int dt) { (void)dt; return 32u; }
 // binary64: values of every 4 whose exact product uses the binary64 fma (the
 // rest use the integer product), by generator
-static uint32_t default_fma(int prng) { return prng == ZIG_L64X128MIX ? 3u : 2u; }
+static uint32_t default_fma(int prng) { (void)prng; return 3u; }
 // binary64 rows go out as warp-wide runs, one row per store (the kernel's only
 // form); the narrower types in warp-cooperative element stores
 static LaunchCfg default_cfg(int dt) {
