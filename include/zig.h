@@ -21,11 +21,16 @@
  *    launch is queued.
  *  - Argument errors are detected on the host and returned synchronously, with
  *    nothing enqueued.  Launch failures return ZIG_ERR_CUDA.  Conditions only the
- *    GPU can see (a chunk overrunning its 2^32-draw budget, a bounded wait that
- *    gave up) are latched in a per-device error word: read it with
+ *    GPU can see (a NULL output for lengths that sum above zero, lengths that sum
+ *    to 2^40 or more, a chunk overrunning its 2^32-draw budget) are latched in an
+ *    error word on the device: the caller's own word for zig_generate_checked
+ *    (scoped to that call), else the device's shared word, read and cleared with
  *    zig_device_status().
  *  - There is no CPU fallback: every step runs in this library's kernels.
- *  - All entry points are thread-safe with respect to distinct streams.
+ *  - Entry points may be called from several host threads and on distinct
+ *    streams at once, with two exceptions stated where they apply: calls of
+ *    zig_generate_noalloc share one fixed scratch array, and calls that latch
+ *    into the device's shared error word share that word.
  */
 #ifndef ZIG_GB300_H
 #define ZIG_GB300_H
@@ -43,7 +48,7 @@ typedef enum {
     ZIG_ERR_NOT_INITIALIZED = 2, /* zig_tables_init was not called on this device */
     ZIG_ERR_CUDA = 3,            /* a CUDA runtime call or launch failed */
     ZIG_ERR_BUDGET = 4,          /* a request exceeds the admission budget */
-    ZIG_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
+    ZIG_ERR_TIMEOUT = 5,         /* a host-side wait gave up (zig_server_wait, zig_server_drain) */
     ZIG_ERR_CHUNK_OVERFLOW = 6,  /* a chunk consumed more than 2^32 raw draws */
     ZIG_ERR_UNSUPPORTED = 7,     /* the device is not sm_103 or the combination is not built */
     ZIG_ERR_TOO_LARGE = 8        /* more streams than zig_generate_noalloc's fixed scratch holds */
@@ -97,6 +102,43 @@ zig_status zig_tables_init(int device);
 zig_status zig_tables_get_zig128(uint32_t *k_host, double *w_host, double *y_host,
                                  float *w32_host, double *R_host);
 
+/* The 128-level ziggurat's tables (Sec. 1; the GSL form): layer i < 127 is the
+ * strip [0, x_{i+1}) x [f(x_{i+1}), f(x_i)), layer 127 the base of width R.
+ * w[i] = RN(x_{i+1} / 2^24) (base: RN(v / f(R) / 2^24)), k[i] = floor(2^24 x_i / x_{i+1})
+ * (base: floor(2^24 R f(R) / v)), y[i] = RN(f(x_i)), w32 the binary32 rounding of
+ * x_{i+1} / 2^24; v is the common layer area. */
+typedef struct {
+    double R, V;
+    double w[128], y[128];
+    uint32_t k[128];
+    float w32[128];
+} zig_tables128;
+
+/* The 256-slot modified ziggurat's tables (Sec. 2, the Java 17 bullet): slot
+ * j < n_r is a rectangle of width x0-scaled xs[j] (x = xs[j] (U >> 11)); an alias
+ * bin b selects region b when the draw's upper 56 bits are below thr[b], else
+ * alias[b]; region 0 is the tail beyond x0, region r in 1..n_r the overhang box
+ * [ox, ox + odx] x [oy, oy + ody] with its shape kind (+1 convex, -1 concave)
+ * and quick-accept distance qa (all indexed by r; index 0 unused). */
+typedef struct {
+    uint64_t n_r;
+    double x0;
+    double xs[256];
+    double ox[256], odx[256], oy[256], ody[256];
+    uint64_t qa[256], thr[256];
+    int32_t kind[256], alias[256];
+} zig_tables256;
+
+/*
+ * zig_tables_get -- copy the tables of transform `alg` to host memory:
+ * a zig_tables128 for ZIG_ZIG128, a zig_tables256 for ZIG_ZIG256, nothing for
+ * ZIG_POLAR (it has no tables).  *bytes: in, the capacity of host_dst; out, the
+ * size of the structure (0 for ZIG_POLAR).  host_dst = NULL only reports the size.
+ * ZIG_ERR_INVALID_ARG for a bad enum, bytes = NULL or too small a capacity.
+ * Needs no device.
+ */
+zig_status zig_tables_get(zig_alg alg, void *host_dst, size_t *bytes);
+
 /*
  * zig_generate -- bulk N(0,1) variates, stream-major and packed.
  *
@@ -121,15 +163,18 @@ zig_status zig_tables_get_zig128(uint32_t *k_host, double *w_host, double *y_hos
  * workspace_bytes    at least zig_generate_workspace_bytes(n_streams) bytes,
  *                    16-byte aligned, owned by the caller and not used by any
  *                    other call in flight.  NULL/0 with lengths_dev != NULL makes
- *                    the library use its own per-device workspace (allocated, or
- *                    grown, with cudaMalloc on first use).  Ignored when
- *                    lengths_dev is NULL.
+ *                    the call allocate its scratch on `stream` (cudaMallocAsync)
+ *                    and free it there after its launch (cudaFreeAsync), so calls
+ *                    on different streams never share it, and a call captured
+ *                    into a graph gives the graph its own allocation.  Ignored
+ *                    when lengths_dev is NULL.
  * stream             cudaStream_t.
  *
- * The sum of all lengths must be < 2^40.  Errors: ZIG_ERR_INVALID_ARG for bad
- * enums, NULL pointers, chunk_log2 out of range, misaligned buffers or too small
- * a workspace; ZIG_ERR_NOT_INITIALIZED if zig_tables_init(device) was not
- * called for the current device.
+ * The sum of all lengths must be < 2^40: a variable-length batch that reaches
+ * it writes nothing and latches ZIG_ERR_INVALID_ARG in the error word.  Errors:
+ * ZIG_ERR_INVALID_ARG for bad enums, NULL pointers, chunk_log2 out of range,
+ * misaligned buffers or too small a workspace; ZIG_ERR_NOT_INITIALIZED if
+ * zig_tables_init(device) was not called for the current device.
  */
 zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t *seeds_dev,
                         const uint64_t *lengths_dev, uint64_t uniform_len, uint64_t n_streams,
@@ -140,8 +185,30 @@ zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t *seeds_dev,
 size_t zig_generate_workspace_bytes(uint64_t n_streams);
 
 /*
+ * zig_generate_checked -- zig_generate with its device-side errors latched in
+ * the caller's own word status_dev (a uint32_t in device memory, 4-byte
+ * aligned) instead of the device's shared word, so that concurrent callers
+ * cannot read or clear one another's errors.  The call ORs error bits into the
+ * word and never clears it: zero it before the call, read it after the stream
+ * has passed the call, and turn it into a status with zig_status_decode.
+ * Computes exactly what zig_generate computes; errors as zig_generate, and
+ * ZIG_ERR_INVALID_ARG for a NULL or misaligned status_dev.
+ */
+zig_status zig_generate_checked(zig_prng prng, zig_alg alg, const uint64_t *seeds_dev,
+                                const uint64_t *lengths_dev, uint64_t uniform_len, uint64_t n_streams,
+                                uint32_t chunk_log2, zig_dtype dtype, void *out_dev,
+                                void *workspace_dev, size_t workspace_bytes, uint32_t *status_dev,
+                                void *stream);
+
+/* The status an error word holds (the word of zig_generate_checked, or the value
+ * zig_device_status reads): ZIG_OK, ZIG_ERR_INVALID_ARG (a NULL output for
+ * lengths summing above zero, or lengths summing to 2^40 or more) or
+ * ZIG_ERR_CHUNK_OVERFLOW, in that order of precedence.  No CUDA call. */
+zig_status zig_status_decode(uint32_t word);
+
+/*
  * zig_generate_noalloc -- zig_generate for a variable-length batch, with no
- * allocation of any kind.  The paper has no counterpart: this is an
+ * allocation of any kind (device or host).  The paper has no counterpart: this is an
  * integration entry point for callers that cannot allocate device memory at
  * call time, e.g. a service that has carved all of HBM into its own pools
  * before serving, a latency-bound loop that cannot absorb cudaMalloc's implicit
@@ -177,16 +244,26 @@ zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uint64_t *seed
  * Launch configuration of the 128-level generation kernel (ZIG_ZIG128).  The
  * paper's single-threaded Java generator has no counterpart; these knobs only
  * change how the same work is laid out on the GPU, never the values:
- *  block        threads per block, a multiple of 32 in [64, 768] (default 768).
- *  batch        candidates each lane draws per batch before the warp decides its
- *               deferred wedge tests and writes: 20 (default) or 10 for
- *               ZIG_F64; 32 (default) or 16 for ZIG_F32 and ZIG_BF16.
- *  store_bytes  0 (default for ZIG_F32, ZIG_BF16): the warp writes each row
- *               cooperatively, one element per lane and store; 32 (default for
- *               ZIG_F64): each lane writes its own row in whole 32-byte sectors
- *               (256-bit stores), carrying a partial sector over to its next
- *               batch, with element stores only at a unit's unaligned start and
- *               at its end.
+ *  block        threads per block, a multiple of 32: in [64, 768] for ZIG_F32 and
+ *               ZIG_BF16 (default 768); in [64, 640] for ZIG_F64 (default 640),
+ *               lowered at launch to what one SM's shared memory holds for the
+ *               generator.
+ *  batch        slots of a lane's row per batch: 32 for ZIG_F64 (the only
+ *               value; 32 - 2 kU of them are draws, kU the raw steps of one
+ *               nextDouble); for ZIG_F32 and ZIG_BF16 the candidates each lane
+ *               draws before the warp decides its deferred wedge tests, 32
+ *               (default) or 16.
+ *  store_bytes  ZIG_F64: 0 (the warp writes each row with one store per lane,
+ *               the row's batch as one contiguous run).  ZIG_F32, ZIG_BF16: 0
+ *               (default; the warp writes each row cooperatively, one element
+ *               per lane and store) or 32 (each lane writes its own row in
+ *               whole 32-byte sectors, carrying a partial sector over to its
+ *               next batch).
+ *  fma_of_4     ZIG_F64: of every 4 rows, how many rebuild their values with one
+ *               binary64 fused multiply-add per value; the others use the same
+ *               correctly rounded product in 32-bit integer arithmetic (GB300's
+ *               binary64 pipe is narrow).  2, 3 or 4; 0 = the library's default
+ *               for the generator.  Must be 0 for ZIG_F32 and ZIG_BF16.
  * One configuration is kept per device, PRNG, dtype and input form
  * (variable_lengths = 1 for calls with a lengths array, 0 for uniform ones);
  * zig_generate and zig_generate_noalloc read it at each call.
@@ -205,9 +282,10 @@ zig_status zig_launch_config_get(int device, zig_prng prng, zig_dtype dtype, int
  * restores the default.  No CUDA call. */
 zig_status zig_launch_config_set(int device, zig_prng prng, zig_dtype dtype, int variable_lengths,
                                  const zig_launch_config *cfg);
-/* The configurations zig_autotune tries for dtype (blocks 256/384/512/768 x both
- * batch widths x both store widths): writes up to max_cands of them to cands
- * (may be NULL) and returns how many there are. */
+/* The configurations zig_autotune tries for dtype (ZIG_F64: blocks
+ * 256/384/512/640 x fma_of_4 2/3/4; otherwise blocks 256/384/512/768 x both batch
+ * widths x both store widths): writes up to max_cands of them to cands (may be
+ * NULL) and returns how many there are. */
 uint32_t zig_autotune_candidates(zig_dtype dtype, zig_launch_config *cands, uint32_t max_cands);
 /*
  * zig_autotune -- time every candidate configuration on the caller's own
@@ -262,6 +340,8 @@ typedef struct {
  * reqs_host: host array (copied before the call returns).  desc_dev: device
  * scratch of at least zig_mutate_batch_desc_bytes(n_req) bytes, 16-byte aligned,
  * not used by another call in flight.  All requests use one generator `prng`.
+ * The call copies the descriptors from host memory it owns only for the call, so
+ * it is refused (ZIG_ERR_INVALID_ARG) while `stream` is being captured into a graph.
  */
 size_t zig_mutate_batch_desc_bytes(uint32_t n_req);
 zig_status zig_mutate_batch(const zig_mutation *reqs_host, uint32_t n_req, zig_prng prng,
@@ -328,10 +408,11 @@ zig_status zig_prng_fill(zig_prng prng, const uint64_t *seeds_dev, uint64_t n_st
                          uint64_t n, uint64_t skip, int kind, uint64_t *out_dev, void *stream);
 
 /*
- * zig_device_status -- read (and, if clear != 0, reset) the device's latched
- * error word.  Synchronizes the device.  Returns ZIG_OK, or the latched
- * condition (ZIG_ERR_INVALID_ARG for a NULL output with nonzero lengths, then
- * ZIG_ERR_TIMEOUT, then ZIG_ERR_CHUNK_OVERFLOW), or ZIG_ERR_CUDA.
+ * zig_device_status -- read (and, if clear != 0, reset) the device's shared
+ * error word, which every call but zig_generate_checked latches into.
+ * Synchronizes the device.  Returns zig_status_decode of the word, or
+ * ZIG_ERR_CUDA.  Concurrent callers share this word (one caller's clear erases
+ * another's flag): callers that need their own scope use zig_generate_checked.
  */
 zig_status zig_device_status(int device, int clear);
 

@@ -81,7 +81,7 @@ def load():
         dp = C.POINTER(C.c_double)
         lib.orc_generate.argtypes = [C.c_int, C.c_int, u64p, u64p, C.c_uint64, C.c_uint64,
                                      C.c_uint32, C.c_void_p, C.c_void_p, dp, dp,
-                                     C.POINTER(Stats)]
+                                     C.POINTER(C.c_uint8), C.POINTER(Stats)]
         lib.orc_generate.restype = C.c_int
         lib.orc_prng_fill.argtypes = [C.c_int, u64p, C.c_uint64, C.c_uint64, C.c_uint64,
                                       C.c_int, u64p]
@@ -206,8 +206,10 @@ def _u64(a):
 
 
 def generate(prng: str, alg: str, seeds, lengths=None, uniform_len: int = 0,
-             chunk_log2: int = 0, with_margins: bool = False):
-    """Bulk FP64 variates, stream-major packed.  Returns (out, margins|None, stats)."""
+             chunk_log2: int = 0, with_margins: bool = False, with_via_log: bool = False):
+    """Bulk FP64 variates, stream-major packed.  Returns (out, margins|None, stats), or with
+    with_via_log (out, margins|None, stats, via_log): per output 1 when its value was computed
+    through log (a tail value; every polar value), else 0."""
     lib = load()
     seeds, sp = _u64(seeds)
     n = len(seeds)
@@ -219,15 +221,19 @@ def generate(prng: str, alg: str, seeds, lengths=None, uniform_len: int = 0,
         total = n * int(uniform_len)
     out = np.empty(total, dtype=np.float64)
     margins = np.empty(total, dtype=np.float64) if with_margins else None
+    via_log = np.empty(total, dtype=np.uint8) if with_via_log else None
     st = Stats()
     rc = lib.orc_generate(
         PRNGS[prng], ALGS[alg], sp, lp, int(uniform_len), n, int(chunk_log2),
         _tab128() if alg == "zig128" else None, _tab256() if alg == "zig256" else None,
         out.ctypes.data_as(C.POINTER(C.c_double)),
         margins.ctypes.data_as(C.POINTER(C.c_double)) if with_margins else None,
+        via_log.ctypes.data_as(C.POINTER(C.c_uint8)) if with_via_log else None,
         C.byref(st))
     if rc != 0:
         raise ValueError("orc_generate rejected its arguments")
+    if with_via_log:
+        return out, margins, st.as_dict(), via_log
     return out, margins, st.as_dict()
 
 

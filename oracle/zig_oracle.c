@@ -419,8 +419,10 @@ static void note_margin(orc_stats *st, double y, double e, double *vm) {
 }
 
 /* Original ziggurat, GSL form.  *vm (may be NULL) receives the smallest margin
- * of the exp tests taken while producing this variate. */
-double orc_zig128_next(orc_prng *g, const orc_zig128_tab *t, orc_stats *st, double *vm) {
+ * of the exp tests taken while producing this variate; *vlog (may be NULL) is
+ * set to 1 when the value itself was computed through log (the tail), else 0. */
+double orc_zig128_next(orc_prng *g, const orc_zig128_tab *t, orc_stats *st, double *vm, int *vlog) {
+    if (vlog) *vlog = 0;
     for (;;) {
         uint32_t u = orc_next_u32(g, st);
         uint32_t i = u & 0xFF;
@@ -450,6 +452,7 @@ double orc_zig128_next(orc_prng *g, const orc_zig128_tab *t, orc_stats *st, doub
         note_margin(st, y, e, vm);
         if (y < e) {
             if (i < 127) st->wedge_acc++; else st->tail_acc++;
+            if (vlog) *vlog = i == 127;
             return sign * x;
         }
     }
@@ -476,8 +479,9 @@ double orc_polar_next(orc_prng *g, orc_stats *st) {
 }
 
 /* Modified ziggurat, 256 slots. */
-double orc_zig256_next(orc_prng *g, const orc_zig256_tab *t, orc_stats *st, double *vm) {
+double orc_zig256_next(orc_prng *g, const orc_zig256_tab *t, orc_stats *st, double *vm, int *vlog) {
     const uint64_t two53 = UINT64_C(1) << 53;
+    if (vlog) *vlog = 0;
     uint64_t U = orc_next_u64(g, st);
     unsigned j = (unsigned)(U & 0xFF);
     double sign = ((U >> 8) & 1) ? -1.0 : 1.0;
@@ -501,6 +505,7 @@ double orc_zig256_next(orc_prng *g, const orc_zig256_tab *t, orc_stats *st, doub
             if (x > 0) note_margin(st, y + y, x * x, vm);
             if (y + y > x * x) {
                 st->tail++;
+                if (vlog) *vlog = 1;
                 return sign * (t->x0 + x);
             }
         }
@@ -548,12 +553,14 @@ double orc_zig256_next(orc_prng *g, const orc_zig256_tab *t, orc_stats *st, doub
  * lengths == NULL: every stream has uniform_len outputs.
  * margins (may be NULL): per output, the smallest exp-test margin used for it
  * (+inf when no exp test was taken).
+ * via_log (may be NULL): per output, 1 when the value was computed through log
+ * (a tail value of either ziggurat; every polar value), else 0.
  * Returns 0, or -1 on bad arguments.
  */
 int orc_generate(int prng, int alg, const uint64_t *seeds, const uint64_t *lengths,
                  uint64_t uniform_len, uint64_t n_streams, uint32_t chunk_log2,
                  const orc_zig128_tab *t128, const orc_zig256_tab *t256, double *out,
-                 double *margins, orc_stats *st) {
+                 double *margins, unsigned char *via_log, orc_stats *st) {
     if (prng != ORC_LCG48 && prng != ORC_SPLITMIX64 && prng != ORC_L64X128MIX &&
         prng != ORC_XOROSHIRO128PP)
         return -1;
@@ -582,12 +589,14 @@ int orc_generate(int prng, int alg, const uint64_t *seeds, const uint64_t *lengt
                 g = chunk_start;
             }
             double vm = INFINITY;
+            int vlog = 1;
             double z;
-            if (alg == ORC_ZIG128) z = orc_zig128_next(&g, t128, st, &vm);
+            if (alg == ORC_ZIG128) z = orc_zig128_next(&g, t128, st, &vm, &vlog);
             else if (alg == ORC_POLAR) z = orc_polar_next(&g, st);
-            else z = orc_zig256_next(&g, t256, st, &vm);
+            else z = orc_zig256_next(&g, t256, st, &vm, &vlog);
             out[off + t] = z;
             if (margins) margins[off + t] = vm;
+            if (via_log) via_log[off + t] = (unsigned char)vlog;
         }
         off += L;
     }
@@ -644,7 +653,7 @@ int64_t orc_zig128_scripted(const uint64_t *words, uint64_t n_words, const orc_z
     memset(st, 0, sizeof(*st));
     st->min_margin = INFINITY;
     for (uint64_t k = 0; k < n; k++) {
-        out[k] = orc_zig128_next(&g, t, st, NULL);
+        out[k] = orc_zig128_next(&g, t, st, NULL, NULL);
         if (g.script_overrun) return -1;
     }
     return (int64_t)g.script_pos;
@@ -657,7 +666,7 @@ int64_t orc_zig256_scripted(const uint64_t *words, uint64_t n_words, const orc_z
     memset(st, 0, sizeof(*st));
     st->min_margin = INFINITY;
     for (uint64_t k = 0; k < n; k++) {
-        out[k] = orc_zig256_next(&g, t, st, NULL);
+        out[k] = orc_zig256_next(&g, t, st, NULL, NULL);
         if (g.script_overrun) return -1;
     }
     return (int64_t)g.script_pos;

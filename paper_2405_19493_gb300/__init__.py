@@ -15,11 +15,13 @@ from ._binding import (  # noqa: F401
     zig_generate_workspace_bytes,
     zig_mutate, zig_mutate_batch, zig_prng_fill, zig_status_string, zig_tables_get_zig128, zig_tables_init,
     zig_version, zig_launch_config_get, zig_launch_config_set, zig_autotune_candidates, zig_autotune,
+    zig_generate_checked, zig_status_decode, zig_tables_get,
 )
 
 __all__ = [
     "ZigError", "generate", "load", "zig_device_status", "zig_generate", "zig_generate_noalloc",
     "zig_generate_workspace_bytes", "zig_mutate", "zig_mutate_batch", "zig_prng_fill", "zig_status_string",
     "zig_tables_get_zig128", "zig_tables_init", "zig_version", "zig_launch_config_get",
-    "zig_launch_config_set", "zig_autotune_candidates", "zig_autotune",
+    "zig_launch_config_set", "zig_autotune_candidates", "zig_autotune", "zig_generate_checked",
+    "zig_status_decode", "zig_tables_get",
 ]

@@ -36,7 +36,7 @@ EXPORTS = (
     "zig_server_create", "zig_server_submit", "zig_server_wait", "zig_server_query",
     "zig_server_drain", "zig_server_stats", "zig_server_destroy", "zig_server_submit_generate",
     "zig_launch_config_get", "zig_launch_config_set", "zig_autotune_candidates", "zig_autotune",
-    "zig_selfcheck",
+    "zig_selfcheck", "zig_generate_checked", "zig_status_decode", "zig_tables_get",
 )
 
 
@@ -137,6 +137,12 @@ def load(build_if_missing: bool = True):
         lib.zig_selfcheck.argtypes = [C.POINTER(u64)]
         lib.zig_selfcheck.restype = i32
         lib.zig_device_status.argtypes = [i32, i32]
+        lib.zig_generate_checked.argtypes = [i32, i32, vp, vp, u64, u64, C.c_uint32, i32, vp, vp,
+                                             C.c_size_t, vp, vp]
+        lib.zig_status_decode.argtypes = [C.c_uint32]
+        lib.zig_tables_get.argtypes = [i32, vp, C.POINTER(C.c_size_t)]
+        for name in ("zig_generate_checked", "zig_status_decode", "zig_tables_get"):
+            getattr(lib, name).restype = i32
         lib.zig_status_string.argtypes = [i32]
         lib.zig_status_string.restype = C.c_char_p
         for name in ("zig_tables_init", "zig_tables_get_zig128", "zig_generate", "zig_mutate",
@@ -177,6 +183,38 @@ def zig_tables_get_zig128():
     return {"k": k, "w": w, "y": y, "w32": w32, "R": float(R[0])}
 
 
+class Tables128(C.Structure):
+    """zig_tables128."""
+    _fields_ = [("R", C.c_double), ("V", C.c_double), ("w", C.c_double * 128), ("y", C.c_double * 128),
+                ("k", C.c_uint32 * 128), ("w32", C.c_float * 128)]
+
+
+class Tables256(C.Structure):
+    """zig_tables256."""
+    _fields_ = [("n_r", C.c_uint64), ("x0", C.c_double), ("xs", C.c_double * 256),
+                ("ox", C.c_double * 256), ("odx", C.c_double * 256), ("oy", C.c_double * 256),
+                ("ody", C.c_double * 256), ("qa", C.c_uint64 * 256), ("thr", C.c_uint64 * 256),
+                ("kind", C.c_int32 * 256), ("alias", C.c_int32 * 256)]
+
+
+def zig_tables_get(alg: str) -> dict:
+    """The tables of ``alg`` as a dict of Python scalars and lists ({} for polar)."""
+    lib = load()
+    n = C.c_size_t(0)
+    _check(lib.zig_tables_get(ALG[alg], None, C.byref(n)), "zig_tables_get")
+    if n.value == 0:
+        return {}
+    t = Tables128() if alg == "zig128" else Tables256()
+    assert C.sizeof(t) == n.value, "zig_tables_get: structure size differs from the header's"
+    _check(lib.zig_tables_get(ALG[alg], C.byref(t), C.byref(n)), "zig_tables_get")
+    return {name: (list(getattr(t, name)) if hasattr(getattr(t, name), "__len__") else getattr(t, name))
+            for name, _ in t._fields_}
+
+
+def zig_status_decode(word: int) -> int:
+    return int(load().zig_status_decode(int(word) & 0xFFFFFFFF))
+
+
 def zig_generate_workspace_bytes(n_streams: int) -> int:
     return int(load().zig_generate_workspace_bytes(n_streams))
 
@@ -193,6 +231,21 @@ def zig_generate(prng: str, alg: str, seeds, out, lengths=None, uniform_len: int
                              int(uniform_len), n, int(chunk_log2), DTYPE[dtype], out.data_ptr(),
                              ws_ptr or None, ws_bytes, _stream_ptr(stream))
     _check(st, "zig_generate")
+
+
+def zig_generate_checked(prng: str, alg: str, seeds, out, status, lengths=None, uniform_len: int = 0,
+                         chunk_log2: int = 0, dtype: str = "f64", workspace=None, stream=None) -> None:
+    """zig_generate whose device-side errors go to ``status`` (a CUDA int32 tensor of one element
+    the caller zeroes; decode it with zig_status_decode after the stream has run the call)."""
+    n = int(seeds.numel())
+    ws_ptr, ws_bytes = (0, 0)
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    st = load().zig_generate_checked(PRNG[prng], ALG[alg], seeds.data_ptr(),
+                                     lengths.data_ptr() if lengths is not None else None,
+                                     int(uniform_len), n, int(chunk_log2), DTYPE[dtype], out.data_ptr() or None,
+                                     ws_ptr or None, ws_bytes, status.data_ptr(), _stream_ptr(stream))
+    _check(st, "zig_generate_checked")
 
 
 def zig_generate_noalloc(prng: str, alg: str, seeds, lengths, out, chunk_log2: int = 0,

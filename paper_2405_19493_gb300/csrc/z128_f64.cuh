@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
     if (lane == 0) ws.tq_n = 0;
     __syncwarp();
     if (a.out == nullptr) {   // only legal when every length is zero
-        if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&d_err, kErrNullOutput);
+        if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.err, kErrNullOutput);
         return;
     }
     const uint64_t n_units = units_total(a);
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
             rem -= (uint64_t)k_out;
             __syncwarp();
         }
-        if (check_chunk && draws > kChunkDraws) atomicOr(&d_err, kErrChunkOverflow);
+        if (check_chunk && draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
     }
     drain_tails(ws, lane);
 }

@@ -16,10 +16,10 @@ constexpr uint64_t kLxmM = 0xD1342543DE82EF95ull;    // L64X128Mix LCG multiplie
 constexpr uint64_t kLeaM = 0xDABA0B6EB09322E3ull;    // Lea's 64-bit mix constant
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Error bits latched in the per-device error word.
+// Error bits latched in a device error word (the caller's, or the device's own).
 constexpr unsigned kErrChunkOverflow = 1u;
-constexpr unsigned kErrTimeout = 2u;
 constexpr unsigned kErrNullOutput = 4u;   // variable lengths summed > 0 with out == NULL
+constexpr unsigned kErrLengthSum = 8u;    // variable lengths summed to 2^40 or more
 
 // Jump-ahead tables for 2^b raw steps, b = 0..63 (filled on the host at init).
 struct JumpTab {

@@ -68,6 +68,7 @@ struct GenArgs {
     const struct MutDesc* reqs;  // batched mutation: request descriptors
     uint32_t n_req;              // batched mutation: number of requests
     uint32_t lane_sectors;       // generation: 1 = lane-per-row flush in 32-byte sectors
+    unsigned* err;               // where device-side errors are latched (a caller's word or the device's)
 };
 
 // One mutation request of a batch (device copy; ustart = its first unit).
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
     OutT* stage = stage_all[threadIdx.x >> 5];
     if (a.out == nullptr) {   // only legal when every length is zero
         if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0)
-            atomicOr(&d_err, kErrNullOutput);
+            atomicOr(a.err, kErrNullOutput);
         return;
     }
     const uint64_t n_units = units_total(a);
@@ -367,7 +368,7 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
         if (a.chunk_log2 && n_unit) {
             const uint64_t per = (PRNG == ZIG_LCG48) ? 2 : 1;   // zig256's first draw is a nextLong
             uint64_t draws = (ALG == ZIG_POLAR) ? (uint64_t)extra : n_unit * per + extra;
-            if (draws > kChunkDraws) atomicOr(&d_err, kErrChunkOverflow);
+            if (draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
         }
     }
 }
@@ -859,7 +860,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
     W& ws = *(W*)(z128_dsm + (size_t)wib * z128_warp_bytes<G, DT, BW>());
     if (MODE == 0 && a.out == nullptr) {   // only legal when every length is zero
         if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0)
-            atomicOr(&d_err, kErrNullOutput);
+            atomicOr(a.err, kErrNullOutput);
         return;
     }
     const uint64_t n_units = units_total(a);
@@ -1122,7 +1123,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             }
             __syncwarp();
         }
-        if (check_chunk && draws > kChunkDraws) atomicOr(&d_err, kErrChunkOverflow);
+        if (check_chunk && draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
     }
 }
 
@@ -1167,7 +1168,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z256_kernel(GenArgs a) {
     uint64_t* const row = (uint64_t*)(z256_dsm + (size_t)wib * z256_warp_bytes()) + lane * kZ256Row;
     if (a.out == nullptr) {   // only legal when every length is zero
         if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0)
-            atomicOr(&d_err, kErrNullOutput);
+            atomicOr(a.err, kErrNullOutput);
         return;
     }
     const uint64_t n_units = units_total(a);
@@ -1232,7 +1233,7 @@ __global__ void __launch_bounds__(kZBlock, 1) z256_kernel(GenArgs a) {
             rem -= (uint64_t)slot;
             z128_flush_f64<B>(row, 0u, slot, slot, rem == 0, dst, nc);
         }
-        if (check_chunk && draws > kChunkDraws) atomicOr(&d_err, kErrChunkOverflow);
+        if (check_chunk && draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
     }
 }
 
@@ -1274,18 +1275,21 @@ __global__ void __launch_bounds__(256) selfcheck_kernel(unsigned long long* coun
     atomicAdd(&counts[5], ne_l);
 }
 
-// Exclusive prefix sums of lengths and unit counts (one block).
+// Exclusive prefix sums of lengths and unit counts (one block).  Sums saturate
+// at 2^40: a batch whose lengths reach it latches kErrLengthSum in *err and
+// gets no units, so nothing is generated or written.
 __global__ void __launch_bounds__(1024) scan_kernel(const uint64_t* lengths, uint64_t n,
                                                     uint32_t chunk_log2, uint64_t* offsets,
-                                                    uint64_t* ustart, uint64_t* totals) {
+                                                    uint64_t* ustart, uint64_t* totals, unsigned* err) {
+    constexpr uint64_t kLim = 1ull << 40;
     __shared__ uint64_t sl[1024], su[1024];
     const int t = threadIdx.x;
     const uint64_t per = (n + 1023) / 1024;
     const uint64_t b = umin64(n, (uint64_t)t * per), e = umin64(n, b + per);
     uint64_t accl = 0, accu = 0;
     for (uint64_t s = b; s < e; ++s) {
-        uint64_t L = lengths[s];
-        accl += L;
+        const uint64_t L = umin64(lengths[s], kLim);
+        accl = umin64(accl + L, kLim);
         accu += chunk_log2 ? ((L + (1ull << chunk_log2) - 1) >> chunk_log2) : (L ? 1 : 0);
     }
     sl[t] = accl;
@@ -1294,22 +1298,24 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint64_t* lengths, uin
     for (int d = 1; d < 1024; d <<= 1) {   // Hillis-Steele inclusive scan
         uint64_t vl = (t >= d) ? sl[t - d] : 0, vu = (t >= d) ? su[t - d] : 0;
         __syncthreads();
-        sl[t] += vl;
+        sl[t] = umin64(sl[t] + vl, kLim);
         su[t] += vu;
         __syncthreads();
     }
     accl = t ? sl[t - 1] : 0;
     accu = t ? su[t - 1] : 0;
     for (uint64_t s = b; s < e; ++s) {
-        uint64_t L = lengths[s];
+        const uint64_t L = umin64(lengths[s], kLim);
         offsets[s] = accl;
         ustart[s] = accu;
-        accl += L;
+        accl = umin64(accl + L, kLim);
         accu += chunk_log2 ? ((L + (1ull << chunk_log2) - 1) >> chunk_log2) : (L ? 1 : 0);
     }
     if (t == 1023) {
-        totals[0] = su[1023];
+        const bool over = sl[1023] >= kLim;
+        totals[0] = over ? 0 : su[1023];
         totals[1] = sl[1023];
+        if (over) atomicOr(err, kErrLengthSum);
     }
 }
 
@@ -1338,8 +1344,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 bool g_init[kMaxDevices];
 int g_sms[kMaxDevices];
-void* g_ws[kMaxDevices];
-size_t g_ws_bytes[kMaxDevices];
+unsigned* g_err_ptr[kMaxDevices];   // the device's own error word (d_err), per device
 
 struct Affine { uint64_t A, C; };
 static Affine compose(Affine o, Affine i) { return {o.A * i.A, o.A * i.C + o.C}; }
@@ -1447,7 +1452,10 @@ static zig_status init_device(int device) {
     ZIG_CUDA(cudaMemcpyToSymbol(d_jump, &jt, sizeof(jt)));
     unsigned zero = 0;
     ZIG_CUDA(cudaMemcpyToSymbol(d_err, &zero, sizeof(zero)));
+    void* ep = nullptr;
+    ZIG_CUDA(cudaGetSymbolAddress(&ep, d_err));
     ZIG_CUDA(cudaDeviceSynchronize());
+    g_err_ptr[device] = (unsigned*)ep;
     g_sms[device] = prop.multiProcessorCount;
     return ZIG_OK;
 }
@@ -1610,8 +1618,12 @@ struct LaunchFacts {
     int block;
     int per_sm;
 };
+// A fixed table (no allocation at call time); when it is full, facts are
+// resolved again at each launch.
+constexpr int kMaxFacts = 2048;
 std::mutex g_facts_mu;
-std::vector<LaunchFacts> g_facts;
+LaunchFacts g_facts[kMaxFacts];
+int g_n_facts = 0;
 
 static bool allow_dyn_smem(const void* fn, size_t bytes) {
     if (bytes == 0) return true;
@@ -1619,7 +1631,8 @@ static bool allow_dyn_smem(const void* fn, size_t bytes) {
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_facts_mu);
     // one record per kernel and device (block = -1): the largest opt-in so far
-    for (LaunchFacts& f : g_facts) {
+    for (int k = 0; k < g_n_facts; ++k) {
+        LaunchFacts& f = g_facts[k];
         if (f.fn == fn && f.dev == dev && f.block == -1) {
             if (bytes <= f.dyn) return true;
             if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
@@ -1630,19 +1643,21 @@ static bool allow_dyn_smem(const void* fn, size_t bytes) {
     }
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return false;
-    g_facts.push_back(LaunchFacts{fn, dev, bytes, -1, 0});
+    if (g_n_facts < kMaxFacts) g_facts[g_n_facts++] = LaunchFacts{fn, dev, bytes, -1, 0};
     return true;
 }
 
 static int blocks_per_sm(const void* fn, int dev, size_t dyn, int block) {
     std::lock_guard<std::mutex> lk(g_facts_mu);
-    for (const LaunchFacts& f : g_facts)
+    for (int k = 0; k < g_n_facts; ++k) {
+        const LaunchFacts& f = g_facts[k];
         if (f.fn == fn && f.dev == dev && f.dyn == dyn && f.block == block) return f.per_sm;
+    }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, dyn) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
-    g_facts.push_back(LaunchFacts{fn, dev, dyn, block, per_sm});
+    if (g_n_facts < kMaxFacts) g_facts[g_n_facts++] = LaunchFacts{fn, dev, dyn, block, per_sm};
     return per_sm;
 }
 
@@ -1702,6 +1717,47 @@ zig_status zig_tables_get_zig128(uint32_t* k_host, double* w_host, double* y_hos
     return ZIG_OK;
 }
 
+zig_status zig_tables_get(zig_alg alg, void* host_dst, size_t* bytes) {
+    if (!bytes || (unsigned)alg > 2u) return ZIG_ERR_INVALID_ARG;
+    const size_t need = alg == ZIG_ZIG128 ? sizeof(zig_tables128) : alg == ZIG_ZIG256 ? sizeof(zig_tables256) : 0;
+    const size_t cap = *bytes;
+    *bytes = need;
+    if (!host_dst || need == 0) return ZIG_OK;
+    if (cap < need) return ZIG_ERR_INVALID_ARG;
+    if (alg == ZIG_ZIG128) {
+        zig_tables128 t;
+        std::memset(&t, 0, sizeof(t));
+        t.R = zigtab::ZIG128_R;
+        t.V = zigtab::ZIG128_V;
+        std::memcpy(t.w, zigtab::ZIG128_W, sizeof(t.w));
+        std::memcpy(t.y, zigtab::ZIG128_Y, sizeof(t.y));
+        std::memcpy(t.k, zigtab::ZIG128_K, sizeof(t.k));
+        std::memcpy(t.w32, zigtab::ZIG128_W32, sizeof(t.w32));
+        std::memcpy(host_dst, &t, sizeof(t));
+    } else {
+        zig_tables256 t;
+        std::memset(&t, 0, sizeof(t));
+        const int nr = zigtab::ZIG256_NR;
+        t.n_r = (uint64_t)nr;
+        t.x0 = zigtab::ZIG256_X0;
+        for (int j = 0; j < nr; ++j) t.xs[j] = zigtab::ZIG256_XS[j];
+        for (int r = 1; r <= nr; ++r) {   // overhang r (1 .. n_r); index 0 is the tail
+            t.ox[r] = zigtab::ZIG256_OX[r - 1];
+            t.odx[r] = zigtab::ZIG256_ODX[r - 1];
+            t.oy[r] = zigtab::ZIG256_OY[r - 1];
+            t.ody[r] = zigtab::ZIG256_ODY[r - 1];
+            t.kind[r] = zigtab::ZIG256_KIND[r - 1];
+            t.qa[r] = zigtab::ZIG256_QA[r - 1];
+        }
+        for (int b = 0; b < 256; ++b) {
+            t.thr[b] = zigtab::ZIG256_THR[b];
+            t.alias[b] = zigtab::ZIG256_ALIAS[b];
+        }
+        std::memcpy(host_dst, &t, sizeof(t));
+    }
+    return ZIG_OK;
+}
+
 size_t zig_generate_workspace_bytes(uint64_t n_streams) {
     return (size_t)(16 * n_streams + 256);
 }
@@ -1713,7 +1769,8 @@ namespace host {
 static zig_status generate_impl(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
                                 const uint64_t* lengths_dev, uint64_t uniform_len, uint64_t n_streams,
                                 uint32_t chunk_log2, zig_dtype dtype, void* out_dev, void* workspace_dev,
-                                size_t workspace_bytes, void* stream, const LaunchCfg* force) {
+                                size_t workspace_bytes, unsigned* status_dev, void* stream,
+                                const LaunchCfg* force) {
     if ((unsigned)prng > 3u || (unsigned)alg > 2u || (unsigned)dtype > 2u) return ZIG_ERR_INVALID_ARG;
     if (chunk_log2 != 0 && (chunk_log2 < 4 || chunk_log2 > 24)) return ZIG_ERR_INVALID_ARG;
     if (n_streams == 0) return ZIG_OK;
@@ -1744,6 +1801,7 @@ static zig_status generate_impl(zig_prng prng, zig_alg alg, const uint64_t* seed
     a.n_streams = n_streams;
     a.chunk_log2 = chunk_log2;
     a.out = out_dev;
+    a.err = status_dev ? status_dev : host::g_err_ptr[dev];
     uint64_t n_groups_hint;
     if (lengths_dev == nullptr) {
         a.units_per_stream = chunk_log2 ? ((uniform_len + (1ull << chunk_log2) - 1) >> chunk_log2) : 1;
@@ -1752,29 +1810,30 @@ static zig_status generate_impl(zig_prng prng, zig_alg alg, const uint64_t* seed
     } else {
         size_t need = zig_generate_workspace_bytes(n_streams);
         uint64_t* ws;
+        void* own = nullptr;   // the call's own scratch, ordered on the stream
         if (workspace_dev) {
             if (workspace_bytes < need || ((uintptr_t)workspace_dev) % 16) return ZIG_ERR_INVALID_ARG;
             ws = (uint64_t*)workspace_dev;
         } else {
-            std::lock_guard<std::mutex> lk(host::g_mu);
-            if (host::g_ws_bytes[dev] < need) {
-                if (host::g_ws[dev]) cudaFree(host::g_ws[dev]);
-                host::g_ws[dev] = nullptr;
-                host::g_ws_bytes[dev] = 0;
-                if (cudaMalloc(&host::g_ws[dev], need) != cudaSuccess) return ZIG_ERR_CUDA;
-                host::g_ws_bytes[dev] = need;
-            }
-            ws = (uint64_t*)host::g_ws[dev];
+            // allocated and freed in the order of the caller's stream: calls on
+            // different streams never share it, and inside stream capture the
+            // graph owns the allocation
+            if (cudaMallocAsync(&own, need, s) != cudaSuccess) return ZIG_ERR_CUDA;
+            ws = (uint64_t*)own;
         }
         a.offsets = ws;
         a.ustart = ws + n_streams;
         a.totals = ws + 2 * n_streams;
         scan_kernel<<<1, 1024, 0, s>>>(lengths_dev, n_streams, chunk_log2, (uint64_t*)a.offsets,
-                                       (uint64_t*)a.ustart, (uint64_t*)a.totals);
-        if (cudaGetLastError() != cudaSuccess) return ZIG_ERR_CUDA;
+                                       (uint64_t*)a.ustart, (uint64_t*)a.totals, a.err);
+        st = cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
         n_groups_hint = ~0ull >> 8;   // unknown on the host: fill the device
+        if (st == ZIG_OK)
+            st = host::launch_gen(alg, prng, dtype, dev, true, n_groups_hint, a, s, force);
+        if (own && cudaFreeAsync(own, s) != cudaSuccess && st == ZIG_OK) st = ZIG_ERR_CUDA;
+        return st;
     }
-    return host::launch_gen(alg, prng, dtype, dev, lengths_dev != nullptr, n_groups_hint, a, s, force);
+    return host::launch_gen(alg, prng, dtype, dev, false, n_groups_hint, a, s, force);
 }
 }  // namespace host
 }  // namespace zig
@@ -1786,7 +1845,17 @@ zig_status zig_generate(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
                         uint32_t chunk_log2, zig_dtype dtype, void* out_dev, void* workspace_dev,
                         size_t workspace_bytes, void* stream) {
     return host::generate_impl(prng, alg, seeds_dev, lengths_dev, uniform_len, n_streams, chunk_log2,
-                               dtype, out_dev, workspace_dev, workspace_bytes, stream, nullptr);
+                               dtype, out_dev, workspace_dev, workspace_bytes, nullptr, stream, nullptr);
+}
+
+zig_status zig_generate_checked(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
+                                const uint64_t* lengths_dev, uint64_t uniform_len, uint64_t n_streams,
+                                uint32_t chunk_log2, zig_dtype dtype, void* out_dev, void* workspace_dev,
+                                size_t workspace_bytes, uint32_t* status_dev, void* stream) {
+    if (!status_dev || ((uintptr_t)status_dev) % 4) return ZIG_ERR_INVALID_ARG;
+    return host::generate_impl(prng, alg, seeds_dev, lengths_dev, uniform_len, n_streams, chunk_log2,
+                               dtype, out_dev, workspace_dev, workspace_bytes, (unsigned*)status_dev, stream,
+                               nullptr);
 }
 
 zig_status zig_launch_config_get(int device, zig_prng prng, zig_dtype dtype, int variable_lengths,
@@ -1870,7 +1939,8 @@ zig_status zig_autotune(zig_prng prng, const uint64_t* seeds_dev, const uint64_t
             if (r == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = ZIG_ERR_CUDA;
             if (st == ZIG_OK)
                 st = host::generate_impl(prng, ZIG_ZIG128, seeds_dev, lengths_dev, uniform_len, n_streams,
-                                         chunk_log2, dtype, out_dev, workspace_dev, workspace_bytes, stream, &c);
+                                         chunk_log2, dtype, out_dev, workspace_dev, workspace_bytes, nullptr,
+                                         stream, &c);
         }
         float ms = 0.0f;
         if (st == ZIG_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -1913,7 +1983,8 @@ zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_
     a.n_units = P * upr;
     a.sigma = sigma;
     a.seeds = nullptr;
-    // the kernel seeds row p with a.uniform_len + p in mutation mode; pass seed there
+    // the kernel seeds row p with a.mut_seed + p in mutation mode
+    a.err = host::g_err_ptr[dev];
     GenArgs am = a;
     host::GenFn fn = prng == ZIG_LCG48 ? z128_kernel<0, ZIG_F32, 1>
                    : prng == ZIG_SPLITMIX64 ? z128_kernel<1, ZIG_F32, 1>
@@ -1959,12 +2030,18 @@ zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_p
     zig_status st = host::current_device(dev);
     if (st != ZIG_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    // the descriptors are copied from host memory this call owns, which a captured
+    // graph would read again after it is gone: refused while the stream captures
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return ZIG_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return ZIG_ERR_INVALID_ARG;
     // pageable source: the copy is staged before this call returns, so reqs_host
     // may be reused at once
     if (cudaMemcpyAsync(desc_dev, d.data(), n_req * sizeof(MutDesc), cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return ZIG_ERR_CUDA;
     GenArgs a{};
+    a.err = host::g_err_ptr[dev];
     a.reqs = (const MutDesc*)desc_dev;
     a.n_req = n_req;
     a.n_units = units;
@@ -2011,9 +2088,12 @@ zig_status zig_device_status(int device, int clear) {
         unsigned zero = 0;
         if (cudaMemcpyToSymbol(d_err, &zero, sizeof(zero)) != cudaSuccess) return ZIG_ERR_CUDA;
     }
-    if (w & kErrNullOutput) return ZIG_ERR_INVALID_ARG;
-    if (w & kErrTimeout) return ZIG_ERR_TIMEOUT;
-    if (w & kErrChunkOverflow) return ZIG_ERR_CHUNK_OVERFLOW;
+    return zig_status_decode(w);
+}
+
+zig_status zig_status_decode(uint32_t word) {
+    if (word & (kErrNullOutput | kErrLengthSum)) return ZIG_ERR_INVALID_ARG;
+    if (word & kErrChunkOverflow) return ZIG_ERR_CHUNK_OVERFLOW;
     return ZIG_OK;
 }
 
@@ -2107,9 +2187,10 @@ extern "C" zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uin
     a.offsets = scratch;
     a.ustart = scratch + ZIG_NOALLOC_MAX_STREAMS;
     a.totals = scratch + 2 * ZIG_NOALLOC_MAX_STREAMS;
+    a.err = host::g_err_ptr[dev];
     // the scan rewrites every offset, unit start and total this call reads
     scan_kernel<<<1, 1024, 0, s>>>(lengths_dev, n_streams, chunk_log2, (uint64_t*)a.offsets,
-                                   (uint64_t*)a.ustart, (uint64_t*)a.totals);
+                                   (uint64_t*)a.ustart, (uint64_t*)a.totals, a.err);
     if (cudaGetLastError() != cudaSuccess) return ZIG_ERR_CUDA;
     return host::launch_gen(alg, prng, dtype, dev, true, ~0ull >> 8, a, s, nullptr);
 }

@@ -66,9 +66,10 @@ def test_every_candidate_gives_the_default_outputs(Z, prng, dtype):
         assert np.array_equal(run(Z, prng, dtype, su, None, 1001, 0, cfg), refu), cfg
     assert Z.zig_device_status(0) == 0
     # and the default matches the oracle
-    o, m, _ = O.generate(prng, "zig128", seeds_np, lengths=L, chunk_log2=10, with_margins=True)
+    o, m, _, vl = O.generate(prng, "zig128", seeds_np, lengths=L, chunk_log2=10, with_margins=True,
+                             with_via_log=True)
     g = ref.view({"f64": np.float64, "f32": np.float32, "bf16": np.uint16}[dtype])
-    compare_streams(g, o, m, offsets_of(L), L, kind=dtype)
+    compare_streams(g, o, m, offsets_of(L), L, kind=dtype, via_log=vl)
 
 
 def test_autotune_records_the_fastest_and_keeps_outputs(Z):

@@ -48,10 +48,11 @@ def gen(Z, prng, alg, seeds, lengths=None, uniform_len=0, chunk_log2=0, dtype="f
 
 def check(Z, prng, alg, seeds, lengths=None, uniform_len=0, chunk_log2=0, dtype="f64"):
     g = gen(Z, prng, alg, seeds, lengths, uniform_len, chunk_log2, dtype)
-    o, m, _ = O.generate(prng, alg, seeds, lengths=lengths, uniform_len=uniform_len,
-                         chunk_log2=chunk_log2, with_margins=True)
+    o, m, _, vl = O.generate(prng, alg, seeds, lengths=lengths, uniform_len=uniform_len,
+                             chunk_log2=chunk_log2, with_margins=True, with_via_log=True)
     L = lengths if lengths is not None else np.full(len(seeds), uniform_len, dtype=np.uint64)
-    return compare_streams(g, o, m, offsets_of(L), L, kind=dtype, all_inexact=(alg == "polar"))
+    return compare_streams(g, o, m, offsets_of(L), L, kind=dtype, all_inexact=(alg == "polar"),
+                           via_log=vl)
 
 
 # ---- uniform generators -------------------------------------------------------------
@@ -93,20 +94,46 @@ def test_narrow_outputs(Z, prng, dtype, alg):
     assert rep.max_ulp <= 1 and rep.flips == 0
 
 
+def full_size_sampled(Z, prng, alg, dtype="f64", n=1 << 20, L=1024, n_pick=1024):
+    """The bulk launch as timed (2^20 streams x 1,024): far more warp groups than
+    resident warps, so every lane runs many units; n_pick streams are compared,
+    the first and the last among them."""
+    seeds = W.seeds(n)
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    out = torch.empty(n * L, dtype=tdt, device="cuda")
+    Z.zig_generate(prng, alg, dev_u64(seeds), out, uniform_len=L, dtype=dtype)
+    pick = np.sort(np.random.default_rng(5).choice(n, n_pick, replace=False))
+    pick[0], pick[-1] = 0, n - 1
+    rows = out.view(n, L)[torch.from_numpy(pick).cuda()]
+    rows = (rows.view(torch.int16).cpu().numpy().view(np.uint16) if dtype == "bf16" else rows.cpu().numpy()).ravel()
+    del out
+    o, m, _, vl = O.generate(prng, alg, seeds[pick], uniform_len=L, with_margins=True, with_via_log=True)
+    Ls = np.full(len(pick), L, dtype=np.uint64)
+    return compare_streams(rows, o, m, offsets_of(Ls), Ls, kind=dtype, all_inexact=(alg == "polar"),
+                           via_log=vl)
+
+
 @pytest.mark.parametrize("prng", PRNGS)
 def test_bulk_full_size_sampled(Z, prng):
-    """The bulk launch as timed: 2^20 streams x 1,024 (2^30 binary64); 1,024 streams sampled."""
-    n, L = 1 << 20, 1024
-    seeds = W.seeds(n)
-    out = torch.empty(n * L, dtype=torch.float64, device="cuda")
-    Z.zig_generate(prng, "zig128", dev_u64(seeds), out, uniform_len=L)
-    pick = np.sort(np.random.default_rng(5).choice(n, 1024, replace=False))
-    pick[0], pick[-1] = 0, n - 1
-    rows = out.view(n, L)[torch.from_numpy(pick).cuda()].cpu().numpy().ravel()
-    del out
-    o, m, _ = O.generate(prng, "zig128", seeds[pick], uniform_len=L, with_margins=True)
-    Ls = np.full(len(pick), L, dtype=np.uint64)
-    compare_streams(rows, o, m, offsets_of(Ls), Ls)
+    """The bulk binary64 launch as timed: 2^20 streams x 1,024 (2^30 values)."""
+    full_size_sampled(Z, prng, "zig128")
+
+
+@pytest.mark.parametrize("prng", PRNGS)
+def test_zig256_full_size_sampled(Z, prng):
+    full_size_sampled(Z, prng, "zig256")
+
+
+@pytest.mark.parametrize("prng", ["lcg48", "splitmix64"])
+def test_polar_full_size_sampled(Z, prng):
+    full_size_sampled(Z, prng, "polar", n_pick=256)
+
+
+@pytest.mark.parametrize("prng", ["splitmix64", "l64x128mix"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_narrow_full_size_sampled(Z, prng, dtype):
+    rep = full_size_sampled(Z, prng, "zig128", dtype=dtype)
+    assert rep.max_ulp <= 1 and rep.flips == 0
 
 
 @pytest.mark.parametrize("prng", PRNGS)
@@ -181,9 +208,9 @@ def test_batched_workload_sampled(Z):
     pick = np.unique(np.concatenate([order[:8], order[-3:], order[::800]]))
     got = np.concatenate([out[int(off[s]):int(off[s] + L[s])].cpu().numpy() for s in pick])
     del out
-    o, m, _ = O.generate("splitmix64", "zig128", seeds[pick], lengths=L[pick], chunk_log2=10,
-                         with_margins=True)
-    compare_streams(got, o, m, offsets_of(L[pick]), L[pick])
+    o, m, _, vl = O.generate("splitmix64", "zig128", seeds[pick], lengths=L[pick], chunk_log2=10,
+                             with_margins=True, with_via_log=True)
+    compare_streams(got, o, m, offsets_of(L[pick]), L[pick], via_log=vl)
 
 
 def test_invalid_arguments(Z):
@@ -216,6 +243,26 @@ def test_mutate(Z, prng):
     # z enters as binary32 (<= 1 ulp from RN(z)), then one fused multiply-add
     tol = 2 * np.spacing(np.abs(want)) + abs(sigma) * 2 * np.spacing(np.abs(z).astype(np.float32))
     assert np.all(np.abs(got.astype(np.float64) - want) <= tol)
+
+
+def test_mutate_large_population_sampled(Z):
+    """4,096 rows of 40,000: 163,840 units of 2^10 variates, more than the resident warps
+    hold at once; 48 rows compared, the first and the last among them."""
+    P, L, sigma, seed = 4096, 40000, 0.25, 987654321
+    x = torch.zeros((P, L), dtype=torch.float32, device="cuda")
+    Z.zig_mutate(x, sigma, P, L, seed, "l64x128mix")
+    torch.cuda.synchronize()
+    pick = np.sort(np.random.default_rng(9).choice(P, 48, replace=False))
+    pick[0], pick[-1] = 0, P - 1
+    got = x[torch.from_numpy(pick).cuda()].cpu().numpy().astype(np.float64)
+    del x
+    z, _, _ = O.generate("l64x128mix", "zig128", np.uint64(seed) + pick.astype(np.uint64),
+                         uniform_len=L, chunk_log2=10)
+    z = z.reshape(len(pick), L)
+    want = np.float64(np.float32(sigma)) * z
+    # x starts at 0: fmaf(sigma, z32, 0) = RN32(sigma z32), z32 within 1 ulp of RN32(z)
+    tol = 2 * np.spacing(np.abs(want).astype(np.float32)).astype(np.float64) + 1e-45
+    assert np.all(np.abs(got - want) <= tol)
 
 
 def test_device_status_clean(Z):

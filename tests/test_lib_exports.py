@@ -153,3 +153,20 @@ def test_more_host_side_argument_errors():
     assert lib.zig_autotune(0, P, None, 16, 4, 0, 0, P, None, 0, 0, None, None, None) == INVALID
     assert lib.zig_autotune(0, P, None, 16, 4, 0, 0, P, None, 0, 1001, None, None, None) == INVALID
     assert lib.zig_selfcheck(None) == INVALID
+
+
+def test_status_decode_and_table_sizes():
+    """Error words decode to statuses; zig_tables_get reports sizes and refuses bad calls."""
+    import ctypes as C
+    for word, want in ((0, 0), (1, 6), (4, 1), (8, 1), (4 | 1, 1), (8 | 1, 1)):
+        assert Z.zig_status_decode(word) == want
+    lib = Z.load()
+    n = C.c_size_t(0)
+    assert lib.zig_tables_get(0, None, C.byref(n)) == 0 and n.value == C.sizeof(B.Tables128)
+    assert lib.zig_tables_get(2, None, C.byref(n)) == 0 and n.value == C.sizeof(B.Tables256)
+    assert lib.zig_tables_get(1, None, C.byref(n)) == 0 and n.value == 0
+    small = C.c_size_t(16)
+    buf = (C.c_uint8 * 16)()
+    assert lib.zig_tables_get(0, buf, C.byref(small)) == 1
+    assert lib.zig_tables_get(3, None, C.byref(n)) == 1
+    assert lib.zig_tables_get(0, None, None) == 1

@@ -74,3 +74,22 @@ def test_generated_file_is_current():
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
     assert open(INC).read() == mod.render()
+
+
+def test_c_abi_tables_equal_the_oracle():
+    """zig_tables_get through the C ABI (no device needed) against the oracle's tables."""
+    import paper_2405_19493_gb300 as Z
+    t = Z.zig_tables_get("zig128")
+    o = O.read_zig128()
+    assert t["R"] == o["R"] and t["V"] == o["v"]
+    assert t["k"] == o["k"] and t["w"] == o["w"] and t["y"] == o["y"]
+    u = Z.zig_tables_get("zig256")
+    o = O.read_zig256()
+    n = o["n_r"]
+    assert u["n_r"] == n and u["x0"] == o["x0"]
+    assert u["xs"][:n] == o["xs"] and all(v == 0.0 for v in u["xs"][n:])
+    for name in ("ox", "odx", "oy", "ody", "qa"):
+        assert u[name][1:n + 1] == o[name][1:], name
+    assert u["kind"][1:n + 1] == o["kind"][1:]
+    assert u["thr"] == o["thr"] and u["alias"] == o["alias"]
+    assert Z.zig_tables_get("polar") == {}
