@@ -10,7 +10,8 @@
  * bullets; Table 3).  This library is the bulk form of that call:
  *
  *     stream s's outputs are exactly the values that repeated nextGaussian
- *     calls return on a generator seeded with seeds[s].
+ *     calls return on a generator seeded with seeds[s] (zig_generate), or on a
+ *     generator kept between calls in a device record (zig_generate_state).
  *
  * Conventions for every entry point:
  *  - Pointers named *_dev are device pointers in the current CUDA context's
@@ -22,7 +23,8 @@
  *  - Argument errors are detected on the host and returned synchronously, with
  *    nothing enqueued.  Launch failures return ZIG_ERR_CUDA.  Conditions only the
  *    GPU can see (a NULL output for lengths that sum above zero, lengths that sum
- *    to 2^40 or more, a chunk overrunning its 2^32-draw budget) are latched in an
+ *    to 2^40 or more, a chunk overrunning its 2^32-draw budget, a stream record
+ *    seeded for another generator) are latched in an
  *    error word on the device: the caller's own word for zig_generate_checked
  *    (scoped to that call), else the device's shared word, read and cleared with
  *    zig_device_status().
@@ -202,9 +204,61 @@ zig_status zig_generate_checked(zig_prng prng, zig_alg alg, const uint64_t *seed
 
 /* The status an error word holds (the word of zig_generate_checked, or the value
  * zig_device_status reads): ZIG_OK, ZIG_ERR_INVALID_ARG (a NULL output for
- * lengths summing above zero, or lengths summing to 2^40 or more) or
+ * lengths summing above zero, lengths summing to 2^40 or more, or a stream
+ * record seeded for another generator) or
  * ZIG_ERR_CHUNK_OVERFLOW, in that order of precedence.  No CUDA call. */
 zig_status zig_status_decode(uint32_t word);
+
+/*
+ * Streams that continue across calls.  The paper's nextGaussian draws from a
+ * generator object that the caller keeps between calls (Sec. 2, Listing 2); a
+ * zig_stream_state is that object for one stream, held in device memory.
+ * zig_state_init seeds the records; each zig_generate_state call continues
+ * every stream where its previous call stopped and advances its record, so
+ * that L1 outputs followed by L2 outputs equal the first L1 + L2 outputs that
+ * one call takes (and that zig_generate with chunk_log2 = 0 takes from the
+ * same seed), for every transform, generator and dtype.
+ *
+ *  gen           the generator's state words, positioned at the stream's next
+ *                raw draw: LCG48 and SplitMix64 gen[0] = s; L64X128Mix gen[0..3]
+ *                = a, s, x0, x1; Xoroshiro128PlusPlus gen[0..1] = x0, x1.
+ *  polar_cached  the polar method's second variate of its last pair, pending
+ *  polar_have    when polar_have = 1: the next ZIG_POLAR call returns it first.
+ *                A call of another transform on the stream discards it.
+ *  prng          the generator the record was seeded for.  A call with another
+ *                generator writes nothing for that stream and latches
+ *                ZIG_ERR_INVALID_ARG in the error word.
+ * 48 bytes per stream, 16-byte aligned arrays, owned by the caller.
+ */
+typedef struct {
+    uint64_t gen[4];
+    double polar_cached;
+    uint32_t polar_have;
+    uint32_t prng;
+} zig_stream_state;
+
+/* zig_state_init -- state_dev[s] = generator `prng` seeded with seeds_dev[s]
+ * exactly as zig_generate seeds stream s, nothing pending (device buffers;
+ * enqueued on stream). */
+zig_status zig_state_init(zig_prng prng, const uint64_t *seeds_dev, uint64_t n_streams,
+                          zig_stream_state *state_dev, void *stream);
+
+/*
+ * zig_generate_state -- zig_generate with stream s continued from state_dev[s]
+ * instead of seeded, and state_dev[s] advanced past its outputs.  Each stream
+ * runs as one sequential generator (no chunking), so a stream of length L is
+ * one thread's work: very long streams of very uneven lengths balance worse than
+ * in zig_generate's chunked form.  lengths_dev / uniform_len, n_streams, dtype,
+ * out_dev, the workspace and the argument errors are those of zig_generate.
+ * status_dev is the caller's error word as for zig_generate_checked, or NULL
+ * for the device's shared word.  A stream of length 0 keeps its record.  The
+ * records of a call must not be read or written by other work until the call
+ * has completed on `stream`.
+ */
+zig_status zig_generate_state(zig_prng prng, zig_alg alg, zig_stream_state *state_dev,
+                              const uint64_t *lengths_dev, uint64_t uniform_len, uint64_t n_streams,
+                              zig_dtype dtype, void *out_dev, void *workspace_dev,
+                              size_t workspace_bytes, uint32_t *status_dev, void *stream);
 
 /*
  * zig_generate_noalloc -- zig_generate for a variable-length batch, with no
@@ -316,27 +370,43 @@ zig_status zig_autotune(zig_prng prng, const uint64_t *seeds_dev, const uint64_t
 zig_status zig_mutate(float *x_dev, float sigma, uint64_t P, uint64_t L, uint64_t seed,
                       zig_prng prng, void *stream);
 
+/*
+ * zig_mutate_state -- zig_mutate whose row p continues the stream kept in
+ * state_dev[p] (P records, zig_stream_state) as one sequential generator and
+ * advances it: row p's increments are the next L outputs of that stream, i.e.
+ * zig_generate_state(prng, ZIG_ZIG128, state_dev, uniform_len = L, ZIG_F32) on
+ * it, so that mutating the same population again continues its streams.
+ * Records seeded for another generator leave their rows unchanged and latch
+ * ZIG_ERR_INVALID_ARG in the device's error word.
+ */
+zig_status zig_mutate_state(float *x_dev, float sigma, uint64_t P, uint64_t L,
+                            zig_stream_state *state_dev, zig_prng prng, void *stream);
+
 /* Request kinds of a batch (zig_mutation.kind). */
 #define ZIG_REQ_MUTATE 0u   /* x_dev += sigma * N(0,1), exactly as zig_mutate */
 #define ZIG_REQ_GENERATE 1u /* x_dev = N(0,1) (sigma ignored): row p equals
                                zig_generate(prng, ZIG_ZIG128, seeds = {seed + p},
                                uniform_len = L, chunk_log2 = 10, ZIG_F32) */
 
-/* One request of a batch on a P x L binary32 row-major device buffer x_dev,
- * rows seeded seed + p.  kind is ZIG_REQ_MUTATE (the zero default) or
- * ZIG_REQ_GENERATE. */
+/* One request of a batch on a P x L binary32 row-major device buffer x_dev.
+ * kind is ZIG_REQ_MUTATE (the zero default) or ZIG_REQ_GENERATE.  state_dev
+ * NULL: rows seeded seed + p and chunked as zig_mutate.  Otherwise P stream
+ * records: row p continues state_dev[p] as zig_mutate_state does (seed
+ * ignored) and advances it; two requests of one batch must not share records. */
 typedef struct {
     float *x_dev;
     uint64_t P, L;
     float sigma;
     uint32_t kind;
     uint64_t seed;
+    zig_stream_state *state_dev;
 } zig_mutation;
 
 /*
  * zig_mutate_batch -- n_req mutation requests in one launch (continuous
  * batching of the Gaussian-mutation workload, Sec. 1).  Each request's result is
- * identical to zig_mutate on it alone; requests must not overlap in memory.
+ * identical to zig_mutate (zig_mutate_state for a request with stream records)
+ * on it alone; requests must not overlap in memory.
  * reqs_host: host array (copied before the call returns).  desc_dev: device
  * scratch of at least zig_mutate_batch_desc_bytes(n_req) bytes, 16-byte aligned,
  * not used by another call in flight.  All requests use one generator `prng`.
@@ -355,7 +425,8 @@ zig_status zig_mutate_batch(const zig_mutation *reqs_host, uint32_t n_req, zig_p
  * max_batch of them into one zig_mutate_batch launch on one of n_slots streams,
  * and retires a launch when its CUDA event completes; requests that arrive
  * meanwhile go to the next free slot, so launches overlap on the device.  Each
- * result equals zig_mutate on that request alone.  Populations are
+ * result equals zig_mutate (zig_mutate_state for requests on a population kept
+ * by the service) on that request alone.  Populations are
  * caller-owned device memory and must not overlap while in flight.
  * device < 0 runs the scheduler without a GPU (launches complete after a
  * simulated time), for testing the admission logic.
@@ -390,6 +461,28 @@ zig_status zig_server_submit(zig_server *server, float *x_dev, uint64_t P, uint6
  * batched and reported like mutation requests (the same tickets and queue). */
 zig_status zig_server_submit_generate(zig_server *server, float *out_dev, uint64_t P, uint64_t L,
                                       uint64_t seed, uint64_t *ticket);
+/*
+ * Populations whose streams the service keeps on the device, so that repeated
+ * requests on one population continue its rows' streams (an evolutionary
+ * algorithm mutating the same population once per generation).
+ * zig_server_population          -- P stream records seeded seed + p
+ *                                   (zig_state_init; device memory the service
+ *                                   owns, 48 B per row); returns a handle.
+ * zig_server_submit_population   -- a request (kind ZIG_REQ_MUTATE or
+ *                                   ZIG_REQ_GENERATE) on P x L binary32 x_dev
+ *                                   whose rows continue the population's
+ *                                   streams (zig_mutate_state).  Requests on
+ *                                   one population run one at a time, in
+ *                                   submission order: a request waits at the
+ *                                   head of the queue while an earlier one on
+ *                                   its population is in flight.
+ * zig_server_population_release  -- wait until no queued or running request uses
+ *                                   the population, then free its records.
+ */
+zig_status zig_server_population(zig_server *server, uint64_t P, uint64_t seed, uint64_t *population);
+zig_status zig_server_submit_population(zig_server *server, uint64_t population, float *x_dev,
+                                        uint64_t L, float sigma, uint32_t kind, uint64_t *ticket);
+zig_status zig_server_population_release(zig_server *server, uint64_t population);
 zig_status zig_server_wait(zig_server *server, uint64_t ticket, double timeout_s);
 zig_status zig_server_query(zig_server *server, uint64_t ticket, int *state, double *latency_us,
                             double *queue_us);

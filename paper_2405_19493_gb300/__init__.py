@@ -15,7 +15,8 @@ from ._binding import (  # noqa: F401
     zig_generate_workspace_bytes,
     zig_mutate, zig_mutate_batch, zig_prng_fill, zig_status_string, zig_tables_get_zig128, zig_tables_init,
     zig_version, zig_launch_config_get, zig_launch_config_set, zig_autotune_candidates, zig_autotune,
-    zig_generate_checked, zig_status_decode, zig_tables_get,
+    zig_generate_checked, zig_status_decode, zig_tables_get, zig_state_new, zig_state_init, zig_state_read,
+    zig_generate_state, zig_mutate_state,
 )
 
 __all__ = [
@@ -23,5 +24,6 @@ __all__ = [
     "zig_generate_workspace_bytes", "zig_mutate", "zig_mutate_batch", "zig_prng_fill", "zig_status_string",
     "zig_tables_get_zig128", "zig_tables_init", "zig_version", "zig_launch_config_get",
     "zig_launch_config_set", "zig_autotune_candidates", "zig_autotune", "zig_generate_checked",
-    "zig_status_decode", "zig_tables_get",
+    "zig_status_decode", "zig_tables_get", "zig_state_new", "zig_state_init", "zig_state_read",
+    "zig_generate_state", "zig_mutate_state",
 ]

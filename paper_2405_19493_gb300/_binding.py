@@ -37,16 +37,29 @@ EXPORTS = (
     "zig_server_drain", "zig_server_stats", "zig_server_destroy", "zig_server_submit_generate",
     "zig_launch_config_get", "zig_launch_config_set", "zig_autotune_candidates", "zig_autotune",
     "zig_selfcheck", "zig_generate_checked", "zig_status_decode", "zig_tables_get",
+    "zig_state_init", "zig_generate_state", "zig_mutate_state", "zig_server_population",
+    "zig_server_submit_population", "zig_server_population_release",
 )
+
+# bytes of one zig_stream_state record (include/zig.h)
+STATE_BYTES = 48
 
 
 REQ_KIND = {"mutate": 0, "generate": 1}   # ZIG_REQ_MUTATE, ZIG_REQ_GENERATE
 
 
 class Mutation(C.Structure):
-    """zig_mutation: one request of a batch (kind: ZIG_REQ_MUTATE or ZIG_REQ_GENERATE)."""
+    """zig_mutation: one request of a batch (kind: ZIG_REQ_MUTATE or ZIG_REQ_GENERATE;
+    state_dev: the rows' stream records, or NULL for rows seeded seed + p)."""
     _fields_ = [("x_dev", C.c_void_p), ("P", C.c_uint64), ("L", C.c_uint64),
-                ("sigma", C.c_float), ("kind", C.c_uint32), ("seed", C.c_uint64)]
+                ("sigma", C.c_float), ("kind", C.c_uint32), ("seed", C.c_uint64),
+                ("state_dev", C.c_void_p)]
+
+
+class StreamState(C.Structure):
+    """zig_stream_state: one stream's generator kept between calls."""
+    _fields_ = [("gen", C.c_uint64 * 4), ("polar_cached", C.c_double), ("polar_have", C.c_uint32),
+                ("prng", C.c_uint32)]
 
 
 class LaunchConfig(C.Structure):
@@ -142,6 +155,15 @@ def load(build_if_missing: bool = True):
         lib.zig_status_decode.argtypes = [C.c_uint32]
         lib.zig_tables_get.argtypes = [i32, vp, C.POINTER(C.c_size_t)]
         for name in ("zig_generate_checked", "zig_status_decode", "zig_tables_get"):
+            getattr(lib, name).restype = i32
+        lib.zig_state_init.argtypes = [i32, vp, u64, vp, vp]
+        lib.zig_generate_state.argtypes = [i32, i32, vp, vp, u64, u64, i32, vp, vp, C.c_size_t, vp, vp]
+        lib.zig_mutate_state.argtypes = [vp, C.c_float, u64, u64, vp, i32, vp]
+        lib.zig_server_population.argtypes = [vp, u64, u64, C.POINTER(u64)]
+        lib.zig_server_submit_population.argtypes = [vp, u64, vp, u64, C.c_float, C.c_uint32, C.POINTER(u64)]
+        lib.zig_server_population_release.argtypes = [vp, u64]
+        for name in ("zig_state_init", "zig_generate_state", "zig_mutate_state", "zig_server_population",
+                     "zig_server_submit_population", "zig_server_population_release"):
             getattr(lib, name).restype = i32
         lib.zig_status_string.argtypes = [i32]
         lib.zig_status_string.restype = C.c_char_p
@@ -248,6 +270,42 @@ def zig_generate_checked(prng: str, alg: str, seeds, out, status, lengths=None, 
     _check(st, "zig_generate_checked")
 
 
+def zig_state_new(n_streams: int):
+    """A device buffer for n_streams zig_stream_state records (48 bytes each, 16-byte aligned)."""
+    import torch
+    return torch.empty(max(int(n_streams), 1) * STATE_BYTES // 8, dtype=torch.int64, device="cuda")
+
+
+def zig_state_init(prng: str, seeds, state, stream=None) -> None:
+    """Seed state[s] as zig_generate seeds stream s (seeds: a CUDA uint64/int64 tensor)."""
+    st = load().zig_state_init(PRNG[prng], seeds.data_ptr(), int(seeds.numel()), state.data_ptr(),
+                               _stream_ptr(stream))
+    _check(st, "zig_state_init")
+
+
+def zig_state_read(state, n_streams: int) -> list:
+    """The records as dicts (copied to the host; for inspection and tests)."""
+    raw = state.view(-1)[: n_streams * STATE_BYTES // 8].cpu().numpy().tobytes()
+    recs = (StreamState * n_streams).from_buffer_copy(raw)
+    return [{"gen": list(r.gen), "polar_cached": r.polar_cached, "polar_have": r.polar_have,
+             "prng": r.prng} for r in recs]
+
+
+def zig_generate_state(prng: str, alg: str, state, out, n_streams: int, lengths=None,
+                       uniform_len: int = 0, dtype: str = "f64", workspace=None, status=None,
+                       stream=None) -> None:
+    """zig_generate continuing each stream from its record and advancing it."""
+    ws_ptr, ws_bytes = (0, 0)
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    st = load().zig_generate_state(PRNG[prng], ALG[alg], state.data_ptr(),
+                                   lengths.data_ptr() if lengths is not None else None,
+                                   int(uniform_len), int(n_streams), DTYPE[dtype], out.data_ptr() or None,
+                                   ws_ptr or None, ws_bytes, status.data_ptr() if status is not None else None,
+                                   _stream_ptr(stream))
+    _check(st, "zig_generate_state")
+
+
 def zig_generate_noalloc(prng: str, alg: str, seeds, lengths, out, chunk_log2: int = 0,
                          dtype: str = "f64", stream=None) -> None:
     """Variable-length generation that allocates nothing, for callers that cannot
@@ -268,18 +326,28 @@ def zig_mutate(x, sigma: float, P: int, L: int, seed: int, prng: str = "splitmix
     _check(st, "zig_mutate")
 
 
+def zig_mutate_state(x, sigma: float, P: int, L: int, state, prng: str = "splitmix64",
+                     stream=None) -> None:
+    """x += sigma z with row p continuing the stream record state[p] (zig_state_init)."""
+    st = load().zig_mutate_state(x.data_ptr(), float(sigma), int(P), int(L), state.data_ptr(),
+                                 PRNG[prng], _stream_ptr(stream))
+    _check(st, "zig_mutate_state")
+
+
 def zig_mutate_batch(requests, prng: str = "splitmix64", desc=None, stream=None) -> None:
-    """requests: list of (x, sigma, seed) or (x, sigma, seed, kind) with x a P x L float32
-    CUDA tensor and kind "mutate" (x += sigma z, the default) or "generate" (x = z)."""
+    """requests: list of (x, sigma, seed), (x, sigma, seed, kind) or (x, sigma, seed, kind, state)
+    with x a P x L float32 CUDA tensor, kind "mutate" (x += sigma z, the default) or
+    "generate" (x = z), and state the rows' stream records (rows continue them; seed ignored)."""
     import torch
     n = len(requests)
     arr = (Mutation * max(n, 1))()
     for k, req in enumerate(requests):
         x, sigma, seed = req[:3]
         kind = REQ_KIND[req[3]] if len(req) > 3 else 0
+        state = req[4] if len(req) > 4 else None
         P, L = (x.shape[0], x.shape[1]) if x.dim() == 2 else (1, x.numel())
         arr[k] = Mutation(x.data_ptr() or None, P, L, float(sigma or 0.0), kind,
-                          int(seed) & (2 ** 64 - 1))
+                          int(seed) & (2 ** 64 - 1), state.data_ptr() if state is not None else None)
     need = int(load().zig_mutate_batch_desc_bytes(n))
     if desc is None:
         desc = torch.empty(need, dtype=torch.uint8, device="cuda")

@@ -355,13 +355,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
         double* dst = out;
         G g;
         g.seed(0);
+        zig_stream_state* srec = nullptr;   // the record to advance when the unit ends
         if (u < n_units) {
             uint64_t s, q, off, n;
             unit_info(a, u, s, q, off, n);
-            g.seed(a.seeds[s]);
-            if (q) g.jump(q * kChunkDraws, &d_jump);
-            rem = n;
-            dst = out + off;
+            bool ok;
+            srec = unit_gen<PRNG>(a, s, q, g, ok);
+            if (ok) {
+                rem = n;
+                dst = out + off;
+            }
         }
         const bool check_chunk = a.chunk_log2 != 0 && rem != 0;
         uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
@@ -472,12 +475,24 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
                 uint32_t keepm = ~D;
                 for (int m = 0; m < k_out; ++m) keepm &= keepm - 1u;   // the slots past the rem-th kept one
                 D |= keepm;
-                if (check_chunk && k_out > 0) {
+                if ((check_chunk || srec) && k_out > 0) {
                     // the draws up to the last output and its uniforms
                     const int c = 31 - __clz(~D);   // slot of the last output
                     int used = c + 1;
                     while (used < n && ((du >> used) & 1u)) ++used;
                     draws += (uint64_t)used;
+                    // the stream's record: the generator after those draws (the
+                    // batch drew n from the state sb)
+                    if (srec) {
+                        G t = g;
+                        if constexpr (PRNG == ZIG_LCG48 || PRNG == ZIG_SPLITMIX64) {
+                            t.s = sb;
+                            t.jump((uint64_t)used, &d_jump);
+                        } else {
+                            for (int k = used; k < n; ++k) t.unstep();
+                        }
+                        state_store(srec, t, false, 0.0);
+                    }
                 }
             } else if (check_chunk) {
                 draws += (uint64_t)n;

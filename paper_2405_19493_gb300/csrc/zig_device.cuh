@@ -20,6 +20,17 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr unsigned kErrChunkOverflow = 1u;
 constexpr unsigned kErrNullOutput = 4u;   // variable lengths summed > 0 with out == NULL
 constexpr unsigned kErrLengthSum = 8u;    // variable lengths summed to 2^40 or more
+constexpr unsigned kErrStateKind = 16u;   // a stream record seeded for another generator
+
+// The inverse of an odd multiplier modulo 2^64 (Newton's iteration x <- x (2 - m x),
+// which doubles the number of correct low bits; m x = 1 mod 8 holds for x = m).
+__host__ __device__ constexpr uint64_t inverse_mod_2_64(uint64_t m) {
+    uint64_t x = m;
+    for (int k = 0; k < 5; ++k) x *= 2 - m * x;
+    return x;
+}
+constexpr uint64_t kLxmMinv = inverse_mod_2_64(kLxmM);
+static_assert(kLxmM * kLxmMinv == 1, "L64X128Mix multiplier inverse");
 
 // Jump-ahead tables for 2^b raw steps, b = 0..63 (filled on the host at init).
 struct JumpTab {
@@ -53,15 +64,22 @@ __device__ __forceinline__ uint64_t mix_lea64(uint64_t z) {
 __device__ __forceinline__ uint64_t rotl64(uint64_t x, int k) {
     return (x << k) | (x >> (64 - k));
 }
+__device__ __forceinline__ uint64_t rotr64(uint64_t x, int k) {
+    return (x >> k) | (x << (64 - k));
+}
 
 // ---------------------------------------------------------------------------
 // generators: one per thread, state in registers
 //   next_u32 = nextInt, next_u64 = nextLong, next_m53 = the 53-bit integer of nextDouble
 // ---------------------------------------------------------------------------
 
+// load/save: the state words of a stream record (zig_stream_state.gen), in the
+// order the C header states for each generator.
 struct GenLcg48 {
     uint64_t s;
     __device__ __forceinline__ void seed(uint64_t x) { s = (x ^ kLcgA) & kMask48; }
+    __device__ __forceinline__ void load(const uint64_t* w) { s = w[0] & kMask48; }
+    __device__ __forceinline__ void save(uint64_t* w) const { w[0] = s; }
     __device__ __forceinline__ uint32_t step(int bits) {
         s = (s * kLcgA + kLcgC) & kMask48;
         return (uint32_t)(s >> (48 - bits));
@@ -110,6 +128,8 @@ struct GenLcg48 {
 struct GenSplitMix64 {
     uint64_t s;
     __device__ __forceinline__ void seed(uint64_t x) { s = x; }
+    __device__ __forceinline__ void load(const uint64_t* w) { s = w[0]; }
+    __device__ __forceinline__ void save(uint64_t* w) const { w[0] = s; }
     __device__ __forceinline__ uint32_t next_u32() { s += kGamma; return mix32(s); }
     __device__ __forceinline__ uint64_t next_u64() { s += kGamma; return mix64(s); }
     __device__ __forceinline__ uint64_t next_m53() { s += kGamma; return mix64(s) >> 11; }
@@ -132,6 +152,27 @@ struct GenL64X128Mix {
         t += kGamma; x0 = mix64(t);
         t += kGamma; x1 = mix64(t);
         if ((x0 | x1) == 0) x1 = kGamma;
+    }
+    __device__ __forceinline__ void load(const uint64_t* w) {
+        a = w[0] | 1;
+        s = w[1];
+        x0 = w[2];
+        x1 = w[3];
+    }
+    __device__ __forceinline__ void save(uint64_t* w) const {
+        w[0] = a;
+        w[1] = s;
+        w[2] = x0;
+        w[3] = x1;
+    }
+    // one raw step back (the inverse of advance): the LCG by the multiplier's
+    // inverse; the xoroshiro128 step by undoing x1 = rotl(t, 37), then
+    // rotl(x0, 24) = x0' ^ t ^ (t << 16), then t = x1 ^ x0
+    __device__ __forceinline__ void unstep() {
+        s = kLxmMinv * (s - a);
+        const uint64_t t = rotr64(x1, 37);
+        x0 = rotr64(x0 ^ t ^ (t << 16), 24);
+        x1 = t ^ x0;
     }
     __device__ __forceinline__ uint64_t next_u64() {
         uint64_t result = mix_lea64(s + x0);
@@ -203,6 +244,21 @@ struct GenXoroshiro128PP {
         t += kGamma; x0 = mix64(t);
         t += kGamma; x1 = mix64(t);
         if ((x0 | x1) == 0) x1 = kGamma;
+    }
+    __device__ __forceinline__ void load(const uint64_t* w) {
+        x0 = w[0];
+        x1 = w[1];
+    }
+    __device__ __forceinline__ void save(uint64_t* w) const {
+        w[0] = x0;
+        w[1] = x1;
+    }
+    // one raw step back: undo x1 = rotl(t, 28), then rotl(x0, 49) = x0' ^ t ^ (t << 21),
+    // then t = x1 ^ x0
+    __device__ __forceinline__ void unstep() {
+        const uint64_t t = rotr64(x1, 28);
+        x0 = rotr64(x0 ^ t ^ (t << 21), 49);
+        x1 = t ^ x0;
     }
     __device__ __forceinline__ uint64_t next_u64() {
         const uint64_t s0 = x0;

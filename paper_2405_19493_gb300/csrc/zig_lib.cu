@@ -69,6 +69,7 @@ struct GenArgs {
     uint32_t n_req;              // batched mutation: number of requests
     uint32_t lane_sectors;       // generation: 1 = lane-per-row flush in 32-byte sectors
     unsigned* err;               // where device-side errors are latched (a caller's word or the device's)
+    zig_stream_state* state;     // stream records to continue and advance (chunk_log2 = 0), or NULL
 };
 
 // One mutation request of a batch (device copy; ustart = its first unit).
@@ -77,9 +78,32 @@ struct MutDesc {
     uint64_t P, L, seed, upr, ustart;
     float sigma;
     uint32_t kind;   // ZIG_REQ_MUTATE: x += sigma z; ZIG_REQ_GENERATE: x = z
+    zig_stream_state* state;   // rows continue these records (one unit per row), or NULL
 };
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+// A stream record's generator (false, and the error bit, for a record seeded
+// for another generator).
+template <int PRNG, class G>
+__device__ __forceinline__ bool state_load(const zig_stream_state* r, G& g, unsigned* err, bool& ok) {
+    if (r->prng != (uint32_t)PRNG) {
+        atomicOr(err, kErrStateKind);
+        ok = false;
+        return false;
+    }
+    g.load(r->gen);
+    return true;
+}
+
+// Advance a stream record past its unit: the generator at the stream's next raw
+// draw, and the polar method's pending second variate (none for the others).
+template <class G>
+__device__ __forceinline__ void state_store(zig_stream_state* r, const G& g, bool have, double cached) {
+    g.save(r->gen);
+    r->polar_cached = have ? cached : 0.0;
+    r->polar_have = have ? 1u : 0u;
+}
 
 // Resolve unit u to (stream s, chunk q, output offset, output count).
 __device__ __forceinline__ void unit_info(const GenArgs& a, uint64_t u, uint64_t& s, uint64_t& q,
@@ -116,6 +140,23 @@ __device__ __forceinline__ void unit_info(const GenArgs& a, uint64_t u, uint64_t
 
 __device__ __forceinline__ uint64_t units_total(const GenArgs& a) {
     return a.lengths ? a.totals[0] : a.n_units;
+}
+
+// The generator of unit (stream s, chunk q): seeded from seeds[s] and moved to
+// chunk q, or continued from the stream's record a.state[s] (calls with records
+// have one unit per stream).  Returns the record to advance at the unit's end
+// (NULL without records); ok = false for a record of another generator, whose
+// stream then gets no outputs.
+template <int PRNG, class G>
+__device__ __forceinline__ zig_stream_state* unit_gen(const GenArgs& a, uint64_t s, uint64_t q, G& g, bool& ok) {
+    ok = true;
+    if (a.state == nullptr) {
+        g.seed(a.seeds[s]);
+        if (q) g.jump(q * kChunkDraws, &d_jump);
+        return nullptr;
+    }
+    zig_stream_state* r = a.state + s;
+    return state_load<PRNG>(r, g, a.err, ok) ? r : nullptr;
 }
 
 // ---------------------------------------------------------------------------
@@ -331,18 +372,25 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
         OutT* dst = out;
         G g;
         g.seed(0);
+        zig_stream_state* srec = nullptr;
+        bool have = false;   // polar: the second variate of the last pair is pending
+        double cached = 0.0;
         if (u < n_units) {
             uint64_t s, q, off, n;
             unit_info(a, u, s, q, off, n);
-            g.seed(a.seeds[s]);
-            if (q) g.jump(q * kChunkDraws, &d_jump);
-            rem = n;
-            dst = out + off;
+            bool ok;
+            srec = unit_gen<PRNG>(a, s, q, g, ok);
+            if (ok) {
+                rem = n;
+                dst = out + off;
+            }
+            if (ALG == ZIG_POLAR && srec && srec->polar_have) {
+                have = true;
+                cached = srec->polar_cached;
+            }
         }
         const uint64_t n_unit = rem;
         uint32_t extra = 0;
-        bool have = false;
-        double cached = 0.0;
         while (__any_sync(kFull, rem > 0)) {
             const int cnt = (int)umin64(rem, (uint64_t)kStageCols);
 #pragma unroll 1
@@ -370,6 +418,8 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
             uint64_t draws = (ALG == ZIG_POLAR) ? (uint64_t)extra : n_unit * per + extra;
             if (draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
         }
+        // a lane draws only for its own outputs, so g stands at the stream's next draw
+        if (srec && n_unit) state_store(srec, g, ALG == ZIG_POLAR && have, cached);
     }
 }
 
@@ -877,7 +927,9 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
         g.seed(0);
         float sigma = a.sigma;
         uint32_t kind = ZIG_REQ_MUTATE;
+        zig_stream_state* srec = nullptr;   // the record to advance at the unit's end
         if (u < n_units) {
+            bool ok = true;
             if constexpr (MODE == 2) {
                 // batched mutation: the request holding unit u (the last with ustart <= u)
                 uint32_t lo = 0, hi = a.n_req;
@@ -887,25 +939,38 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
                 }
                 const MutDesc& r = a.reqs[lo];
                 const uint64_t ur = u - r.ustart, p = ur / r.upr, qd = ur - p * r.upr;
-                g.seed(r.seed + p);
-                if (qd) g.jump(qd * kChunkDraws, &d_jump);
+                if (r.state) {   // one unit per row, continuing its record
+                    if (state_load<PRNG>(r.state + p, g, a.err, ok)) srec = r.state + p;
+                } else {
+                    g.seed(r.seed + p);
+                    if (qd) g.jump(qd * kChunkDraws, &d_jump);
+                }
                 const uint64_t t0 = qd << 10;
-                rem = umin64(r.L - t0, 1024);
-                dst = (OutT*)(r.x + p * r.L + t0);
+                if (ok) {
+                    rem = r.state ? r.L : umin64(r.L - t0, 1024);
+                    dst = (OutT*)(r.x + p * r.L + t0);
+                }
                 sigma = r.sigma;
                 kind = r.kind;
             } else {
                 uint64_t s, qd, off, n;
                 unit_info(a, u, s, qd, off, n);
-                g.seed(MODE == 0 ? a.seeds[s] : a.mut_seed + s);   // mutation: seed + row
-                if (qd) g.jump(qd * kChunkDraws, &d_jump);
-                rem = n;
-                dst = out + off;
+                if (a.state) {
+                    srec = unit_gen<PRNG>(a, s, 0, g, ok);
+                } else {
+                    g.seed(MODE == 0 ? a.seeds[s] : a.mut_seed + s);   // mutation: seed + row
+                    if (qd) g.jump(qd * kChunkDraws, &d_jump);
+                }
+                if (ok) {
+                    rem = n;
+                    dst = out + off;
+                }
             }
         }
         uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
         int nc = 0;           // values carried to the next batch (lane-per-row flush)
-        const bool check_chunk = (MODE == 2 || a.chunk_log2 != 0) && rem != 0;
+        const bool check_chunk = srec == nullptr && (MODE == 2 || a.chunk_log2 != 0) && rem != 0;
+        const bool any_out = rem != 0;
 
         while (__any_sync(kFull, rem > 0)) {
             ws.rej[lane] = 0;
@@ -1124,6 +1189,9 @@ __global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
             __syncwarp();
         }
         if (check_chunk && draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
+        // every draw of a lane is one of its candidates or their uniforms, so g
+        // stands at the stream's next draw
+        if (srec && any_out) state_store(srec, g, false, 0.0);
     }
 }
 
@@ -1183,15 +1251,19 @@ __global__ void __launch_bounds__(kZBlock, 1) z256_kernel(GenArgs a) {
         double* dst = out;
         G g;
         g.seed(0);
+        zig_stream_state* srec = nullptr;
         if (u < n_units) {
             uint64_t s, q, off, n;
             unit_info(a, u, s, q, off, n);
-            g.seed(a.seeds[s]);
-            if (q) g.jump(q * kChunkDraws, &d_jump);
-            rem = n;
-            dst = out + off;
+            bool ok;
+            srec = unit_gen<PRNG>(a, s, q, g, ok);
+            if (ok) {
+                rem = n;
+                dst = out + off;
+            }
         }
         const bool check_chunk = a.chunk_log2 != 0 && rem != 0;
+        const bool any_out = rem != 0;
         uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
         int nc = 0;           // values carried to the next batch
         while (__any_sync(kFull, rem > 0)) {
@@ -1234,6 +1306,8 @@ __global__ void __launch_bounds__(kZBlock, 1) z256_kernel(GenArgs a) {
             z128_flush_f64<B>(row, 0u, slot, slot, rem == 0, dst, nc);
         }
         if (check_chunk && draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
+        // a lane draws only while it needs values, so g stands at the stream's next draw
+        if (srec && any_out) state_store(srec, g, false, 0.0);
     }
 }
 
@@ -1317,6 +1391,22 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint64_t* lengths, uin
         totals[1] = sl[1023];
         if (over) atomicOr(err, kErrLengthSum);
     }
+}
+
+// Stream records seeded as the stateless calls seed their streams.
+template <int PRNG>
+__global__ void state_init_kernel(const uint64_t* seeds, uint64_t n, zig_stream_state* st) {
+    const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    typename GenOf<PRNG>::T g;
+    g.seed(seeds[s]);
+    zig_stream_state r;
+    r.gen[0] = r.gen[1] = r.gen[2] = r.gen[3] = 0;
+    g.save(r.gen);
+    r.polar_cached = 0.0;
+    r.polar_have = 0;
+    r.prng = PRNG;
+    st[s] = r;
 }
 
 // Raw draws for generator parity checks.
@@ -1766,19 +1856,23 @@ size_t zig_generate_workspace_bytes(uint64_t n_streams) {
 
 namespace zig {
 namespace host {
+// Stateless calls seed stream s from seeds_dev[s]; calls with records (state
+// non-NULL, seeds_dev NULL, chunk_log2 0) continue and advance state[s].
 static zig_status generate_impl(zig_prng prng, zig_alg alg, const uint64_t* seeds_dev,
                                 const uint64_t* lengths_dev, uint64_t uniform_len, uint64_t n_streams,
                                 uint32_t chunk_log2, zig_dtype dtype, void* out_dev, void* workspace_dev,
                                 size_t workspace_bytes, unsigned* status_dev, void* stream,
-                                const LaunchCfg* force) {
+                                const LaunchCfg* force, zig_stream_state* state = nullptr) {
     if ((unsigned)prng > 3u || (unsigned)alg > 2u || (unsigned)dtype > 2u) return ZIG_ERR_INVALID_ARG;
     if (chunk_log2 != 0 && (chunk_log2 < 4 || chunk_log2 > 24)) return ZIG_ERR_INVALID_ARG;
+    if (state && chunk_log2 != 0) return ZIG_ERR_INVALID_ARG;
     if (n_streams == 0) return ZIG_OK;
     // out_dev may be NULL only with lengths_dev (an all-zero batch); the kernel
     // latches ZIG_ERR_INVALID_ARG in the error word if the lengths sum above zero
-    if (!seeds_dev || (!out_dev && !lengths_dev)) return ZIG_ERR_INVALID_ARG;
+    if ((!seeds_dev && !state) || (!out_dev && !lengths_dev)) return ZIG_ERR_INVALID_ARG;
     const size_t esz = dtype == ZIG_F64 ? 8 : dtype == ZIG_F32 ? 4 : 2;
-    if (((uintptr_t)out_dev) % esz || ((uintptr_t)seeds_dev) % 8) return ZIG_ERR_INVALID_ARG;
+    if (((uintptr_t)out_dev) % esz || ((uintptr_t)seeds_dev) % 8 || ((uintptr_t)state) % 16)
+        return ZIG_ERR_INVALID_ARG;
     if (lengths_dev == nullptr) {
         if (uniform_len == 0) return ZIG_OK;
         if (uniform_len >= (1ull << 40) || n_streams > ((1ull << 40) - 1) / uniform_len)
@@ -1796,6 +1890,7 @@ static zig_status generate_impl(zig_prng prng, zig_alg alg, const uint64_t* seed
 
     GenArgs a{};
     a.seeds = seeds_dev;
+    a.state = state;
     a.lengths = lengths_dev;
     a.uniform_len = uniform_len;
     a.n_streams = n_streams;
@@ -1856,6 +1951,36 @@ zig_status zig_generate_checked(zig_prng prng, zig_alg alg, const uint64_t* seed
     return host::generate_impl(prng, alg, seeds_dev, lengths_dev, uniform_len, n_streams, chunk_log2,
                                dtype, out_dev, workspace_dev, workspace_bytes, (unsigned*)status_dev, stream,
                                nullptr);
+}
+
+zig_status zig_state_init(zig_prng prng, const uint64_t* seeds_dev, uint64_t n_streams,
+                          zig_stream_state* state_dev, void* stream) {
+    if ((unsigned)prng > 3u || n_streams > (1ull << 32)) return ZIG_ERR_INVALID_ARG;
+    if (n_streams == 0) return ZIG_OK;
+    if (!seeds_dev || !state_dev || ((uintptr_t)seeds_dev) % 8 || ((uintptr_t)state_dev) % 16)
+        return ZIG_ERR_INVALID_ARG;
+    int dev;
+    zig_status st = host::current_device(dev);
+    if (st != ZIG_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned grid = (unsigned)((n_streams + 255) / 256);
+    switch (prng) {
+    case ZIG_LCG48: state_init_kernel<0><<<grid, 256, 0, s>>>(seeds_dev, n_streams, state_dev); break;
+    case ZIG_SPLITMIX64: state_init_kernel<1><<<grid, 256, 0, s>>>(seeds_dev, n_streams, state_dev); break;
+    case ZIG_L64X128MIX: state_init_kernel<2><<<grid, 256, 0, s>>>(seeds_dev, n_streams, state_dev); break;
+    default: state_init_kernel<3><<<grid, 256, 0, s>>>(seeds_dev, n_streams, state_dev); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
+}
+
+zig_status zig_generate_state(zig_prng prng, zig_alg alg, zig_stream_state* state_dev,
+                              const uint64_t* lengths_dev, uint64_t uniform_len, uint64_t n_streams,
+                              zig_dtype dtype, void* out_dev, void* workspace_dev, size_t workspace_bytes,
+                              uint32_t* status_dev, void* stream) {
+    if (!state_dev || ((uintptr_t)status_dev) % 4) return ZIG_ERR_INVALID_ARG;
+    return host::generate_impl(prng, alg, nullptr, lengths_dev, uniform_len, n_streams, 0, dtype, out_dev,
+                               workspace_dev, workspace_bytes, (unsigned*)status_dev, stream, nullptr,
+                               state_dev);
 }
 
 zig_status zig_launch_config_get(int device, zig_prng prng, zig_dtype dtype, int variable_lengths,
@@ -1962,28 +2087,36 @@ zig_status zig_autotune(zig_prng prng, const uint64_t* seeds_dev, const uint64_t
     return ZIG_OK;
 }
 
-zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_t seed,
-                      zig_prng prng, void* stream) {
+}  // extern "C"
+
+namespace zig {
+namespace host {
+// x += sigma z on P x L binary32 rows: row p seeded seed + p and chunked at
+// 2^10 outputs, or (state non-NULL) continuing record state[p] unchunked.
+static zig_status mutate_impl(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_t seed,
+                              zig_stream_state* state, zig_prng prng, void* stream) {
     if ((unsigned)prng > 3u || !std::isfinite(sigma)) return ZIG_ERR_INVALID_ARG;
     if (P == 0 || L == 0) return ZIG_OK;
-    if (!x_dev || ((uintptr_t)x_dev) % 4 || L >= (1ull << 40) || P > ((1ull << 40) - 1) / L)
+    if (!x_dev || ((uintptr_t)x_dev) % 4 || L >= (1ull << 40) || P > ((1ull << 40) - 1) / L ||
+        ((uintptr_t)state) % 16)
         return ZIG_ERR_INVALID_ARG;
     int dev;
     zig_status st = host::current_device(dev);
     if (st != ZIG_OK) return st;
-    const uint64_t upr = (L + 1023) >> 10;
+    const uint64_t upr = state ? 1 : (L + 1023) >> 10;
     const uint64_t groups = (P * upr + 31) / 32;
     cudaStream_t s = (cudaStream_t)stream;
     GenArgs a{};
     a.uniform_len = L;          // row length
     a.n_streams = P;
-    a.chunk_log2 = 10;
+    a.chunk_log2 = state ? 0 : 10;
     a.out = x_dev;
     a.units_per_stream = upr;
     a.n_units = P * upr;
     a.sigma = sigma;
     a.seeds = nullptr;
-    // the kernel seeds row p with a.mut_seed + p in mutation mode
+    a.state = state;
+    // without records the kernel seeds row p with a.mut_seed + p in mutation mode
     a.err = host::g_err_ptr[dev];
     GenArgs am = a;
     host::GenFn fn = prng == ZIG_LCG48 ? z128_kernel<0, ZIG_F32, 1>
@@ -1996,6 +2129,21 @@ zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_
     int grid = host::grid_for((const void*)fn, dev, groups, dyn, kZBlock);
     fn<<<grid, kZBlock, dyn, s>>>(am);
     return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
+}
+}  // namespace host
+}  // namespace zig
+
+extern "C" {
+
+zig_status zig_mutate(float* x_dev, float sigma, uint64_t P, uint64_t L, uint64_t seed,
+                      zig_prng prng, void* stream) {
+    return host::mutate_impl(x_dev, sigma, P, L, seed, nullptr, prng, stream);
+}
+
+zig_status zig_mutate_state(float* x_dev, float sigma, uint64_t P, uint64_t L, zig_stream_state* state_dev,
+                            zig_prng prng, void* stream) {
+    if (!state_dev) return ZIG_ERR_INVALID_ARG;
+    return host::mutate_impl(x_dev, sigma, P, L, 0, state_dev, prng, stream);
 }
 
 size_t zig_mutate_batch_desc_bytes(uint32_t n_req) { return (size_t)n_req * sizeof(MutDesc) + 256; }
@@ -2012,7 +2160,7 @@ zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_p
     for (uint32_t r = 0; r < n_req; ++r) {
         const zig_mutation& q = reqs_host[r];
         if (q.kind > ZIG_REQ_GENERATE || (q.kind == ZIG_REQ_MUTATE && !std::isfinite(q.sigma)) ||
-            (q.P && q.L && (!q.x_dev || ((uintptr_t)q.x_dev) % 4)) ||
+            (q.P && q.L && (!q.x_dev || ((uintptr_t)q.x_dev) % 4)) || ((uintptr_t)q.state_dev) % 16 ||
             q.L >= (1ull << 40) || (q.L && q.P > ((1ull << 40) - 1) / q.L))
             return ZIG_ERR_INVALID_ARG;
         d[r].x = q.x_dev;
@@ -2020,7 +2168,8 @@ zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_p
         d[r].L = q.L;
         d[r].seed = q.seed;
         d[r].sigma = q.sigma;
-        d[r].upr = q.L ? (q.L + 1023) >> 10 : 1;
+        d[r].state = q.state_dev;
+        d[r].upr = (q.L && !q.state_dev) ? (q.L + 1023) >> 10 : 1;
         d[r].ustart = units;
         d[r].kind = q.kind;
         units += (q.P && q.L) ? q.P * d[r].upr : 0;
@@ -2092,7 +2241,7 @@ zig_status zig_device_status(int device, int clear) {
 }
 
 zig_status zig_status_decode(uint32_t word) {
-    if (word & (kErrNullOutput | kErrLengthSum)) return ZIG_ERR_INVALID_ARG;
+    if (word & (kErrNullOutput | kErrLengthSum | kErrStateKind)) return ZIG_ERR_INVALID_ARG;
     if (word & kErrChunkOverflow) return ZIG_ERR_CHUNK_OVERFLOW;
     return ZIG_OK;
 }

@@ -10,6 +10,9 @@
 // others are on the GPU join the next launch on another slot, so work from
 // different batches overlaps on the device.  Each request's result is exactly
 // what zig_mutate computes for it alone (seeds and chunking are per request).
+// A population keeps one stream record per row on the device, so that its
+// requests continue the rows' streams (zig_mutate_state); requests on one
+// population run one at a time, in submission order.
 //
 // device < 0 selects a dry run: no CUDA call is made and a launch "completes"
 // after a simulated time proportional to its bytes, which lets the admission
@@ -43,6 +46,16 @@ struct Req {
     double t_submit, t_launch, t_done;
     int state;
     zig_status status;
+    int64_t pop;   // the population whose streams the request continues, or -1
+};
+
+// A population: P stream records on the device (none in a dry run).
+struct Pop {
+    zig_stream_state* state = nullptr;
+    uint64_t P = 0;
+    uint64_t pending = 0;   // its requests queued or running
+    bool busy = false;      // one of its requests is in flight
+    bool released = false;
 };
 
 struct Slot {
@@ -69,6 +82,7 @@ struct zig_server {
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
     std::vector<Req> reqs;
+    std::vector<Pop> pops;
     std::vector<Slot> slots;
     uint64_t inflight_bytes = 0, peak_inflight_bytes = 0;
     uint64_t batches = 0, batched_requests = 0;
@@ -100,6 +114,10 @@ void retire(zig_server* S) {
             r.state = S->worker_error == ZIG_OK ? kDone : kFailed;
             r.status = S->worker_error;
             r.t_done = t;
+            if (r.pop >= 0) {
+                S->pops[r.pop].busy = false;
+                S->pops[r.pop].pending -= 1;
+            }
         }
         S->inflight_bytes -= sl.bytes;
         sl.busy = false;
@@ -117,7 +135,9 @@ bool form_batch(zig_server* S, Slot& sl) {
         const uint64_t k = S->queue.front();
         Req& r = S->reqs[k];
         if (S->inflight_bytes + sl.bytes + r.bytes > S->budget) break;   // wait for memory
+        if (r.pop >= 0 && S->pops[r.pop].busy) break;   // its population's previous request first
         S->queue.pop_front();
+        if (r.pop >= 0) S->pops[r.pop].busy = true;
         sl.tickets.push_back(k);
         sl.batch.push_back(r.m);
         sl.bytes += r.bytes;
@@ -223,16 +243,24 @@ zig_status zig_server_create(int device, zig_prng prng, uint64_t budget_bytes, u
 }  // extern "C"
 
 namespace {
+// pop < 0: rows seeded seed + p; else rows continue population pop's records.
 zig_status submit(zig_server* S, float* x_dev, uint64_t P, uint64_t L, float sigma, uint32_t kind,
-                  uint64_t seed, uint64_t* ticket) {
-    if (!S || !ticket || (kind == ZIG_REQ_MUTATE && !std::isfinite(sigma)) || (P && L && !x_dev) ||
-        (L && P > ((1ull << 40) - 1) / L))
+                  uint64_t seed, int64_t pop, uint64_t* ticket) {
+    if (!S || !ticket || kind > ZIG_REQ_GENERATE || (kind == ZIG_REQ_MUTATE && !std::isfinite(sigma)))
         return ZIG_ERR_INVALID_ARG;
-    const uint64_t bytes = P * L * sizeof(float);
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stop) return ZIG_ERR_INVALID_ARG;
+    zig_stream_state* state = nullptr;
+    if (pop >= 0) {
+        if ((uint64_t)pop >= S->pops.size() || S->pops[pop].released) return ZIG_ERR_INVALID_ARG;
+        P = S->pops[pop].P;
+        state = S->pops[pop].state;
+    }
+    if ((P && L && !x_dev) || (L && P > ((1ull << 40) - 1) / L)) return ZIG_ERR_INVALID_ARG;
+    const uint64_t bytes = P * L * sizeof(float);
     Req r;
-    r.m = zig_mutation{x_dev, P, L, sigma, kind, seed};
+    r.m = zig_mutation{x_dev, P, L, sigma, kind, seed, state};
+    r.pop = pop;
     r.bytes = bytes;
     r.t_submit = now_us();
     r.t_launch = r.t_done = 0;
@@ -248,6 +276,7 @@ zig_status submit(zig_server* S, float* x_dev, uint64_t P, uint64_t L, float sig
     }
     S->reqs.push_back(r);
     S->queue.push_back(*ticket);
+    if (pop >= 0) S->pops[pop].pending += 1;
     S->cv_work.notify_one();
     return ZIG_OK;
 }
@@ -257,12 +286,64 @@ extern "C" {
 
 zig_status zig_server_submit(zig_server* S, float* x_dev, uint64_t P, uint64_t L, float sigma,
                              uint64_t seed, uint64_t* ticket) {
-    return submit(S, x_dev, P, L, sigma, ZIG_REQ_MUTATE, seed, ticket);
+    return submit(S, x_dev, P, L, sigma, ZIG_REQ_MUTATE, seed, -1, ticket);
 }
 
 zig_status zig_server_submit_generate(zig_server* S, float* out_dev, uint64_t P, uint64_t L,
                                       uint64_t seed, uint64_t* ticket) {
-    return submit(S, out_dev, P, L, 0.0f, ZIG_REQ_GENERATE, seed, ticket);
+    return submit(S, out_dev, P, L, 0.0f, ZIG_REQ_GENERATE, seed, -1, ticket);
+}
+
+zig_status zig_server_population(zig_server* S, uint64_t P, uint64_t seed, uint64_t* population) {
+    if (!S || !population || P == 0 || P > (1ull << 32)) return ZIG_ERR_INVALID_ARG;
+    Pop pp;
+    pp.P = P;
+    if (!S->dry) {
+        // the records are seeded on the legacy stream and complete before this call
+        // returns, so the service's streams see them initialized
+        if (cudaSetDevice(S->device) != cudaSuccess) return ZIG_ERR_CUDA;
+        std::vector<uint64_t> seeds(P);
+        for (uint64_t p = 0; p < P; ++p) seeds[p] = seed + p;
+        uint64_t* seeds_dev = nullptr;
+        if (cudaMalloc(&pp.state, P * sizeof(zig_stream_state)) != cudaSuccess) return ZIG_ERR_CUDA;
+        zig_status st = ZIG_OK;
+        if (cudaMalloc(&seeds_dev, P * sizeof(uint64_t)) != cudaSuccess ||
+            cudaMemcpy(seeds_dev, seeds.data(), P * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess)
+            st = ZIG_ERR_CUDA;
+        if (st == ZIG_OK) st = zig_state_init(S->prng, seeds_dev, P, pp.state, nullptr);
+        if (st == ZIG_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) st = ZIG_ERR_CUDA;
+        if (seeds_dev) cudaFree(seeds_dev);
+        if (st != ZIG_OK) {
+            cudaFree(pp.state);
+            return st;
+        }
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    *population = S->pops.size();
+    S->pops.push_back(pp);
+    return ZIG_OK;
+}
+
+zig_status zig_server_submit_population(zig_server* S, uint64_t population, float* x_dev, uint64_t L,
+                                        float sigma, uint32_t kind, uint64_t* ticket) {
+    if (!S || population >= (1ull << 62)) return ZIG_ERR_INVALID_ARG;
+    return submit(S, x_dev, 0, L, sigma, kind, 0, (int64_t)population, ticket);
+}
+
+zig_status zig_server_population_release(zig_server* S, uint64_t population) {
+    if (!S) return ZIG_ERR_INVALID_ARG;
+    zig_stream_state* state = nullptr;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (population >= S->pops.size() || S->pops[population].released) return ZIG_ERR_INVALID_ARG;
+        S->cv_work.notify_one();
+        S->cv_done.wait(lk, [&] { return S->pops[population].pending == 0; });
+        S->pops[population].released = true;
+        state = S->pops[population].state;
+        S->pops[population].state = nullptr;
+    }
+    if (state && cudaFree(state) != cudaSuccess) return ZIG_ERR_CUDA;
+    return ZIG_OK;
 }
 
 zig_status zig_server_wait(zig_server* S, uint64_t ticket, double timeout_s) {
@@ -349,6 +430,8 @@ zig_status zig_server_destroy(zig_server* S) {
             cudaEventDestroy(sl.done);
             cudaStreamDestroy(sl.stream);
         }
+        for (Pop& pp : S->pops)
+            if (pp.state) cudaFree(pp.state);
     }
     delete S;
     return st;

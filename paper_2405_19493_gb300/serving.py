@@ -60,6 +60,33 @@ class MutationServer:
             self._keep[t.value] = out
         return t.value
 
+    def population(self, P: int, seed: int) -> int:
+        """A population of P rows whose streams (seeded seed + p) the service keeps on the device."""
+        h = C.c_uint64()
+        B._check(self._lib.zig_server_population(self._h, int(P), int(seed) & (2 ** 64 - 1), C.byref(h)),
+                 "zig_server_population")
+        return h.value
+
+    def submit_population(self, population: int, x, sigma: float = 0.0, kind: str = "mutate",
+                          L: int | None = None, x_ptr: int | None = None) -> int:
+        """Enqueue a request whose rows continue the population's streams (x: P x L float32)."""
+        if x is not None:
+            L = x.shape[1] if x.dim() == 2 else x.numel()
+            ptr = x.data_ptr() or None
+        else:
+            ptr = x_ptr
+        t = C.c_uint64()
+        st = self._lib.zig_server_submit_population(self._h, int(population), ptr, int(L), float(sigma),
+                                                    B.REQ_KIND[kind], C.byref(t))
+        B._check(st, "zig_server_submit_population")
+        if x is not None:
+            self._keep[t.value] = x
+        return t.value
+
+    def release_population(self, population: int) -> None:
+        B._check(self._lib.zig_server_population_release(self._h, int(population)),
+                 "zig_server_population_release")
+
     def wait(self, ticket: int, timeout_s: float = -1.0) -> None:
         st = self._lib.zig_server_wait(self._h, ticket, float(timeout_s))
         self._keep.pop(ticket, None)

@@ -158,7 +158,7 @@ def test_more_host_side_argument_errors():
 def test_status_decode_and_table_sizes():
     """Error words decode to statuses; zig_tables_get reports sizes and refuses bad calls."""
     import ctypes as C
-    for word, want in ((0, 0), (1, 6), (4, 1), (8, 1), (4 | 1, 1), (8 | 1, 1)):
+    for word, want in ((0, 0), (1, 6), (4, 1), (8, 1), (16, 1), (4 | 1, 1), (8 | 1, 1), (16 | 1, 1)):
         assert Z.zig_status_decode(word) == want
     lib = Z.load()
     n = C.c_size_t(0)
@@ -170,3 +170,16 @@ def test_status_decode_and_table_sizes():
     assert lib.zig_tables_get(0, buf, C.byref(small)) == 1
     assert lib.zig_tables_get(3, None, C.byref(n)) == 1
     assert lib.zig_tables_get(0, None, None) == 1
+
+
+def test_stream_state_record_layout():
+    import ctypes as C
+    assert C.sizeof(B.StreamState) == B.STATE_BYTES == 48
+    assert B.StreamState.polar_cached.offset == 32 and B.StreamState.prng.offset == 44
+    assert C.sizeof(B.Mutation) == 48 and B.Mutation.state_dev.offset == 40
+    lib = Z.load()
+    # argument errors return before any device work
+    assert lib.zig_state_init(9, None, 1, None, None) == 1
+    assert lib.zig_generate_state(0, 0, None, None, 4, 4, 0, None, None, 0, None, None) == 1
+    assert lib.zig_mutate_state(None, 0.5, 4, 4, None, 0, None) == 1
+    assert lib.zig_generate_state(0, 0, 8, None, 4, 4, 0, 64, None, 0, None, None) == 1   # misaligned records

@@ -86,3 +86,42 @@ def test_dry_run_generate_and_mutate_share_queue_and_budget():
         assert st["elements"] == 12 * 32 * 32768
         assert st["peak_inflight_bytes"] <= budget
         assert all(srv.query(k)["state"] == 2 for k in t)
+
+
+def test_dry_run_population_requests_run_one_at_a_time_in_order():
+    # requests on one population continue its streams, so they may never share a
+    # launch or overlap; requests on other populations still batch
+    # 2 GiB requests: a dry launch lasts about 2 ms
+    with MutationServer(device=-1, budget_bytes=16 << 30, n_slots=4, max_batch=16) as srv:
+        a = srv.population(P=512, seed=1)
+        b = srv.population(P=512, seed=2)
+        ta = [srv.submit_population(a, None, 0.5, L=1 << 20, x_ptr=FAKE) for _ in range(5)]
+        tb = [srv.submit_population(b, None, 0.5, L=1 << 20, x_ptr=FAKE) for _ in range(5)]
+        srv.drain(timeout_s=30)
+        st = srv.stats()
+        assert st["completed"] == 10 and st["failed"] == 0
+        assert st["batches"] >= 5                                      # a's five never share one
+        for ts in (ta, tb):
+            q = [srv.query(t) for t in ts]
+            assert all(x["state"] == 2 for x in q)
+            # times are from each request's own submission, and the requests were
+            # submitted back to back (microseconds apart; 1 ms of slack, half a launch, for
+            # a descheduled submitting thread): each launched after its predecessor finished
+            done = [x["latency_us"] for x in q]
+            starts = [x["queue_us"] for x in q]
+            for k in range(1, len(ts)):
+                assert starts[k] >= done[k - 1] - 1000.0
+        srv.release_population(a)
+        with pytest.raises(B.ZigError):
+            srv.submit_population(a, None, 0.5, L=16, x_ptr=FAKE)    # released
+        with pytest.raises(B.ZigError):
+            srv.submit_population(99, None, 0.5, L=16, x_ptr=FAKE)   # no such population
+        srv.release_population(b)
+
+
+def test_dry_run_population_release_waits_for_its_requests():
+    with MutationServer(device=-1, budget_bytes=8 << 30, n_slots=2, max_batch=4) as srv:
+        a = srv.population(P=4096, seed=7)
+        ts = [srv.submit_population(a, None, 0.1, L=131072, x_ptr=FAKE) for _ in range(3)]
+        srv.release_population(a)             # returns once all three have run
+        assert all(srv.query(t)["state"] == 2 for t in ts)
