@@ -514,16 +514,19 @@ const char *zig_status_string(zig_status status);
 
 /*
  * zig_selfcheck -- exhaustive check of the fast path's arithmetic on the current
- * device (test support; the paper has no counterpart).  Computes RN(j * w[i]) by
- * the kernel's fused multiply-add construction for every abscissa j < 2^24 of
- * every layer i < 128 and compares it with IEEE multiplication (__dmul_rn), and
- * rounds every finite binary32 bit pattern to bfloat16 by the kernel's routine
- * and compares it with __float2bfloat16_rn, and compares the tail step's own
- * binary64 log with CUDA's log on 2^31 uniforms in (0, 1).  Writes
- * counts_host[0] = product mismatches, [1] = bfloat16 mismatches, [2] = products
- * checked (2^31), [3] = patterns checked, [4] = logs more than one ulp from
- * CUDA's, [5] = logs not equal to CUDA's.  Synchronous; allocates 48 bytes of
- * device memory for the call.  ZIG_ERR_NOT_INITIALIZED without zig_tables_init.
+ * device (test support; the paper has no counterpart).  Computes RN(j * w[i])
+ * for every abscissa j < 2^24 of every layer i < 128 by each construction the
+ * kernels use -- the fused multiply-add one, and the binary64 batch kernel's
+ * fused multiply-add and 32-bit integer ones on both signed table entries
+ * (+-2^52 w[i]) -- and compares each with IEEE multiplication (__dmul_rn, negated
+ * for the negative entries); rounds every finite binary32 bit pattern to
+ * bfloat16 by the kernel's routine and compares it with __float2bfloat16_rn; and
+ * compares the tail step's own binary64 log with CUDA's log on 2^31 uniforms in
+ * (0, 1).  Writes counts_host[0] = product mismatches, [1] = bfloat16
+ * mismatches, [2] = products checked (5 * 2^31), [3] = patterns checked, [4] =
+ * logs more than one ulp from CUDA's, [5] = logs not equal to CUDA's.
+ * Synchronous; allocates 48 bytes of device memory for the call.
+ * ZIG_ERR_NOT_INITIALIZED without zig_tables_init.
  */
 zig_status zig_selfcheck(uint64_t counts_host[6]);
 

@@ -127,12 +127,13 @@ __device__ __forceinline__ uint64_t first_state_of(const G& g) {
 
 // ---- shared memory ----
 // The fast table: one 256-byte block per signed layer ix = w & 0xFF (layer
-// ix & 127, positive when bit 7 is set).  Words 0..31: 8 copies of the entry
-// {low, high word of b = 2^52 w[i], eh | sign, K}, one per lane & 7, so that
-// the 8 lanes of a quarter warp reading 16-byte entries of random layers hit
-// distinct banks; words 32..63: 32 copies of K, one per lane.  K = k[i] << 8,
-// so j >= k[i] is w >= K; eh = (E(w[i]) + 30) << 20 is the exponent field of
-// the integer product; sign is bit 31 of the output's high word.  The block
+// ix & 127, positive when bit 7 is set).  Words 0..31: 16 copies of the signed
+// b = +-2^52 w[i] (low word, high word), one per lane & 15, so that the 16 lanes
+// of a half warp reading 8-byte entries of random layers hit distinct banks;
+// words 32..63: 32 copies of K = k[i] << 8, one per lane (j >= k[i] is w >= K).
+// The sign rides on b: the fma below rounds -(j w[i]) exactly as it rounds
+// j w[i] (its zero, for j = 0, takes b's sign by an OR), and the integer
+// product takes it from b's sign bit.  The block
 // stride of 256 bytes makes each address one byte permute of w.
 struct Tab {
     uint32_t blk[256][64];
@@ -178,15 +179,9 @@ __device__ __forceinline__ void tab_load(Tab& t, SlowTab& s) {
         if (wd >= 32) {
             v = K;
         } else {
-            const long long b = __double_as_longlong(__dmul_rn(wi, 0x1p52));   // exact scaling
-            const uint32_t ew = (uint32_t)(__double_as_longlong(wi) >> 52) & 0x7FFu;
-            const uint32_t sign = ix < 128 ? 0x80000000u : 0u;
-            switch (wd & 3) {
-            case 0: v = (uint32_t)b; break;
-            case 1: v = (uint32_t)(b >> 32); break;
-            case 2: v = ((ew + 30u) << 20) | sign; break;
-            default: v = K; break;
-            }
+            const double bd = __dmul_rn(ix < 128 ? -wi : wi, 0x1p52);   // exact scaling, signed
+            const long long b = __double_as_longlong(bd);
+            v = (wd & 1) ? (uint32_t)(b >> 32) : (uint32_t)b;
         }
         t.blk[ix][wd] = v;
     }
@@ -221,19 +216,21 @@ __device__ __forceinline__ uint64_t int_mul_jw(uint32_t j, uint32_t mlo, uint32_
 }
 
 // x = sign RN(j w[i]) for the draw w, as binary64 bits: one binary64 fma
-// fma(1 + j 2^-52, b, -b) with b = 2^52 w[i] (exact before its one rounding;
-// 1 + j 2^-52 is built from j's bits), or (kInt) int_mul_jw.
+// fma(1 + j 2^-52, b, -b) with the signed b = +-2^52 w[i] (exact before its one
+// rounding; 1 + j 2^-52 is built from j's bits), or (kInt) int_mul_jw with the
+// significand, exponent and sign read off b (E(b) = E(w[i]) + 52).
 template <bool kInt>
-__device__ __forceinline__ uint64_t x_of(const unsigned char* tab, uint32_t w, uint32_t copy16) {
-    const uint4 e = *(const uint4*)(tab + __byte_perm(w, copy16, 0x5504));   // block ix, copy
+__device__ __forceinline__ uint64_t x_of(const unsigned char* tab, uint32_t w, uint32_t copy8) {
+    const uint2 e = *(const uint2*)(tab + __byte_perm(w, copy8, 0x5504));   // block ix, copy
     const uint32_t j = w >> 8;
     if constexpr (kInt) {
         const uint32_t mhi = __funnelshift_l(e.x, (e.y & 0xFFFFFu) | 0x100000u, 11);
-        return int_mul_jw(j, e.x << 11, mhi, e.z);
+        const uint32_t eh = (e.y & 0xFFF00000u) - (22u << 20);   // sign | (E(w[i]) + 30) << 20
+        return int_mul_jw(j, e.x << 11, mhi, eh);
     } else {
         const double b = __hiloint2double((int)e.y, (int)e.x);
         const double x = __fma_rn(__hiloint2double(0x3FF00000, (int)j), b, -b);
-        return (uint64_t)__double_as_longlong(x) | ((uint64_t)(e.z & 0x80000000u) << 32);
+        return (uint64_t)__double_as_longlong(x) | ((uint64_t)(e.y & 0x80000000u) << 32);
     }
 }
 
@@ -285,11 +282,11 @@ __device__ __forceinline__ void decide(W& ws, const SlowTab& slow, uint32_t it, 
 // Write row r of the warp's batch: lane c takes slot c.
 template <int PRNG, bool kInt, class W>
 __device__ __forceinline__ void write_row(const W& ws, const unsigned char* tb, int r, int lane, uint32_t lane_bit,
-                                          uint32_t lt_mask, uint32_t copy16) {
+                                          uint32_t lt_mask, uint32_t copy8) {
     using GT = Gen<PRNG>;
     const uint4 inf = ws.info[r];
     const uint32_t w = ws.stage[r * W::RS + GT::SW * lane + GT::SW - 1];
-    const uint64_t v = x_of<kInt>(tb, w, copy16);
+    const uint64_t v = x_of<kInt>(tb, w, copy8);
     const uint32_t e = __popc(~inf.z & lt_mask);
     const uint64_t addr = ((uint64_t)inf.x | (uint64_t)inf.y << 32) + 8ull * e;
     asm volatile(
@@ -334,7 +331,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
     const int n_warps = blockDim.x >> 5;
     W& ws = *(W*)(zf_dsm + head_bytes() + (size_t)wib * warp_bytes<PRNG>());
     uint32_t* const row = ws.stage + lane * W::RS;
-    const uint32_t copy16 = (uint32_t)(lane & 7) << 4;    // this lane's copy of a fast entry
+    const uint32_t copy8 = (uint32_t)(lane & 15) << 3;    // this lane's copy of b
     const uint32_t kcopy = 0x80u + ((uint32_t)lane << 2);  // this lane's copy of K
 
     if (lane == 0) ws.tq_n = 0;
@@ -502,10 +499,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
             // products q = 0..3 of every two steps: the binary64 fma for q < NDF
 #pragma unroll 2
             for (int r = 0; r < 32; r += 4) {
-                write_row<PRNG, (0 >= NDF)>(ws, tb, r + 0, lane, lane_bit, lt_mask, copy16);
-                write_row<PRNG, (1 >= NDF)>(ws, tb, r + 1, lane, lane_bit, lt_mask, copy16);
-                write_row<PRNG, (2 >= NDF)>(ws, tb, r + 2, lane, lane_bit, lt_mask, copy16);
-                write_row<PRNG, (3 >= NDF)>(ws, tb, r + 3, lane, lane_bit, lt_mask, copy16);
+                write_row<PRNG, (0 >= NDF)>(ws, tb, r + 0, lane, lane_bit, lt_mask, copy8);
+                write_row<PRNG, (1 >= NDF)>(ws, tb, r + 1, lane, lane_bit, lt_mask, copy8);
+                write_row<PRNG, (2 >= NDF)>(ws, tb, r + 2, lane, lane_bit, lt_mask, copy8);
+                write_row<PRNG, (3 >= NDF)>(ws, tb, r + 3, lane, lane_bit, lt_mask, copy8);
             }
             // accepted tails join the queue (one per lane per round), evaluated 32 at a time
             uint32_t Lk = L & ~D;

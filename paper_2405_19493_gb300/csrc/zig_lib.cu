@@ -1326,8 +1326,24 @@ __global__ void __launch_bounds__(256) selfcheck_kernel(unsigned long long* coun
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t i = (uint32_t)(k >> 24), j = (uint32_t)k & 0xFFFFFFu;
         const double w = d_z128_W[i];
-        bad_p += __double_as_longlong(mul_j_w(j, __dmul_rn(w, 0x1p52))) != __double_as_longlong(__dmul_rn((double)j, w));
-        ++n_p;
+        const long long want = __double_as_longlong(__dmul_rn((double)j, w));
+        const long long want_neg = want ^ (long long)0x8000000000000000ull;   // RN(-j w) = -RN(j w)
+        bad_p += __double_as_longlong(mul_j_w(j, __dmul_rn(w, 0x1p52))) != want;
+        // the binary64 batch kernel's two constructions, on both signed table entries
+        // (the values its rows compute, from the entries its tables hold)
+        for (uint32_t neg = 0; neg < 2; ++neg) {
+            const long long b = __double_as_longlong(__dmul_rn(neg ? -w : w, 0x1p52));
+            const uint32_t blo = (uint32_t)b, bhi = (uint32_t)(b >> 32);
+            const uint32_t mhi = __funnelshift_l(blo, (bhi & 0xFFFFFu) | 0x100000u, 11);
+            const uint32_t eh = (bhi & 0xFFF00000u) - (22u << 20);
+            const long long vi = (long long)zf::int_mul_jw(j, blo << 11, mhi, eh);
+            const double bd = __longlong_as_double(b);
+            const long long vf = __double_as_longlong(__fma_rn(__hiloint2double(0x3FF00000, (int)j), bd, -bd)) |
+                                 (long long)((uint64_t)(bhi & 0x80000000u) << 32);
+            const long long wnt = neg ? want_neg : want;
+            bad_p += (vi != wnt) + (vf != wnt);
+        }
+        n_p += 5;
         const double u = m53_to_double(((k * 0x9E3779B97F4A7C15ull) >> 11) | 1u);   // in (0, 1)
         const long long dl = __double_as_longlong(zlog(u)) - __double_as_longlong(log(u));
         far_l += dl > 1 || dl < -1;
