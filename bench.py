@@ -194,22 +194,42 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
-def load_traffic_record():
-    """Per-launch DRAM traffic of the dominant kernel from the committed ncu summary,
-    valid only while the kernel sources are unchanged."""
+KERNEL_SOURCES = ("zig_lib.cu", "z128_f64.cuh", "zig_device.cuh", "zig_tables.inc")
+
+
+def kernel_sources_sha256():
     import hashlib
-    rec = os.path.join(ROOT, "profiles", "zig128_f64_bulk_traffic.json")
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2405_19493_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def load_kernel_record(name):
+    """Per-launch counters of a kernel from a committed ncu summary (profiles/<name>.json):
+    DRAM bytes and warp instructions, scaled to the bench's launch.  Valid only while the
+    kernel sources are unchanged since the capture; None otherwise."""
+    rec = os.path.join(ROOT, "profiles", name + ".json")
     if not os.path.exists(rec):
         return None
     with open(rec) as fh:
         d = json.load(fh)
-    h = hashlib.sha256()
-    for f in ("zig_lib.cu", "zig_device.cuh", "zig_tables.inc"):
-        with open(os.path.join(ROOT, "paper_2405_19493_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    if d.get("source_sha256") != h.hexdigest():
+    if d.get("source_sha256") != kernel_sources_sha256():
         return None
     return d
+
+
+def issue_roofline(rec, launch_ms, sm_mhz, n_sms):
+    """Issue-slot roofline: warp instructions per second against 4 per SM per clock (one
+    per scheduler) at the SM clock sampled during the timed region."""
+    if not rec or not sm_mhz or "warp_instructions_per_launch" not in rec:
+        return None
+    achieved = rec["warp_instructions_per_launch"] / (launch_ms / 1e3) / 1e9
+    peak = 4 * n_sms * sm_mhz * 1e6 / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s", "frac": achieved / peak,
+            "warp_instructions_per_launch": rec["warp_instructions_per_launch"],
+            "peak_basis": f"4 issue slots per SM per clock x {n_sms} SMs x {sm_mhz:.0f} MHz (median under load)"}
 
 
 def run_gpu(args):
@@ -273,11 +293,14 @@ def run_gpu(args):
     alg_bytes = N_STREAMS * PER_STREAM * BYTES_F64 + N_STREAMS * 8
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9
-    traffic = load_traffic_record()
+    rec = load_kernel_record(f"z128f_f64_{dom}_record")
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clk["sm_mhz"] if clk else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
-                "kernel": f"z128_kernel<{dom}, f64>", "peak_source": f"{peak_src} copy bandwidth",
-                "algorithmic_bytes_per_launch": alg_bytes}
+                "frac": achieved / peak, "traffic": rec["dram_bytes_per_launch"] if rec else None,
+                "kernel": f"z128f_kernel<{dom}, f64>", "peak_source": f"{peak_src} copy bandwidth",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "issue": issue_roofline(rec, dom_ms, sm_mhz, n_sms)}
     all_ms = sorted(x for p in PRNGS for x in per_launch[p])
     line_extra = {
         "per_prng": {p: {"variates_per_s": N_STREAMS * PER_STREAM / (statistics.mean(per_launch[p]) / 1e3),
@@ -301,6 +324,19 @@ def run_gpu(args):
 
     # comparisons on the same seeds: other transforms and narrower outputs (rank 0 reports)
     line_extra["comparisons"] = compare_variants(Z, torch, seeds, stream, args)
+    # binary32 output: its own HBM and issue-slot rooflines (the bulk launch of splitmix64)
+    f32 = line_extra["comparisons"]["zig128/splitmix64/f32"]
+    f32_bytes = N_STREAMS * PER_STREAM * 4 + N_STREAMS * 8
+    f32_hbm = f32_bytes / (f32["ms_mean"] / 1e3) / 1e9
+    rec32 = load_kernel_record("z128_f32_splitmix64_record")
+    line_extra["roofline_f32"] = {
+        "kernel": "z128_kernel<splitmix64, f32>", "bound": "alu",
+        "hbm": {"achieved": f32_hbm, "peak": peak, "unit": "GB/s", "frac": f32_hbm / peak,
+                "algorithmic_bytes_per_launch": f32_bytes,
+                "traffic": rec32["dram_bytes_per_launch"] if rec32 else None},
+        "issue": issue_roofline(rec32, f32["ms_mean"], sm_mhz, n_sms),
+        "instructions_per_variate": (rec32["warp_instructions_per_launch"] * 32 / (N_STREAMS * PER_STREAM)
+                                     if rec32 else None)}
     if rank == 0 and not args.no_precision:
         line_extra["precision"] = measure_precision(Z, torch, stream)
         line_extra["lcg_low_bits"] = measure_lcg_low_bits(Z, torch, stream)

@@ -10,15 +10,15 @@
 //     comparison) only sets a bit of the lane's mask nf.  A slot holds the
 //     32-bit draw w, or for the generators whose draws are nextLong outputs the
 //     whole output (a wedge or tail test may read it as its uniform).
-//  B. Each lane walks its nf bits in draw order.  A slow candidate at draw p
-//     (j >= k[i]) consumes the next kU (wedge, i < 127) or 2 kU (tail) draws as
-//     its uniforms; a consumed draw is not a candidate, whatever its bit says.
-//     A lane whose last slow candidate needs draws past the batch takes them
-//     now.  The warp lists its slow candidates and decides them 32 at a time,
-//     the wedge and tail tests first in binary32 with proven margins.  A
-//     rejected candidate and every consumed draw are dropped.  An accepted
-//     tail's value, R - ln(U1)/R in binary64, is not computed here: its U1 and
-//     output address join a per-warp queue that is evaluated 32 at a time.
+//  B. Each lane walks its nf bits in draw order and decides its own slow
+//     candidates (about 0.36 per lane and batch, so the warp's loop runs about
+//     twice).  A slow candidate at draw p (j >= k[i]) consumes the next kU
+//     (wedge, i < 127) or 2 kU (tail) draws as its uniforms; a consumed draw is
+//     not a candidate, whatever its bit says.  Uniforms past the batch are drawn
+//     at once.  The wedge and tail tests run first in binary32 with proven
+//     margins.  A rejected candidate and every consumed draw are dropped.  An
+//     accepted tail's value, R - ln(U1)/R in binary64, is not computed here: its
+//     U1 and output address join a per-warp queue that is evaluated 32 at a time.
 //  C. The warp writes its rows one at a time, all 32 lanes on one row, lane c
 //     on slot c: a kept slot's output index is the number of kept slots below
 //     it, so one store instruction writes the row's batch as one contiguous
@@ -143,7 +143,10 @@ struct SlowTab {   // the wedge test's tables (z128_wedge_accept)
     double Wd[128], Y[128];
 };
 
-constexpr int kMaxThreads = 640;   // 20 warps: the register budget is 65536 / 640 = 102
+// Threads per block for a generator (the register budget is 65536 / threads:
+// 102 at 640); kMaxThreads bounds them all.
+__host__ __device__ constexpr int max_threads(int prng) { return prng >= 0 ? 640 : 640; }
+constexpr int kMaxThreads = 640;
 
 template <int PRNG>
 struct Warp {
@@ -151,11 +154,7 @@ struct Warp {
     static constexpr int B = 32 - 2 * kU;                  // draws per batch
     static constexpr int RS = SW == 1 ? 33 : 66;            // row stride in words
     uint32_t stage[32 * RS];   // row r, slot d: words r RS + SW d ..
-    uint4 info[32];            // per row: output address (low, high), dropped slots, accepted tails
-    uint64_t s0[32];           // per row: the state before the batch's first draw (SplitMix64)
-    uint32_t drop[32];         // per row: candidates rejected in the decision pass
-    uint32_t lit[32];          // per row: accepted tails
-    uint32_t list[64];         // slow candidates: row | draw << 5 | tail << 10
+    uint4 info[32];            // per row: output address (low, high), dropped slots
     uint64_t tq_addr[64];      // accepted tails waiting for their value: output address | negative
     uint64_t tq_m1[64];        // and their uniform m1 (U1 = 1 - m1 2^-53)
     uint32_t tq_n;
@@ -234,51 +233,6 @@ __device__ __forceinline__ uint64_t x_of(const unsigned char* tab, uint32_t w, u
     }
 }
 
-// Decide listed slow candidate `it` (row | draw << 5 | tail << 10), for the
-// lanes with has set (all 32 lanes call this): a rejected candidate is marked
-// in drop[row]; an accepted tail's m1 goes to the words of its first uniform
-// (the next slot, or two for 4-byte slots) and its slot is marked in lit[row].
-// The binary64 wedge test and the tail test run only when some lane needs them.
-template <int PRNG, class W>
-__device__ __forceinline__ void decide(W& ws, const SlowTab& slow, uint32_t it, bool has) {
-    using GT = Gen<PRNG>;
-    const int o = (int)(it & 31u), p = (int)((it >> 5) & 31u);
-    uint32_t* st = ws.stage + o * W::RS;
-    const bool wedge = has && !(it >> 10), tail = has && (it >> 10);
-    uint32_t w = 0;
-    uint64_t m1 = 0;
-    if (has) {
-        w = st[GT::SW * p + GT::SW - 1];
-        m1 = GT::m53(st, p + 1, ws.s0[o]);
-    }
-    int f = 1;
-    if (wedge) f = z128_wedge_filter(slow, w & 0x7Fu, w >> 8, m1);
-    if (__any_sync(kFull, f < 0)) {
-        if (f < 0) f = z128_wedge_exact(slow, w & 0x7Fu, w >> 8, m1) ? 1 : 0;
-    }
-    if (wedge && f == 0) atomicOr(&ws.drop[o], 1u << p);
-    if (__any_sync(kFull, tail)) {
-        uint64_t m2 = 0;
-        int ft = 1;
-        if (tail) {
-            m2 = GT::m53(st, p + 1 + GT::kU, ws.s0[o]);
-            ft = z128_tail_filter(m1, m2);
-        }
-        if (__any_sync(kFull, ft < 0)) {
-            if (ft < 0) ft = z128_tail_exact(m1, m2) ? 1 : 0;
-        }
-        if (tail) {
-            if (ft == 0) {
-                atomicOr(&ws.drop[o], 1u << p);
-            } else {   // m1 goes to the uniforms' words (dropped slots) for the value pass
-                st[GT::SW * (p + 1)] = (uint32_t)m1;
-                st[GT::SW * (p + 1) + 1] = (uint32_t)(m1 >> 32);
-                atomicOr(&ws.lit[o], 1u << p);
-            }
-        }
-    }
-}
-
 // Write row r of the warp's batch: lane c takes slot c.
 template <int PRNG, bool kInt, class W>
 __device__ __forceinline__ void write_row(const W& ws, const unsigned char* tb, int r, int lane, uint32_t lane_bit,
@@ -312,7 +266,7 @@ __device__ __forceinline__ void drain_tails(W& ws, int lane) {
 }
 
 template <int PRNG, int NDF>
-__global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
+__global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) {
     using GT = Gen<PRNG>;
     using G = typename GT::G;
     using W = Warp<PRNG>;
@@ -365,12 +319,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
         }
         const bool check_chunk = a.chunk_log2 != 0 && rem != 0;
         uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
-        ws.drop[lane] = 0;
-        ws.lit[lane] = 0;
 
         while (__any_sync(kFull, rem > 0)) {
             // ---- A: B draws per lane, lockstep; nf marks the slow candidates ----
-            if constexpr (PRNG == ZIG_SPLITMIX64) ws.s0[lane] = GT::first_state(g);
             uint32_t nf = 0;
             const uint64_t sb = first_state_of(g);
             auto step = [&](auto dc) {
@@ -387,84 +338,49 @@ __global__ void __launch_bounds__(kMaxThreads, 1) z128f_kernel(GenArgs a) {
             };
             unroll<B>(step);
             if constexpr (PRNG == ZIG_LCG48) GT::template skip<B>(g);
-            // ---- B: the slow candidates, in draw order; list, then decide ----
-            // Each lane walks its nf bits once: a bit not consumed by an earlier
-            // slow candidate is one (R; tails also in T), and consumes the next kU
-            // or 2 kU draws (du).  Draws past the batch for the last one are taken now.
-            uint32_t R = 0, T = 0, du = 0;
+            // ---- B: each lane decides its own slow candidates, in draw order ----
+            // Walking its nf bits, a lane meets each slow draw that an earlier one
+            // did not consume; that draw consumes the next kU (wedge) or 2 kU (tail)
+            // draws as its uniforms, taken past the batch now if need be.  The wedge
+            // and tail tests run first in binary32 with proven margins (binary64 only
+            // inside them).  A rejected candidate goes to the drops; an accepted
+            // tail's m1 goes to the words of its first uniform for the value pass.
+            uint32_t du = 0, Dr = 0, L = 0;   // consumed uniforms, rejected, accepted tails
             int ne = 0;
-            if (rem > 0) {
-                if constexpr (kU == 1) {
-                    // As if every slow candidate were a wedge (one uniform): in each run
-                    // of consecutive nf bits the candidates are the bits at even
-                    // distance from the run's start.  A tail consumes one more draw:
-                    // the candidates after it are found again from its second uniform on.
-                    auto cands = [](uint32_t f) {
-                        const uint32_t S = f & ~(f << 1);                      // run starts
-                        const uint32_t re = f & ~(f + (S & 0x55555555u));      // runs starting at even bits
-                        return (re & 0x55555555u) | (f & ~re & 0xAAAAAAAAu);
-                    };
-                    R = cands(nf);
-                    for (uint32_t m = R; m; m &= m - 1u) {
-                        const int p = __ffs(m) - 1;
-                        const uint32_t w = row[SW * p + SW - 1];
-                        if ((w & 0x7Fu) == 0x7Fu) {   // a tail: draws p + 1 and p + 2 are its uniforms
-                            T |= 1u << p;
-                            const uint32_t Rn = cands(p + 3 >= 32 ? 0u : nf & (~0u << (p + 3)));
-                            R = (R & ((2u << p) - 1u)) | Rn;
-                            m = Rn | (1u << p);   // the loop clears bit p, then continues with Rn
-                        }
-                    }
-                    du = (R << 1) | (T << 2);
-                } else {
-                    uint32_t m = nf;
-                    while (m) {
-                        const int p = __ffs(m) - 1;
-                        const uint32_t w = row[SW * p + SW - 1];
-                        const bool tail = (w & 0x7Fu) == 0x7Fu;
-                        const int need = tail ? 2 * kU : kU;
-                        const int last = p + need;   // the last draw it consumes (< 32)
-                        R |= 1u << p;
-                        T |= tail ? 1u << p : 0u;
-                        du |= ((1u << need) - 1u) << (p + 1);
-                        m &= last >= 31 ? 0u : ~0u << (last + 1);
-                    }
-                }
-                const int lastU = du ? 31 - __clz(du) : -1;
-                while (B + ne <= lastU) {   // past the batch (rare)
+            for (uint32_t m = rem > 0 ? nf : 0u; m;) {
+                const int p = __ffs(m) - 1;
+                m &= m - 1u;
+                if ((du >> p) & 1u) continue;   // a uniform of an earlier candidate
+                const uint32_t w = row[SW * p + SW - 1];
+                const bool tail = (w & 0x7Fu) == 0x7Fu;
+                const int need = tail ? 2 * kU : kU;
+                du |= ((1u << need) - 1u) << (p + 1);   // p + need <= 31 + 4: bits past 31 drop out
+                while (B + ne <= p + need) {   // uniforms past the batch (rare)
                     uint32_t wx;
                     GT::draw(g, row + SW * (B + ne), wx);
                     ++ne;
                 }
-            }
-            // list them in lane order: this lane's first at the exclusive prefix sum of the counts
-            const int cnt = __popc(R);
-            int incl = cnt;
-#pragma unroll
-            for (int dd = 1; dd < 32; dd <<= 1) {
-                const int t = __shfl_up_sync(kFull, incl, dd);
-                if (lane >= dd) incl += t;
-            }
-            const int n_items = __shfl_sync(kFull, incl, 31);
-            for (int b0 = 0; b0 < n_items; b0 += 64) {   // 64 at a time (more is rare)
-                int idx = incl - cnt;
-                for (uint32_t m = R; m; m &= m - 1u, ++idx) {
-                    if (idx >= b0 && idx < b0 + 64) {
-                        const int p = __ffs(m) - 1;
-                        ws.list[idx - b0] = (uint32_t)lane | (uint32_t)p << 5 | ((T >> p) & 1u) << 10;
+                const uint64_t m1 = GT::m53(row, p + 1, sb);
+                if (!tail) {
+                    int f = z128_wedge_filter(slow, w & 0x7Fu, w >> 8, m1);
+                    if (f < 0) f = z128_wedge_exact(slow, w & 0x7Fu, w >> 8, m1) ? 1 : 0;
+                    Dr |= (f == 0 ? 1u : 0u) << p;
+                } else {
+                    const uint64_t m2 = GT::m53(row, p + 1 + kU, sb);
+                    int ft = z128_tail_filter(m1, m2);
+                    if (ft < 0) ft = z128_tail_exact(m1, m2) ? 1 : 0;
+                    if (ft == 0) {
+                        Dr |= 1u << p;
+                    } else {   // m1 goes to the first uniform's words (a dropped slot)
+                        row[SW * (p + 1)] = (uint32_t)m1;
+                        row[SW * (p + 1) + 1] = (uint32_t)(m1 >> 32);
+                        L |= 1u << p;
                     }
                 }
-                __syncwarp();
-                decide<PRNG>(ws, slow, ws.list[lane], b0 + lane < n_items);
-                if (b0 + 32 < n_items) decide<PRNG>(ws, slow, ws.list[32 + lane], b0 + 32 + lane < n_items);
-                __syncwarp();
             }
             // ---- C: drops, the unit's end, then the rows ----
             const int n = B + ne;   // slots drawn
-            uint32_t D = du | ws.drop[lane] | (n >= 32 ? 0u : (~0u << n));
-            const uint32_t L = ws.lit[lane];
-            ws.drop[lane] = 0;
-            ws.lit[lane] = 0;
+            uint32_t D = du | Dr | (n >= 32 ? 0u : (~0u << n));
             const int kept = 32 - __popc(D);
             int k_out = kept;
             if ((uint64_t)kept >= rem) {   // the unit ends in this batch: keep rem outputs

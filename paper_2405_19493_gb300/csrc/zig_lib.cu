@@ -1659,9 +1659,9 @@ static size_t zf_smem(int prng, int warps) {
     }
 }
 // The most threads a block of that kernel can have: as many warps as one SM's
-// shared memory holds (227 KB per block), at most zf::kMaxThreads.
+// shared memory holds (227 KB per block), at most zf::max_threads(prng).
 static int zf_max_block(int prng) {
-    int w = zf::kMaxThreads / 32;
+    int w = zf::max_threads(prng) / 32;
     while (w > 1 && zf_smem(prng, w) > 227 * 1024) --w;
     return 32 * w;
 }
