@@ -298,26 +298,19 @@ zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uint64_t *seed
  * Launch configuration of the 128-level generation kernel (ZIG_ZIG128).  The
  * paper's single-threaded Java generator has no counterpart; these knobs only
  * change how the same work is laid out on the GPU, never the values:
- *  block        threads per block, a multiple of 32: in [64, 768] for ZIG_F32 and
- *               ZIG_BF16 (default 768); in [64, 640] for ZIG_F64 (default 640),
+ *  block        threads per block, a multiple of 32 in [64, 640] (default 640),
  *               lowered at launch to what one SM's shared memory holds for the
  *               generator.
- *  batch        slots of a lane's row per batch: 32 for ZIG_F64 (the only
- *               value; 32 - 2 kU of them are draws, kU the raw steps of one
- *               nextDouble); for ZIG_F32 and ZIG_BF16 the candidates each lane
- *               draws before the warp decides its deferred wedge tests, 32
- *               (default) or 16.
- *  store_bytes  ZIG_F64: 0 (the warp writes each row with one store per lane,
- *               the row's batch as one contiguous run).  ZIG_F32, ZIG_BF16: 0
- *               (default; the warp writes each row cooperatively, one element
- *               per lane and store) or 32 (each lane writes its own row in
- *               whole 32-byte sectors, carrying a partial sector over to its
- *               next batch).
+ *  batch        slots of a lane's row per batch: 32, the only value (32 - 2 kU
+ *               of them are draws, kU the raw steps of one nextDouble).
+ *  store_bytes  0, the only value: the warp writes each row with one store per
+ *               lane, the row's batch as one contiguous run, for every dtype.
  *  fma_of_4     ZIG_F64: of every 4 rows, how many rebuild their values with one
  *               binary64 fused multiply-add per value; the others use the same
  *               correctly rounded product in 32-bit integer arithmetic (GB300's
  *               binary64 pipe is narrow).  2, 3 or 4; 0 = the library's default
- *               for the generator.  Must be 0 for ZIG_F32 and ZIG_BF16.
+ *               for the generator.  Must be 0 for ZIG_F32 and ZIG_BF16, whose
+ *               rows take one binary32 multiplication per value.
  * One configuration is kept per device, PRNG, dtype and input form
  * (variable_lengths = 1 for calls with a lengths array, 0 for uniform ones);
  * zig_generate and zig_generate_noalloc read it at each call.

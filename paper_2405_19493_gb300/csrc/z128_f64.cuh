@@ -127,14 +127,16 @@ __device__ __forceinline__ uint64_t first_state_of(const G& g) {
 
 // ---- shared memory ----
 // The fast table: one 256-byte block per signed layer ix = w & 0xFF (layer
-// ix & 127, positive when bit 7 is set).  Words 0..31: 16 copies of the signed
-// b = +-2^52 w[i] (low word, high word), one per lane & 15, so that the 16 lanes
-// of a half warp reading 8-byte entries of random layers hit distinct banks;
-// words 32..63: 32 copies of K = k[i] << 8, one per lane (j >= k[i] is w >= K).
-// The sign rides on b: the fma below rounds -(j w[i]) exactly as it rounds
-// j w[i] (its zero, for j = 0, takes b's sign by an OR), and the integer
-// product takes it from b's sign bit.  The block
-// stride of 256 bytes makes each address one byte permute of w.
+// ix & 127, positive when bit 7 is set).  Words 0..31, binary64 output: 16
+// copies of the signed b = +-2^52 w[i] (low word, high word), one per lane & 15,
+// so that the 16 lanes of a half warp reading 8-byte entries of random layers
+// hit distinct banks; binary32 and bfloat16 output: 32 copies of the signed
+// binary32 +-w32[i] = +-RN32(w[i]), one per lane.  Words 32..63: 32 copies of
+// K = k[i] << 8, one per lane (j >= k[i] is w >= K).  The sign rides on the
+// entry: the fma below rounds -(j w[i]) exactly as it rounds j w[i] (its zero,
+// for j = 0, takes b's sign by an OR), the integer product takes it from b's
+// sign bit, and the binary32 product j (-w32[i]) is -(j w32[i]), -0 for j = 0.
+// The block stride of 256 bytes makes each address one byte permute of w.
 struct Tab {
     uint32_t blk[256][64];
 };
@@ -169,6 +171,7 @@ __host__ __device__ constexpr size_t smem_bytes(int warps) {
     return head_bytes() + warp_bytes<PRNG>() * (size_t)warps;
 }
 
+template <int DT>
 __device__ __forceinline__ void tab_load(Tab& t, SlowTab& s) {
     for (int k = threadIdx.x; k < 256 * 64; k += blockDim.x) {
         const int ix = k >> 6, wd = k & 63, i = ix & 127;
@@ -177,10 +180,13 @@ __device__ __forceinline__ void tab_load(Tab& t, SlowTab& s) {
         uint32_t v;
         if (wd >= 32) {
             v = K;
-        } else {
+        } else if (DT == ZIG_F64) {
             const double bd = __dmul_rn(ix < 128 ? -wi : wi, 0x1p52);   // exact scaling, signed
             const long long b = __double_as_longlong(bd);
             v = (wd & 1) ? (uint32_t)(b >> 32) : (uint32_t)b;
+        } else {
+            const float w32 = d_z128_W32[i];
+            v = __float_as_uint(ix < 128 ? -w32 : w32);
         }
         t.blk[ix][wd] = v;
     }
@@ -233,31 +239,59 @@ __device__ __forceinline__ uint64_t x_of(const unsigned char* tab, uint32_t w, u
     }
 }
 
-// Write row r of the warp's batch: lane c takes slot c.
-template <int PRNG, bool kInt, class W>
+// The binary32 value RN32(j w32[i]) with the entry's sign, for the draw w
+// (binary32 and bfloat16 output; j < 2^24 converts exactly).
+__device__ __forceinline__ uint32_t x32_of(const unsigned char* tab, uint32_t w, uint32_t copy4) {
+    const float e = *(const float*)(tab + __byte_perm(w, copy4, 0x5504));   // block ix, copy
+    return __float_as_uint(__fmul_rn((float)(w >> 8), e));
+}
+
+// Write row r of the warp's batch: lane c takes slot c (binary64: kInt selects
+// the integer product).  bfloat16 is rounded from the binary32 value.
+template <int PRNG, int DT, bool kInt, class W>
 __device__ __forceinline__ void write_row(const W& ws, const unsigned char* tb, int r, int lane, uint32_t lane_bit,
-                                          uint32_t lt_mask, uint32_t copy8) {
+                                          uint32_t lt_mask, uint32_t copy) {
     using GT = Gen<PRNG>;
     const uint4 inf = ws.info[r];
     const uint32_t w = ws.stage[r * W::RS + GT::SW * lane + GT::SW - 1];
-    const uint64_t v = x_of<kInt>(tb, w, copy8);
     const uint32_t e = __popc(~inf.z & lt_mask);
-    const uint64_t addr = ((uint64_t)inf.x | (uint64_t)inf.y << 32) + 8ull * e;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %2, 0;\n\t@p st.global.cs.b64 [%0], %1;\n\t}" ::"l"(addr), "l"(v),
-        "r"(inf.z & lane_bit));
+    const uint64_t base = (uint64_t)inf.x | (uint64_t)inf.y << 32;
+    if constexpr (DT == ZIG_F64) {
+        const uint64_t v = x_of<kInt>(tb, w, copy);
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %2, 0;\n\t@p st.global.cs.b64 [%0], %1;\n\t}" ::"l"(base + 8ull * e),
+            "l"(v), "r"(inf.z & lane_bit));
+    } else if constexpr (DT == ZIG_F32) {
+        const uint32_t v = x32_of(tb, w, copy);
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %2, 0;\n\t@p st.global.cs.b32 [%0], %1;\n\t}" ::"l"(base + 4ull * e),
+            "r"(v), "r"(inf.z & lane_bit));
+    } else {
+        const uint16_t v = f32_to_bf16_bits(__uint_as_float(x32_of(tb, w, copy)));
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %2, 0;\n\t@p st.global.cs.b16 [%0], %1;\n\t}" ::"l"(base + 2ull * e),
+            "h"(v), "r"(inf.z & lane_bit));
+    }
 }
 
-// The values of queued accepted tails, 32 at a time (all 32 lanes call this).
-template <class W>
+// The values of queued accepted tails, 32 at a time (all 32 lanes call this):
+// binary64 x, or (binary32, bfloat16) RN32(x) with the sign, rounded once more
+// to bfloat16 for that output.  An entry's address carries the sign in bit 0.
+template <int DT, class W>
 __device__ __forceinline__ void drain_tails(W& ws, int lane) {
     const uint32_t n = ws.tq_n;
     for (uint32_t b = 0; b < n; b += 32) {
         if (b + lane < n) {
             const uint64_t ad = ws.tq_addr[b + lane];
             const double x = z128_tail_value(ws.tq_m1[b + lane]);
-            __stcs((unsigned long long*)(ad & ~7ull),
-                   (unsigned long long)__double_as_longlong(x) | (unsigned long long)(ad & 1u) << 63);
+            if constexpr (DT == ZIG_F64) {
+                __stcs((unsigned long long*)(ad & ~1ull),
+                       (unsigned long long)__double_as_longlong(x) | (unsigned long long)(ad & 1u) << 63);
+            } else {
+                const uint32_t v = __float_as_uint(__double2float_rn(x)) | (uint32_t)(ad & 1u) << 31;
+                if constexpr (DT == ZIG_F32) __stcs((unsigned int*)(ad & ~1ull), v);
+                else __stcs((unsigned short*)(ad & ~1ull), f32_to_bf16_bits(__uint_as_float(v)));
+            }
         }
     }
     __syncwarp();
@@ -265,17 +299,19 @@ __device__ __forceinline__ void drain_tails(W& ws, int lane) {
     __syncwarp();
 }
 
-template <int PRNG, int NDF>
+template <int PRNG, int DT, int NDF>
 __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) {
     using GT = Gen<PRNG>;
     using G = typename GT::G;
     using W = Warp<PRNG>;
+    using OutT = typename OutOf<DT>::T;
     constexpr int kU = GT::kU, SW = GT::SW, B = W::B;
     static_assert(NDF >= 2 && NDF <= 4, "rows per 4 with the binary64 fma");
+    static_assert(DT == ZIG_F64 || NDF == 4, "binary32 and bfloat16 rows have one product");
     extern __shared__ __align__(16) unsigned char zf_dsm[];
     Tab& tab = *(Tab*)zf_dsm;
     SlowTab& slow = *(SlowTab*)(zf_dsm + sizeof(Tab));
-    tab_load(tab, slow);
+    tab_load<DT>(tab, slow);
     __syncthreads();
     const unsigned char* const tb = zf_dsm;
 
@@ -285,7 +321,8 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
     const int n_warps = blockDim.x >> 5;
     W& ws = *(W*)(zf_dsm + head_bytes() + (size_t)wib * warp_bytes<PRNG>());
     uint32_t* const row = ws.stage + lane * W::RS;
-    const uint32_t copy8 = (uint32_t)(lane & 15) << 3;    // this lane's copy of b
+    // this lane's copy of the fast entry: b (binary64) or w32
+    const uint32_t copy = DT == ZIG_F64 ? (uint32_t)(lane & 15) << 3 : (uint32_t)lane << 2;
     const uint32_t kcopy = 0x80u + ((uint32_t)lane << 2);  // this lane's copy of K
 
     if (lane == 0) ws.tq_n = 0;
@@ -298,12 +335,12 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
     const uint64_t n_groups = (n_units + 31) >> 5;
     const uint64_t warp_id = (uint64_t)blockIdx.x * n_warps + wib;
     const uint64_t warp_stride = (uint64_t)gridDim.x * n_warps;
-    double* const out = (double*)a.out;
+    OutT* const out = (OutT*)a.out;
 
     for (uint64_t grp = warp_id; grp < n_groups; grp += warp_stride) {
         const uint64_t u = grp * 32 + lane;
         uint64_t rem = 0;
-        double* dst = out;
+        OutT* dst = out;
         G g;
         g.seed(0);
         zig_stream_state* srec = nullptr;   // the record to advance when the unit ends
@@ -415,10 +452,10 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
             // products q = 0..3 of every two steps: the binary64 fma for q < NDF
 #pragma unroll 2
             for (int r = 0; r < 32; r += 4) {
-                write_row<PRNG, (0 >= NDF)>(ws, tb, r + 0, lane, lane_bit, lt_mask, copy8);
-                write_row<PRNG, (1 >= NDF)>(ws, tb, r + 1, lane, lane_bit, lt_mask, copy8);
-                write_row<PRNG, (2 >= NDF)>(ws, tb, r + 2, lane, lane_bit, lt_mask, copy8);
-                write_row<PRNG, (3 >= NDF)>(ws, tb, r + 3, lane, lane_bit, lt_mask, copy8);
+                write_row<PRNG, DT, (0 >= NDF)>(ws, tb, r + 0, lane, lane_bit, lt_mask, copy);
+                write_row<PRNG, DT, (1 >= NDF)>(ws, tb, r + 1, lane, lane_bit, lt_mask, copy);
+                write_row<PRNG, DT, (2 >= NDF)>(ws, tb, r + 2, lane, lane_bit, lt_mask, copy);
+                write_row<PRNG, DT, (3 >= NDF)>(ws, tb, r + 3, lane, lane_bit, lt_mask, copy);
             }
             // accepted tails join the queue (one per lane per round), evaluated 32 at a time
             uint32_t Lk = L & ~D;
@@ -436,7 +473,7 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
                 __syncwarp();
                 if (lane == 0) ws.tq_n += __popc(bal);
                 __syncwarp();
-                if (ws.tq_n >= 32) drain_tails(ws, lane);
+                if (ws.tq_n >= 32) drain_tails<DT>(ws, lane);
             }
             dst += k_out;
             rem -= (uint64_t)k_out;
@@ -444,7 +481,7 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
         }
         if (check_chunk && draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
     }
-    drain_tails(ws, lane);
+    drain_tails<DT>(ws, lane);
 }
 
 }  // namespace zf

@@ -1581,9 +1581,9 @@ typedef void (*GenFn)(GenArgs);
 template <int PRNG>
 static GenFn pick_zf(int fma) {
     switch (fma) {
-    case 2: return zf::z128f_kernel<PRNG, 2>;
-    case 3: return zf::z128f_kernel<PRNG, 3>;
-    default: return zf::z128f_kernel<PRNG, 4>;
+    case 2: return zf::z128f_kernel<PRNG, ZIG_F64, 2>;
+    case 3: return zf::z128f_kernel<PRNG, ZIG_F64, 3>;
+    default: return zf::z128f_kernel<PRNG, ZIG_F64, 4>;
     }
 }
 
@@ -1592,8 +1592,8 @@ static GenFn pick_dt(int dt, bool half_batch, int fma) {
     if constexpr (ALG == ZIG_ZIG128) {
         switch (dt) {
         case ZIG_F64: return pick_zf<PRNG>(fma);
-        case ZIG_F32: return half_batch ? z128_kernel<PRNG, ZIG_F32, 0, 16> : z128_kernel<PRNG, ZIG_F32, 0>;
-        default: return half_batch ? z128_kernel<PRNG, ZIG_BF16, 0, 16> : z128_kernel<PRNG, ZIG_BF16, 0>;
+        case ZIG_F32: return zf::z128f_kernel<PRNG, ZIG_F32, 4>;
+        default: return zf::z128f_kernel<PRNG, ZIG_BF16, 4>;
         }
     } else {
         switch (dt) {
@@ -1666,15 +1666,18 @@ static int zf_max_block(int prng) {
     return 32 * w;
 }
 
-static size_t dyn_smem_of(int alg, int dt, int prng, bool half_batch = false, int block = kZBlock) {
+static size_t dyn_smem_of(int alg, int dt, int prng, bool half_batch = false, int block = kZBlock,
+                          bool mutation = false) {
     if (alg == ZIG_ZIG256 && dt == ZIG_F64) return z256_warp_bytes() * (size_t)(block / 32);
     if (alg != ZIG_ZIG128) return 0;
-    const int warps = block / 32;
-    if (dt == ZIG_F64) return zf_smem(prng, warps);
-    return prng == ZIG_LCG48 ? z128_dyn_for<GenLcg48>(dt, half_batch, warps)
-         : prng == ZIG_SPLITMIX64 ? z128_dyn_for<GenSplitMix64>(dt, half_batch, warps)
-         : prng == ZIG_L64X128MIX ? z128_dyn_for<GenL64X128Mix>(dt, half_batch, warps)
-                                  : z128_dyn_for<GenXoroshiro128PP>(dt, half_batch, warps);
+    if (mutation) {   // the mutation kernel (binary32 into the population)
+        const int warps = block / 32;
+        return prng == ZIG_LCG48 ? z128_dyn_for<GenLcg48>(dt, half_batch, warps)
+             : prng == ZIG_SPLITMIX64 ? z128_dyn_for<GenSplitMix64>(dt, half_batch, warps)
+             : prng == ZIG_L64X128MIX ? z128_dyn_for<GenL64X128Mix>(dt, half_batch, warps)
+                                      : z128_dyn_for<GenXoroshiro128PP>(dt, half_batch, warps);
+    }
+    return zf_smem(prng, block / 32);   // the batch kernel, whatever the output type
 }
 
 // ---- launch configuration of the 128-level generation kernel ----
@@ -1691,20 +1694,18 @@ static uint32_t default_batch(int dt) { (void)dt; return 32u; }
 // binary64: values of every 4 whose exact product uses the binary64 fma (the
 // rest use the integer product), by generator
 static uint32_t default_fma(int prng) { (void)prng; return 3u; }
-// binary64 rows go out as warp-wide runs, one row per store (the kernel's only
-// form); the narrower types in warp-cooperative element stores
+// every output type goes out as warp-wide row runs, one row per store (the batch
+// kernel's only form); the block is lowered at launch to what shared memory holds
 static LaunchCfg default_cfg(int dt) {
-    if (dt == ZIG_F64) return LaunchCfg{(uint32_t)zf::kMaxThreads, 32u, 0u, 0u};
-    return LaunchCfg{(uint32_t)kZBlock, default_batch(dt), 0u, 0u};
+    (void)dt;
+    return LaunchCfg{(uint32_t)zf::kMaxThreads, 32u, 0u, 0u};
 }
 
 static bool cfg_valid(int dt, const LaunchCfg& c) {
-    const uint32_t b = default_batch(dt);
-    if (!(c.block >= 64 && c.block % 32 == 0 && (c.batch == b || c.batch == b / 2))) return false;
-    if (dt == ZIG_F64)
-        return c.block <= (uint32_t)zf::kMaxThreads && c.batch == b && c.store_bytes == 0 &&
-               (c.fma == 0 || (c.fma >= 2 && c.fma <= 4));
-    return c.block <= (uint32_t)kZBlock && (c.store_bytes == 0 || c.store_bytes == 32) && c.fma == 0;
+    if (!(c.block >= 64 && c.block % 32 == 0 && c.block <= (uint32_t)zf::kMaxThreads &&
+          c.batch == default_batch(dt) && c.store_bytes == 0))
+        return false;
+    return dt == ZIG_F64 ? (c.fma == 0 || (c.fma >= 2 && c.fma <= 4)) : c.fma == 0;
 }
 
 static LaunchCfg cfg_of(int dev, int prng, int dt, bool variable) {
@@ -1782,13 +1783,12 @@ static zig_status launch_gen(int alg, int prng, int dt, int dev, bool variable, 
                              GenArgs& a, cudaStream_t s, const LaunchCfg* force) {
     const bool z128 = alg == ZIG_ZIG128;
     const LaunchCfg c = force ? *force : z128 ? cfg_of(dev, prng, dt, variable) : default_cfg(dt);
-    const bool half = z128 && c.batch != default_batch(dt);
     int block = z128 ? (int)c.block : (alg == ZIG_ZIG256 && dt == ZIG_F64) ? kZBlock : kBlock;
-    if (z128 && dt == ZIG_F64) block = std::min(block, zf_max_block(prng));
-    a.lane_sectors = (z128 && c.store_bytes == 32) ? 1u : 0u;
+    if (z128) block = std::min(block, zf_max_block(prng));
+    a.lane_sectors = 0u;
     const int fma = c.fma ? (int)c.fma : (int)default_fma(prng);
-    GenFn fn = pick(alg, prng, dt, half, fma);
-    const size_t dyn = dyn_smem_of(alg, dt, prng, half, block);
+    GenFn fn = pick(alg, prng, dt, false, fma);
+    const size_t dyn = dyn_smem_of(alg, dt, prng, false, block);
     if (!allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
     const int grid = grid_for((const void*)fn, dev, n_groups_hint, dyn, block);
     fn<<<grid, block, dyn, s>>>(a);
@@ -2041,13 +2041,11 @@ uint32_t zig_autotune_candidates(zig_dtype dtype, zig_launch_config* cands, uint
             }
         return n;
     }
-    static const uint32_t blocks[] = {256, 384, 512, 768};
-    for (uint32_t bl : blocks)
-        for (uint32_t bw : {b / 2, b})
-            for (uint32_t sb : {0u, 32u}) {
-                if (cands && n < max_cands) cands[n] = zig_launch_config{bl, bw, sb, 0};
-                ++n;
-            }
+    static const uint32_t blocks[] = {256, 384, 512, 640};
+    for (uint32_t bl : blocks) {
+        if (cands && n < max_cands) cands[n] = zig_launch_config{bl, b, 0u, 0u};
+        ++n;
+    }
     return n;
 }
 
@@ -2140,7 +2138,7 @@ static zig_status mutate_impl(float* x_dev, float sigma, uint64_t P, uint64_t L,
                    : prng == ZIG_L64X128MIX ? z128_kernel<2, ZIG_F32, 1>
                                             : z128_kernel<3, ZIG_F32, 1>;
     am.mut_seed = seed;
-    const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32, prng);
+    const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32, prng, false, kZBlock, true);
     if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
     int grid = host::grid_for((const void*)fn, dev, groups, dyn, kZBlock);
     fn<<<grid, kZBlock, dyn, s>>>(am);
@@ -2215,7 +2213,7 @@ zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_p
                    : prng == ZIG_SPLITMIX64 ? z128_kernel<1, ZIG_F32, 2>
                    : prng == ZIG_L64X128MIX ? z128_kernel<2, ZIG_F32, 2>
                                             : z128_kernel<3, ZIG_F32, 2>;
-    const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32, prng);
+    const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32, prng, false, kZBlock, true);
     if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
     int grid = host::grid_for((const void*)fn, dev, (units + 31) / 32, dyn, kZBlock);
     fn<<<grid, kZBlock, dyn, s>>>(a);
