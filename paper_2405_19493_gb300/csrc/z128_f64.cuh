@@ -150,7 +150,7 @@ struct SlowTab {   // the wedge test's tables (z128_wedge_accept)
 __host__ __device__ constexpr int max_threads(int prng) { return prng >= 0 ? 640 : 640; }
 constexpr int kMaxThreads = 640;
 
-template <int PRNG>
+template <int PRNG, int DT>
 struct Warp {
     static constexpr int kU = Gen<PRNG>::kU, SW = Gen<PRNG>::SW;
     static constexpr int B = 32 - 2 * kU;                  // draws per batch
@@ -161,14 +161,14 @@ struct Warp {
     uint64_t tq_m1[64];        // and their uniform m1 (U1 = 1 - m1 2^-53)
     uint32_t tq_n;
 };
-template <int PRNG>
+template <int PRNG, int DT>
 __host__ __device__ constexpr size_t warp_bytes() {
-    return (sizeof(Warp<PRNG>) + 15) & ~(size_t)15;
+    return (sizeof(Warp<PRNG, DT>) + 15) & ~(size_t)15;
 }
 __host__ __device__ constexpr size_t head_bytes() { return sizeof(Tab) + ((sizeof(SlowTab) + 15) & ~(size_t)15); }
-template <int PRNG>
+template <int PRNG, int DT>
 __host__ __device__ constexpr size_t smem_bytes(int warps) {
-    return head_bytes() + warp_bytes<PRNG>() * (size_t)warps;
+    return head_bytes() + warp_bytes<PRNG, DT>() * (size_t)warps;
 }
 
 template <int DT>
@@ -303,7 +303,7 @@ template <int PRNG, int DT, int NDF>
 __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) {
     using GT = Gen<PRNG>;
     using G = typename GT::G;
-    using W = Warp<PRNG>;
+    using W = Warp<PRNG, DT>;
     using OutT = typename OutOf<DT>::T;
     constexpr int kU = GT::kU, SW = GT::SW, B = W::B;
     static_assert(NDF >= 2 && NDF <= 4, "rows per 4 with the binary64 fma");
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
     const uint32_t lane_bit = 1u << lane, lt_mask = lane_bit - 1u;
     const int wib = threadIdx.x >> 5;
     const int n_warps = blockDim.x >> 5;
-    W& ws = *(W*)(zf_dsm + head_bytes() + (size_t)wib * warp_bytes<PRNG>());
+    W& ws = *(W*)(zf_dsm + head_bytes() + (size_t)wib * warp_bytes<PRNG, DT>());
     uint32_t* const row = ws.stage + lane * W::RS;
     // this lane's copy of the fast entry: b (binary64) or w32
     const uint32_t copy = DT == ZIG_F64 ? (uint32_t)(lane & 15) << 3 : (uint32_t)lane << 2;

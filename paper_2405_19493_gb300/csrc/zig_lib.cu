@@ -1650,19 +1650,24 @@ static size_t z128_dyn_for(int dt, bool half_batch, int warps) {
 }
 
 // Shared memory of the binary64 128-level kernel: tables plus one warp area per warp.
-static size_t zf_smem(int prng, int warps) {
+template <int DT>
+static size_t zf_smem_dt(int prng, int warps) {
     switch (prng) {
-    case ZIG_LCG48: return zf::smem_bytes<0>(warps);
-    case ZIG_SPLITMIX64: return zf::smem_bytes<1>(warps);
-    case ZIG_L64X128MIX: return zf::smem_bytes<2>(warps);
-    default: return zf::smem_bytes<3>(warps);
+    case ZIG_LCG48: return zf::smem_bytes<0, DT>(warps);
+    case ZIG_SPLITMIX64: return zf::smem_bytes<1, DT>(warps);
+    case ZIG_L64X128MIX: return zf::smem_bytes<2, DT>(warps);
+    default: return zf::smem_bytes<3, DT>(warps);
     }
+}
+static size_t zf_smem(int prng, int dt, int warps) {
+    return dt == ZIG_F64 ? zf_smem_dt<ZIG_F64>(prng, warps)
+         : dt == ZIG_F32 ? zf_smem_dt<ZIG_F32>(prng, warps) : zf_smem_dt<ZIG_BF16>(prng, warps);
 }
 // The most threads a block of that kernel can have: as many warps as one SM's
 // shared memory holds (227 KB per block), at most zf::max_threads(prng).
-static int zf_max_block(int prng) {
+static int zf_max_block(int prng, int dt) {
     int w = zf::max_threads(prng) / 32;
-    while (w > 1 && zf_smem(prng, w) > 227 * 1024) --w;
+    while (w > 1 && zf_smem(prng, dt, w) > 227 * 1024) --w;
     return 32 * w;
 }
 
@@ -1677,7 +1682,7 @@ static size_t dyn_smem_of(int alg, int dt, int prng, bool half_batch = false, in
              : prng == ZIG_L64X128MIX ? z128_dyn_for<GenL64X128Mix>(dt, half_batch, warps)
                                       : z128_dyn_for<GenXoroshiro128PP>(dt, half_batch, warps);
     }
-    return zf_smem(prng, block / 32);   // the batch kernel, whatever the output type
+    return zf_smem(prng, dt, block / 32);   // the batch kernel
 }
 
 // ---- launch configuration of the 128-level generation kernel ----
@@ -1784,7 +1789,7 @@ static zig_status launch_gen(int alg, int prng, int dt, int dev, bool variable, 
     const bool z128 = alg == ZIG_ZIG128;
     const LaunchCfg c = force ? *force : z128 ? cfg_of(dev, prng, dt, variable) : default_cfg(dt);
     int block = z128 ? (int)c.block : (alg == ZIG_ZIG256 && dt == ZIG_F64) ? kZBlock : kBlock;
-    if (z128) block = std::min(block, zf_max_block(prng));
+    if (z128) block = std::min(block, zf_max_block(prng, dt));
     a.lane_sectors = 0u;
     const int fma = c.fma ? (int)c.fma : (int)default_fma(prng);
     GenFn fn = pick(alg, prng, dt, false, fma);
