@@ -513,11 +513,13 @@ const char *zig_status_string(zig_status status);
  * fused multiply-add and 32-bit integer ones on both signed table entries
  * (+-2^52 w[i]) -- and compares each with IEEE multiplication (__dmul_rn, negated
  * for the negative entries); rounds every finite binary32 bit pattern to
- * bfloat16 by the kernel's routine and compares it with __float2bfloat16_rn; and
- * compares the tail step's own binary64 log with CUDA's log on 2^31 uniforms in
- * (0, 1).  Writes counts_host[0] = product mismatches, [1] = bfloat16
- * mismatches, [2] = products checked (5 * 2^31), [3] = patterns checked, [4] =
- * logs more than one ulp from CUDA's, [5] = logs not equal to CUDA's.
+ * bfloat16 by the kernel's routine and compares it with __float2bfloat16_rn,
+ * and 2^32 binary64 values in [2^-113, 8) of both signs to binary32 and compares
+ * that with __double2float_rn; and compares the tail step's own binary64 log
+ * with CUDA's log on 2^31 uniforms in (0, 1).  Writes counts_host[0] = product
+ * mismatches, [1] = rounding mismatches, [2] = products checked (5 * 2^31),
+ * [3] = roundings checked, [4] = logs more than one ulp from CUDA's, [5] = logs
+ * not equal to CUDA's.
  * Synchronous; allocates 48 bytes of device memory for the call.
  * ZIG_ERR_NOT_INITIALIZED without zig_tables_init.
  */

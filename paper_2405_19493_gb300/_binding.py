@@ -409,8 +409,8 @@ def zig_selfcheck() -> dict:
     """Exhaustive check of the fast-path product and the bfloat16 rounding (see zig.h)."""
     c = (C.c_uint64 * 6)()
     _check(load().zig_selfcheck(c), "zig_selfcheck")
-    return {"product_mismatches": int(c[0]), "bf16_mismatches": int(c[1]),
-            "products_checked": int(c[2]), "patterns_checked": int(c[3]),
+    return {"product_mismatches": int(c[0]), "rounding_mismatches": int(c[1]),
+            "products_checked": int(c[2]), "roundings_checked": int(c[3]),
             "logs_beyond_one_ulp": int(c[4]), "logs_not_equal": int(c[5])}
 
 

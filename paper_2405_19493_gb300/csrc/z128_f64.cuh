@@ -1,5 +1,5 @@
 // 128-level ziggurat with binary64 output: the speculative batch kernel.
-// Included by zig_lib.cu after the samplers, the unit helpers and z256_kernel.
+// Included by zig_lib.cu after the samplers and the unit helpers.
 //
 // Each lane owns one unit (a stream, or a 2^c chunk of one) with its generator
 // in registers; a warp works on its 32 units in batches of B draws per lane,
@@ -140,7 +140,7 @@ __device__ __forceinline__ uint64_t first_state_of(const G& g) {
 struct Tab {
     uint32_t blk[256][64];
 };
-struct SlowTab {   // the wedge test's tables (z128_wedge_accept)
+struct SlowTab {   // the wedge test's tables (z128_wedge_filter, z128_wedge_exact)
     float W32[128], Y32[128], DY32[128];
     double Wd[128], Y[128];
 };
@@ -150,7 +150,7 @@ struct SlowTab {   // the wedge test's tables (z128_wedge_accept)
 __host__ __device__ constexpr int max_threads(int prng) { return prng >= 0 ? 640 : 640; }
 constexpr int kMaxThreads = 640;
 
-template <int PRNG, int DT>
+template <int PRNG, int DT, int MUT = 0>
 struct Warp {
     static constexpr int kU = Gen<PRNG>::kU, SW = Gen<PRNG>::SW;
     static constexpr int B = 32 - 2 * kU;                  // draws per batch
@@ -159,16 +159,21 @@ struct Warp {
     uint4 info[32];            // per row: output address (low, high), dropped slots
     uint64_t tq_addr[64];      // accepted tails waiting for their value: output address | negative
     uint64_t tq_m1[64];        // and their uniform m1 (U1 = 1 - m1 2^-53)
+    uint32_t tq_sig[MUT ? 64 : 1];   // mutation: and their row's sigma bits (kGenerate: x = z)
+    uint32_t tails[MUT ? 32 : 1];    // mutation: per row, the accepted tails (their queue entry updates x)
     uint32_t tq_n;
 };
-template <int PRNG, int DT>
+template <int PRNG, int DT, int MUT = 0>
 __host__ __device__ constexpr size_t warp_bytes() {
-    return (sizeof(Warp<PRNG, DT>) + 15) & ~(size_t)15;
+    return (sizeof(Warp<PRNG, DT, MUT>) + 15) & ~(size_t)15;
 }
+// a mutation row's sigma word when the request generates (x = z): a NaN pattern
+// no finite sigma has
+constexpr uint32_t kGenerate = 0xFFFFFFFFu;
 __host__ __device__ constexpr size_t head_bytes() { return sizeof(Tab) + ((sizeof(SlowTab) + 15) & ~(size_t)15); }
-template <int PRNG, int DT>
+template <int PRNG, int DT, int MUT = 0>
 __host__ __device__ constexpr size_t smem_bytes(int warps) {
-    return head_bytes() + warp_bytes<PRNG, DT>() * (size_t)warps;
+    return head_bytes() + warp_bytes<PRNG, DT, MUT>() * (size_t)warps;
 }
 
 template <int DT>
@@ -274,17 +279,50 @@ __device__ __forceinline__ void write_row(const W& ws, const unsigned char* tb, 
     }
 }
 
+// Mutation rows r0 .. r0 + 7 (binary32 population x, row pointer and sigma word
+// in the row's info): every lane loads its eight elements of x first, so that the
+// loads overlap, then stores x + sigma z (fmaf, one rounding) or z.  Each element
+// is read once, by the thread that then writes it; an accepted tail's element is
+// left to its queue entry, which reads and writes it once its value is known.
+template <int PRNG, class W>
+__device__ __forceinline__ void mutate_rows8(const W& ws, const unsigned char* tb, int r0, int lane,
+                                             uint32_t lane_bit, uint32_t lt_mask, uint32_t copy) {
+    using GT = Gen<PRNG>;
+    float* px[8];
+    float xv[8];
+    uint32_t sg[8];
+    bool st[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint4 inf = ws.info[r0 + k];
+        px[k] = (float*)((uint64_t)inf.x | (uint64_t)inf.y << 32) + __popc(~inf.z & lt_mask);
+        sg[k] = inf.w;
+        st[k] = !((inf.z | ws.tails[r0 + k]) & lane_bit);   // a kept slot that is no queued tail
+        xv[k] = (st[k] && sg[k] != kGenerate) ? __ldcs(px[k]) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float z = __uint_as_float(x32_of(tb, ws.stage[(r0 + k) * W::RS + GT::SW * lane + GT::SW - 1], copy));
+        if (st[k]) __stcs(px[k], sg[k] == kGenerate ? z : fmaf(__uint_as_float(sg[k]), z, xv[k]));
+    }
+}
+
 // The values of queued accepted tails, 32 at a time (all 32 lanes call this):
 // binary64 x, or (binary32, bfloat16) RN32(x) with the sign, rounded once more
 // to bfloat16 for that output.  An entry's address carries the sign in bit 0.
-template <int DT, class W>
+template <int DT, int MUT, class W>
 __device__ __forceinline__ void drain_tails(W& ws, int lane) {
     const uint32_t n = ws.tq_n;
     for (uint32_t b = 0; b < n; b += 32) {
         if (b + lane < n) {
             const uint64_t ad = ws.tq_addr[b + lane];
             const double x = z128_tail_value(ws.tq_m1[b + lane]);
-            if constexpr (DT == ZIG_F64) {
+            if constexpr (MUT != 0) {   // binary32 into the population: x = z, or x += sigma z
+                const float z = __uint_as_float(__float_as_uint(__double2float_rn(x)) | (uint32_t)(ad & 1u) << 31);
+                float* const px = (float*)(ad & ~1ull);
+                const uint32_t sg = ws.tq_sig[b + lane];
+                __stcs(px, sg == kGenerate ? z : fmaf(__uint_as_float(sg), z, __ldcs(px)));
+            } else if constexpr (DT == ZIG_F64) {
                 __stcs((unsigned long long*)(ad & ~1ull),
                        (unsigned long long)__double_as_longlong(x) | (unsigned long long)(ad & 1u) << 63);
             } else {
@@ -299,15 +337,18 @@ __device__ __forceinline__ void drain_tails(W& ws, int lane) {
     __syncwarp();
 }
 
-template <int PRNG, int DT, int NDF>
+// MUT: 0 generation; 1 mutation of a P x L population (row p seeded mut_seed + p,
+// or continuing state[p]); 2 a batch of mutation and generation requests.
+template <int PRNG, int DT, int NDF, int MUT = 0>
 __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) {
     using GT = Gen<PRNG>;
     using G = typename GT::G;
-    using W = Warp<PRNG, DT>;
+    using W = Warp<PRNG, DT, MUT>;
     using OutT = typename OutOf<DT>::T;
     constexpr int kU = GT::kU, SW = GT::SW, B = W::B;
     static_assert(NDF >= 2 && NDF <= 4, "rows per 4 with the binary64 fma");
     static_assert(DT == ZIG_F64 || NDF == 4, "binary32 and bfloat16 rows have one product");
+    static_assert(MUT == 0 || DT == ZIG_F32, "populations are binary32");
     extern __shared__ __align__(16) unsigned char zf_dsm[];
     Tab& tab = *(Tab*)zf_dsm;
     SlowTab& slow = *(SlowTab*)(zf_dsm + sizeof(Tab));
@@ -319,7 +360,7 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
     const uint32_t lane_bit = 1u << lane, lt_mask = lane_bit - 1u;
     const int wib = threadIdx.x >> 5;
     const int n_warps = blockDim.x >> 5;
-    W& ws = *(W*)(zf_dsm + head_bytes() + (size_t)wib * warp_bytes<PRNG, DT>());
+    W& ws = *(W*)(zf_dsm + head_bytes() + (size_t)wib * warp_bytes<PRNG, DT, MUT>());
     uint32_t* const row = ws.stage + lane * W::RS;
     // this lane's copy of the fast entry: b (binary64) or w32
     const uint32_t copy = DT == ZIG_F64 ? (uint32_t)(lane & 15) << 3 : (uint32_t)lane << 2;
@@ -327,7 +368,7 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
 
     if (lane == 0) ws.tq_n = 0;
     __syncwarp();
-    if (a.out == nullptr) {   // only legal when every length is zero
+    if (MUT == 0 && a.out == nullptr) {   // only legal when every length is zero
         if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.err, kErrNullOutput);
         return;
     }
@@ -344,17 +385,49 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
         G g;
         g.seed(0);
         zig_stream_state* srec = nullptr;   // the record to advance when the unit ends
+        uint32_t sig = 0;                    // mutation: the row's sigma bits, or kGenerate
         if (u < n_units) {
-            uint64_t s, q, off, n;
-            unit_info(a, u, s, q, off, n);
-            bool ok;
-            srec = unit_gen<PRNG>(a, s, q, g, ok);
-            if (ok) {
-                rem = n;
-                dst = out + off;
+            bool ok = true;
+            if constexpr (MUT == 2) {
+                // the request holding unit u (the last with ustart <= u); a row has
+                // units of 2^10 outputs from 2^32-draw windows, or one unit continuing
+                // its record
+                uint32_t lo = 0, hi = a.n_req;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (a.reqs[mid].ustart <= u) lo = mid; else hi = mid;
+                }
+                const MutDesc& r = a.reqs[lo];
+                const uint64_t ur = u - r.ustart, p = ur / r.upr, qd = ur - p * r.upr;
+                if (r.state) {
+                    if (state_load<PRNG>(r.state + p, g, a.err, ok)) srec = r.state + p;
+                } else {
+                    g.seed(r.seed + p);
+                    if (qd) g.jump(qd * kChunkDraws, &d_jump);
+                }
+                const uint64_t t0 = qd << 10;
+                if (ok) {
+                    rem = r.state ? r.L : umin64(r.L - t0, 1024);
+                    dst = (OutT*)(r.x + p * r.L + t0);
+                }
+                sig = r.kind == ZIG_REQ_GENERATE ? kGenerate : __float_as_uint(r.sigma);
+            } else {
+                uint64_t s, q, off, n;
+                unit_info(a, u, s, q, off, n);
+                if (MUT == 1 && a.state == nullptr) {   // mutation: row s seeded mut_seed + s
+                    g.seed(a.mut_seed + s);
+                    if (q) g.jump(q * kChunkDraws, &d_jump);
+                } else {
+                    srec = unit_gen<PRNG>(a, s, q, g, ok);
+                }
+                if (ok) {
+                    rem = n;
+                    dst = out + off;
+                }
+                sig = __float_as_uint(a.sigma);
             }
         }
-        const bool check_chunk = a.chunk_log2 != 0 && rem != 0;
+        const bool check_chunk = srec == nullptr && a.chunk_log2 != 0 && rem != 0;
         uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
 
         while (__any_sync(kFull, rem > 0)) {
@@ -447,15 +520,21 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
             } else if (check_chunk) {
                 draws += (uint64_t)n;
             }
-            ws.info[lane] = make_uint4((uint32_t)(uintptr_t)dst, (uint32_t)((uintptr_t)dst >> 32), D, 0u);
+            ws.info[lane] = make_uint4((uint32_t)(uintptr_t)dst, (uint32_t)((uintptr_t)dst >> 32), D, sig);
+            if constexpr (MUT != 0) ws.tails[lane] = L & ~D;
             __syncwarp();
-            // products q = 0..3 of every two steps: the binary64 fma for q < NDF
+            if constexpr (MUT != 0) {
+#pragma unroll 1
+                for (int r = 0; r < 32; r += 8) mutate_rows8<PRNG>(ws, tb, r, lane, lane_bit, lt_mask, copy);
+            } else {
+                // products q = 0..3 of every two steps: the binary64 fma for q < NDF
 #pragma unroll 2
-            for (int r = 0; r < 32; r += 4) {
-                write_row<PRNG, DT, (0 >= NDF)>(ws, tb, r + 0, lane, lane_bit, lt_mask, copy);
-                write_row<PRNG, DT, (1 >= NDF)>(ws, tb, r + 1, lane, lane_bit, lt_mask, copy);
-                write_row<PRNG, DT, (2 >= NDF)>(ws, tb, r + 2, lane, lane_bit, lt_mask, copy);
-                write_row<PRNG, DT, (3 >= NDF)>(ws, tb, r + 3, lane, lane_bit, lt_mask, copy);
+                for (int r = 0; r < 32; r += 4) {
+                    write_row<PRNG, DT, (0 >= NDF)>(ws, tb, r + 0, lane, lane_bit, lt_mask, copy);
+                    write_row<PRNG, DT, (1 >= NDF)>(ws, tb, r + 1, lane, lane_bit, lt_mask, copy);
+                    write_row<PRNG, DT, (2 >= NDF)>(ws, tb, r + 2, lane, lane_bit, lt_mask, copy);
+                    write_row<PRNG, DT, (3 >= NDF)>(ws, tb, r + 3, lane, lane_bit, lt_mask, copy);
+                }
             }
             // accepted tails join the queue (one per lane per round), evaluated 32 at a time
             uint32_t Lk = L & ~D;
@@ -469,11 +548,12 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
                     const uint32_t w = row[SW * p + SW - 1];
                     ws.tq_addr[idx] = (uint64_t)(uintptr_t)(dst + __popc(~D & ((1u << p) - 1u))) | ((~w >> 7) & 1u);
                     ws.tq_m1[idx] = (uint64_t)row[SW * (p + 1)] | (uint64_t)row[SW * (p + 1) + 1] << 32;
+                    if constexpr (MUT != 0) ws.tq_sig[idx] = sig;
                 }
                 __syncwarp();
                 if (lane == 0) ws.tq_n += __popc(bal);
                 __syncwarp();
-                if (ws.tq_n >= 32) drain_tails<DT>(ws, lane);
+                if (ws.tq_n >= 32) drain_tails<DT, MUT>(ws, lane);
             }
             dst += k_out;
             rem -= (uint64_t)k_out;
@@ -481,7 +561,7 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
         }
         if (check_chunk && draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
     }
-    drain_tails<DT>(ws, lane);
+    drain_tails<DT, MUT>(ws, lane);
 }
 
 }  // namespace zf

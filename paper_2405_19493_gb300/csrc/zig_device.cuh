@@ -324,6 +324,20 @@ __device__ __forceinline__ uint16_t f64_to_bf16_bits(double x) {
     return (uint16_t)((sign << 15) | (e << 7) | (q & 0x7F));
 }
 
+// RN-even binary64 -> binary32 bits for zero and for magnitudes in [2^-126, 2^128)
+// (the exponent is rebiased by 1023 - 127 after the rounding carry).
+__device__ __forceinline__ uint32_t f64_to_f32_bits(double x) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const uint64_t mag = b & 0x7FFFFFFFFFFFFFFFull;
+    if (mag == 0) return sign;
+    uint64_t q = mag >> 29;
+    const uint64_t rem = mag & ((1ull << 29) - 1);
+    const uint64_t half = 1ull << 28;
+    q += (rem > half) | ((rem == half) & (q & 1));
+    return sign | (uint32_t)(q - (896ull << 23));
+}
+
 // RN-even binary32 -> bfloat16 bits (finite inputs).
 __device__ __forceinline__ uint16_t f32_to_bf16_bits(float x) {
     uint32_t b = __float_as_uint(x);

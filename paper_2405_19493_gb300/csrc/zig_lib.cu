@@ -67,7 +67,6 @@ struct GenArgs {
     uint64_t mut_seed;         // mutation only: row p is seeded mut_seed + p
     const struct MutDesc* reqs;  // batched mutation: request descriptors
     uint32_t n_req;              // batched mutation: number of requests
-    uint32_t lane_sectors;       // generation: 1 = lane-per-row flush in 32-byte sectors
     unsigned* err;               // where device-side errors are latched (a caller's word or the device's)
     zig_stream_state* state;     // stream records to continue and advance (chunk_log2 = 0), or NULL
 };
@@ -270,63 +269,6 @@ __device__ __forceinline__ int z256_overhang_filter(float ox, float odx, float o
     return -1;
 }
 
-template <class G>
-__device__ __forceinline__ double z256_slow(G& g, const Z256Smem& t, uint32_t& extra) {
-    constexpr uint32_t kSteps64 = std::is_same<G, GenLcg48>::value ? 2u : 1u;
-    constexpr uint32_t kStepsPerDouble = kSteps64;
-    const uint64_t two53 = 1ull << 53;
-    uint64_t V = g.next_u64();
-    extra += kSteps64;
-    uint32_t b = (uint32_t)(V & 0xFF);
-    int r = ((V >> 8) < t.THR[b]) ? (int)b : t.ALIAS[b];
-    if (r == 0) {
-        const double x0 = zigtab::ZIG256_X0;
-        for (;;) {
-            double U1 = __dsub_rn(1.0, m53_to_double(g.next_m53()));
-            double U2 = __dsub_rn(1.0, m53_to_double(g.next_m53()));
-            extra += 2 * kStepsPerDouble;
-            double x = __ddiv_rn(-zlog(U1), x0);
-            double y = -zlog(U2);
-            if (__dadd_rn(y, y) > __dmul_rn(x, x)) return __dadd_rn(x0, x);
-        }
-    }
-    const int kd = d_z256_KIND[r - 1];
-    const double ox = d_z256_OX[r - 1], odx = d_z256_ODX[r - 1];
-    const double oy = d_z256_OY[r - 1], ody = d_z256_ODY[r - 1];
-    const uint64_t qa = d_z256_QA[r - 1];
-    for (;;) {
-        uint64_t m1 = g.next_m53();
-        uint64_t m2 = g.next_m53();
-        extra += 2 * kStepsPerDouble;
-        if (kd > 0 && m1 + m2 > two53) {
-            m1 = two53 - m1;
-            m2 = two53 - m2;
-        }
-        const double x = __dadd_rn(ox, __dmul_rn(odx, u53_to_double(m1, 53)));
-        if (kd > 0 && m1 + m2 <= two53 - qa) return x;
-        if (kd < 0 && m1 + m2 < two53) return x;
-        const int f = z256_overhang_filter((float)ox, (float)odx, (float)oy, (float)ody, m1, m2);
-        if (f == 1) return x;
-        if (f == 0) continue;
-        const double y = __dadd_rn(oy, __dmul_rn(ody, u53_to_double(m2, 53)));
-        if (y < exp(neg_half_sq(x))) return x;
-    }
-}
-
-template <class G>
-__device__ __forceinline__ double z256_f64(G& g, const Z256Smem& t, uint32_t& extra) {
-    uint64_t U = g.next_u64();
-    uint32_t j = (uint32_t)(U & 0xFF);
-    bool neg = (U >> 8) & 1;
-    double x;
-    if (j < (uint32_t)zigtab::ZIG256_NR) {
-        x = __dmul_rn(t.XS[j], u53_to_double(U >> 11));
-    } else {
-        x = z256_slow(g, t, extra);
-    }
-    return __longlong_as_double(__double_as_longlong(x) | ((long long)neg << 63));   // x >= 0
-}
-
 // ---------------------------------------------------------------------------
 // output conversion
 // ---------------------------------------------------------------------------
@@ -343,15 +285,13 @@ template <> __device__ __forceinline__ uint16_t from_f64<ZIG_BF16>(double z) { r
 // ---------------------------------------------------------------------------
 // generation kernel
 // ---------------------------------------------------------------------------
+// The polar method (Marsaglia), one stream per lane, outputs staged per warp.
 template <int ALG, int PRNG, int DT>
 __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
     using G = typename GenOf<PRNG>::T;
     using OutT = typename OutOf<DT>::T;
-    static_assert(ALG == ZIG_POLAR || ALG == ZIG_ZIG256, "zig128 runs in z128_kernel");
-    __shared__ Z256Smem t256;
+    static_assert(ALG == ZIG_POLAR, "the ziggurats run in their batch kernels");
     __shared__ OutT stage_all[kWarps][32 * kStageCols];
-    if (ALG == ZIG_ZIG256) z256_load(t256);
-    __syncthreads();
 
     const int lane = threadIdx.x & 31;
     OutT* stage = stage_all[threadIdx.x >> 5];
@@ -396,13 +336,7 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
 #pragma unroll 1
             for (int v = 0; v < kStageCols; ++v) {
                 if (v < cnt) {
-                    OutT z;
-                    if (ALG == ZIG_POLAR) {
-                        z = from_f64<DT>(polar_f64(g, have, cached, extra));
-                    } else {
-                        z = from_f64<DT>(z256_f64(g, t256, extra));
-                    }
-                    stage[stage_idx<OutT>(lane, v)] = z;
+                    stage[stage_idx<OutT>(lane, v)] = from_f64<DT>(polar_f64(g, have, cached, extra));
                 }
             }
             __syncwarp();
@@ -411,87 +345,18 @@ __global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
             dst += cnt;
             rem -= cnt;
         }
-        // A chunk must stay inside its 2^32-draw window.  Each variate's first
-        // draw takes `per` raw steps; `extra` counts every other step.
-        if (a.chunk_log2 && n_unit) {
-            const uint64_t per = (PRNG == ZIG_LCG48) ? 2 : 1;   // zig256's first draw is a nextLong
-            uint64_t draws = (ALG == ZIG_POLAR) ? (uint64_t)extra : n_unit * per + extra;
-            if (draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
-        }
+        // A chunk must stay inside its 2^32-draw window; `extra` counts the raw steps.
+        if (a.chunk_log2 && n_unit && (uint64_t)extra > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
         // a lane draws only for its own outputs, so g stands at the stream's next draw
-        if (srec && n_unit) state_store(srec, g, ALG == ZIG_POLAR && have, cached);
+        if (srec && n_unit) state_store(srec, g, have, cached);
     }
 }
 
 // ---------------------------------------------------------------------------
-// 128-level ziggurat (GSL form): one launch per bulk request
+// 128-level ziggurat (GSL form): the slow tests shared by the batch kernel
 // ---------------------------------------------------------------------------
-// Each lane owns one unit (stream or chunk) with its generator in registers.
-// A warp works in batches of B candidates per lane (B = 20 for binary64, 32
-// otherwise, or half that by launch configuration), staged in shared memory:
-//  A. the lanes draw their candidates in lockstep; one warp vote per candidate
-//     guards the rare slow draws.
-//     - fast path (j < k[i]): x = RN(j * w[i]) on the spot.  For binary64 this
-//       is one fused multiply-add, fma(1 + j 2^-52, 2^52 w, -2^52 w) = RN(j w)
-//       exactly (1 + j 2^-52 is built from j's bits, 2^52 w is in the table);
-//       GB300's narrow binary64 pipe keeps up with one per candidate, and the
-//       same product in integer arithmetic costs far more issue slots.
-//       binary32/bfloat16 use fl32(j * w32[i]).
-//     - wedge (i < 127): deferred.  The slot keeps the draw w,
-//       the generator writes an 8-byte record from which the test's uniform is
-//       rebuilt (G::snap) and moves past that uniform at once.  A lane holds up
-//       to kZRec records per batch; a further wedge is decided on the spot.
-//     - tail (i = 127, j >= k[127]; 0.06 % of draws): decided in the lane.
-//  B. at the end of the batch the warp's deferred wedges are listed and tested
-//     32 at a time, in binary32 with a proven margin (binary64 only inside it);
-//     an accepted slot gets RN(j w[i]), a rejected one is flagged.
-//  C. the rows are written, skipping rejected slots: binary64 rows by their own
-//     lanes in whole 32-byte sectors, the narrower types B lanes per row; the
-//     unit continues in the next batch.
-// The outputs of a unit are its accepted candidates in draw order: exactly the
-// sequence a one-variate-at-a-time loop produces.
-
-
-// The fast path's table.  Binary64 kernels index it by the draw's low byte
-// ix = w & 0xFF (layer ix & 127, positive when bit 7 is set); one 16-byte entry
-// holds everything a candidate needs: {low, high word of 2^52 w[i], k[i], the
-// output's sign bit}, in 8 copies so that the 8 lanes of a quarter warp
-// reading 16-byte entries hit distinct banks.  The narrower types keep k[i]
-// in one copy per lane.
-struct Z128FastF64 { uint4 T[256][8]; };
-struct Z128FastNarrow { uint32_t K[128][32]; };
-template <int DT>
-struct Z128Tab : std::conditional<DT == ZIG_F64, Z128FastF64, Z128FastNarrow>::type {
-    float W32[128];         // RN32(x_{i+1} / 2^24)
-    float Y32[128];         // RN32(y[i])
-    float DY32[128];        // RN32(y[i] - y[i+1])
-    double Wd[128];
-    double Y[128];
-};
 __device__ float d_z128_Y32[128];
 __device__ float d_z128_DY32[128];
-
-template <int DT>
-__device__ __forceinline__ void z128tab_load(Z128Tab<DT>& t) {
-    if constexpr (DT == ZIG_F64) {
-        for (int k = threadIdx.x; k < 256 * 8; k += blockDim.x) {
-            const int ix = k >> 3, i = ix & 127;
-            const double b = __dmul_rn(d_z128_W[i], 0x1p52);   // exact: a power-of-two scaling
-            const long long bb = __double_as_longlong(b);
-            t.T[ix][k & 7] = make_uint4((uint32_t)bb, (uint32_t)(bb >> 32), d_z128_kE[i] & 0xFFFFFFu,
-                                        ix < 128 ? 0x80000000u : 0u);
-        }
-    } else {
-        for (int k = threadIdx.x; k < 128 * 32; k += blockDim.x) t.K[k >> 5][k & 31] = d_z128_kE[k >> 5] & 0xFFFFFFu;
-    }
-    for (int i = threadIdx.x; i < 128; i += blockDim.x) {
-        t.W32[i] = d_z128_W32[i];
-        t.Y32[i] = d_z128_Y32[i];
-        t.DY32[i] = d_z128_DY32[i];
-        t.Wd[i] = d_z128_W[i];
-        t.Y[i] = d_z128_Y[i];
-    }
-}
 
 // RN(j * w) with one binary64 fma, given b = 2^52 w: a = 1 + j 2^-52 (built
 // from bits; j < 2^24) gives a b - b = j w exactly before the single rounding.
@@ -529,11 +394,6 @@ __device__ __forceinline__ bool z128_wedge_exact(const Tab& t, uint32_t i, uint3
     const double U = m53_to_double(m1);
     const double y = __dadd_rn(t.Y[i + 1], __dmul_rn(__dsub_rn(t.Y[i], t.Y[i + 1]), U));
     return y < exp(neg_half_sq(x));
-}
-template <class Tab>
-__device__ __forceinline__ bool z128_wedge_accept(const Tab& t, uint32_t i, uint32_t j, uint64_t m1) {
-    const int f = z128_wedge_filter(t, i, j, m1);
-    return f >= 0 ? f == 1 : z128_wedge_exact(t, i, j, m1);
 }
 
 // RN(z / R) without a division: q = RN(z RN(1/R)) and one fused multiply-add
@@ -574,10 +434,6 @@ __device__ __forceinline__ bool z128_tail_exact(uint64_t m1, uint64_t m2) {
     const double s = -div_by_R(zlog(m53_to_double(n1)));
     return zlog(m53_to_double(m2)) < __dmul_rn(__dmul_rn(-0.5, s), s);
 }
-__device__ __forceinline__ bool z128_tail_accept(uint64_t m1, uint64_t m2) {
-    const int f = z128_tail_filter(m1, m2);
-    return f >= 0 ? f == 1 : z128_tail_exact(m1, m2);
-}
 
 // The tail step's value for an accepted U1 = 1 - m1 2^-53: x = R - ln(U1)/R.
 __device__ __forceinline__ double z128_tail_value(uint64_t m1) {
@@ -585,733 +441,8 @@ __device__ __forceinline__ double z128_tail_value(uint64_t m1) {
     return __dsub_rn(zigtab::ZIG128_R, div_by_R(zlog(U1)));
 }
 
-// The tail step, inline and free of calls: the accepted x = R - ln(U1)/R, or -1
-// if rejected.
-__device__ __forceinline__ double z128_tail(uint64_t m1, uint64_t m2) {
-    if (!z128_tail_accept(m1, m2)) return -1.0;
-    return z128_tail_value(m1);
-}
-
-// Staging word per slot: binary64 bits, or binary32 bits (binary32 and bfloat16
-// outputs; bfloat16 is rounded at the store).  A deferred wedge's slot holds
-// its 32-bit draw w until it is decided.
-template <int DT> struct ZStage { using T = uint32_t; };
-template <> struct ZStage<ZIG_F64> { using T = uint64_t; };
-
-
-// The candidate of the 32-bit draw w (layer i = w & 127, positive when bit 7
-// is set, abscissa j = w >> 8): its staging word sign RN(j w[i]) and whether
-// it leaves the fast path (j >= k[i]).
-template <int DT>
-__device__ __forceinline__ typename ZStage<DT>::T z128_fast(const Z128Tab<DT>& t, uint32_t w, int lane,
-                                                             bool& slow) {
-    const uint32_t j = w >> 8;
-    if constexpr (DT == ZIG_F64) {
-        const uint4 e = t.T[w & 0xFFu][lane & 7];
-        slow = j >= e.z;
-        const double b = __hiloint2double((int)e.y, (int)e.x);
-        return (uint64_t)__double_as_longlong(mul_j_w(j, b)) | ((uint64_t)e.w << 32);
-    } else {
-        const uint32_t i = w & 0x7Fu;
-        slow = j >= t.K[i][lane];
-        return __float_as_uint(__fmul_rn((float)j, t.W32[i])) | ((~w << 24) & 0x80000000u);
-    }
-}
-
-template <int DT>
-__device__ __forceinline__ typename ZStage<DT>::T z128_value(const Z128Tab<DT>& t, uint32_t w, int lane) {
-    bool slow;
-    return z128_fast<DT>(t, w, lane, slow);
-}
-
-// A tail's staging word: x with the sign of the draw w.
-template <int DT>
-__device__ __forceinline__ typename ZStage<DT>::T z128_from64(double x, uint32_t w) {
-    const uint32_t neg = (~w >> 7) & 1u;
-    if constexpr (DT == ZIG_F64) return (uint64_t)__double_as_longlong(x) | ((uint64_t)neg << 63);
-    else return __float_as_uint(__double2float_rn(x)) | (neg << 31);
-}
-
-
-// Batch width (candidates per lane per batch): by default 32 slots with 4-byte
-// staging words and 20 with 8-byte words (the most that fits 24 warps' stages
-// in one SM's shared memory); half that is the other choice a launch
-// configuration can make.
-template <int DT> struct ZBatch { static constexpr int B = (DT == ZIG_F64) ? 20 : 32; };
-
-// The kind of wedge record a kernel instantiation keeps: L64X128Mix batches
-// draw every output with nextLong anyway and record that output; the other
-// generators record their cheaper snapshot (G::snap; Xoroshiro128PlusPlus's is
-// its output too).
-template <class G, int DT>
-constexpr bool kRecOut = std::is_same<G, GenL64X128Mix>::value;
-
-// Deferred wedges a lane may hold per batch (one 8-byte record each); a lane's
-// next wedge in the same batch is decided on the spot.  With 2.7 % wedges a
-// lane defers more than 4 of its 16 (32) candidates in about 6e-5 (3e-3) of
-// its batches.
-constexpr int kZRec = 4;
-
-template <class G, int DT, int BW>
-struct ZWarp {
-    static constexpr int B = BW;
-    using S = typename ZStage<DT>::T;
-    using OutT = typename OutOf<DT>::T;
-    static constexpr int EPS = 32 / (int)sizeof(OutT);   // output elements per 32-byte sector
-    // Row stride of the stage: binary64 rows hold the lane's carried values in
-    // columns 1..3 and the batch's slots from column 4, at an odd stride of
-    // 8-byte words (the 32 lanes' rows start on distinct banks); 4-byte rows
-    // are B wide and swizzled, with the carry kept apart (CW wide).
-    static constexpr int RS = sizeof(S) == 8 ? B + 5 : B;
-    static constexpr int CW = sizeof(S) == 8 ? 1 : (EPS == 8 ? 9 : 17);
-    S stage[32 * RS];
-    S carry[sizeof(S) == 8 ? 1 : 32 * CW];   // values a lane has not written yet (4-byte rows)
-    uint64_t rec[32][kZRec];              // each deferred wedge's uniform record (G::snap)
-    uint32_t list[32 * kZRec];            // the batch's deferred wedges: row | slot << 5 | record << 10
-    uint32_t rej[32];
-};
-
-// Slot (row, col) of the stage, laid out so that the 32 lanes writing column
-// col of their own rows, and the lanes of a row reading it, hit distinct
-// banks: 8-byte rows at an odd stride (B + 5 words, slots from column 4),
-// 4-byte rows swizzled.
-template <int B, typename S>
-__device__ __forceinline__ int zslot(int row, int col) {
-    static_assert(sizeof(S) == 8 ? (B == 20 || B == 10) : (B == 32 || B == 16), "unsupported batch width");
-    if constexpr (sizeof(S) == 8) return row * (B + 5) + 4 + col;
-    else if constexpr (B == 32) return row * 32 + (col ^ row);
-    else return row * 16 + (col ^ ((row >> 1) & 15));
-}
-
-constexpr int kZBlock = 768;              // the default block: 24 warps, one block per SM
-constexpr int kZWarps = kZBlock / 32;     // the most warps a block may have
-
-template <class G, int DT, int BW = ZBatch<DT>::B>
-__host__ __device__ constexpr size_t z128_warp_bytes() {
-    return (sizeof(ZWarp<G, DT, BW>) + 15) & ~(size_t)15;
-}
-
-// Phase C, lane-per-row form: each lane writes its own row's accepted values,
-// in output order, as whole 32-byte sectors (one 256-bit store each), after the
-// values it carried over from its previous batch.  What does not fill a sector
-// is carried to the lane's next batch; element stores remain only before the
-// first sector boundary of a unit and at the unit's end.  (A GB300 writes
-// per-lane full sectors at nearly the rate of coalesced warp stores, but
-// partial-sector stores from many lanes at a fraction of it.)
-template <typename OutT, typename S>
-__device__ __forceinline__ void z128_store1(OutT* p, S z) {
-    if constexpr (sizeof(OutT) == 8) __stcs((unsigned long long*)p, (unsigned long long)z);
-    else if constexpr (sizeof(OutT) == 4) __stcs((unsigned int*)p, (unsigned int)z);
-    else __stcs((unsigned short*)p, f32_to_bf16_bits(__uint_as_float((uint32_t)z)));
-}
-
-template <typename OutT, typename S, int EPS>
-__device__ __forceinline__ void z128_store_sector(OutT* p, const S (&v)[EPS]) {
-    uint64_t q[4];
-    if constexpr (sizeof(OutT) == 8) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) q[k] = (uint64_t)v[k];
-    } else if constexpr (sizeof(OutT) == 4) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) q[k] = (uint64_t)(uint32_t)v[2 * k] | ((uint64_t)(uint32_t)v[2 * k + 1] << 32);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint64_t w = 0;
-#pragma unroll
-            for (int h = 0; h < 4; ++h)
-                w |= (uint64_t)f32_to_bf16_bits(__uint_as_float((uint32_t)v[4 * k + h])) << (16 * h);
-            q[k] = w;
-        }
-    }
-    asm volatile("st.global.cs.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(q[0]), "l"(q[1]), "l"(q[2]),
-                 "l"(q[3])
-                 : "memory");
-}
-
-// Writes the lane's nc carried values (carry[0..nc)) and the row's accepted
-// slots (the `produced` slots minus the rejected ones in rj) from dst on.
-// Advances dst past what was written and leaves the rest in carry / nc, or
-// writes everything when the unit ends with this batch.
-template <int B, int EPS, int CW, typename S, typename OutT>
-__device__ __forceinline__ void z128_flush_lane(const S* stage, S* carry, int lane, uint32_t rj, int n_acc,
-                                                bool unit_end, OutT*& dst, int& nc) {
-    constexpr int ESZ = (int)sizeof(OutT);
-    const int total = nc + n_acc;
-    const int mis = (int)(((uintptr_t)dst & 31) / ESZ);   // nonzero only at a unit's start
-    const int h = umin64(mis ? EPS - mis : 0, total);       // elements before the first boundary
-    const int body = (total - h) / EPS;                     // whole sectors
-    const int tail = total - h - body * EPS;
-    S* const cr = carry + lane * CW;
-    int e = 0;                                              // next element, in output order
-    int src = 0;                                            // next stage slot to read
-    while (((uint64_t)rj >> src) & 1u) ++src;
-    auto next = [&]() -> S {
-        S z;
-        if (e < nc) {
-            z = cr[e];
-        } else {
-            z = stage[zslot<B, S>(lane, src)];
-            ++src;
-            while (((uint64_t)rj >> src) & 1u) ++src;
-        }
-        ++e;
-        return z;
-    };
-    for (int k = 0; k < h; ++k) z128_store1<OutT, S>(dst + k, next());
-    OutT* p = dst + h;
-    for (int q = 0; q < body; ++q) {
-        S v[EPS];
-#pragma unroll
-        for (int k = 0; k < EPS; ++k) v[k] = next();
-        z128_store_sector<OutT, S, EPS>(p, v);
-        p += EPS;
-    }
-    // the remainder: written if the unit ends, else carried (position k <= e:
-    // a carried value is never overwritten before it is read)
-    for (int k = 0; k < tail; ++k) {
-        const S z = next();
-        if (unit_end) z128_store1<OutT, S>(p + k, z);
-        else cr[k] = z;
-    }
-    dst = unit_end ? p + tail : p;
-    nc = unit_end ? 0 : tail;
-}
-
-// Phase C for binary64 rows, lane-per-row form.  The lane's row holds the nc
-// values carried over from its previous batch in columns 4 - nc .. 3 and the
-// batch's slots from column 4, so its output sequence (the carry, then the
-// accepted slots) is contiguous but for rejected slots.  A lane with one
-// rejected slot reads around it; one with more first closes them up.  The
-// lane writes whole 32-byte sectors, one 256-bit store each; element stores
-// remain only before the first sector boundary of a unit and at its end;
-// the rest (at most 3 values) moves to columns 4 - nc' .. 3 for the next batch
-// (each value moves left or stays, in ascending order, so none is overwritten
-// before it is read).
-template <int B, bool kAligned>
-__device__ __forceinline__ void z128_flush_f64_body(uint64_t* row, int t, int total, bool unit_end,
-                                                    double*& dst, int& nc) {
-    const uint64_t* const s0 = row + 4 - nc;   // sequence element e: s0[e], or s0[e + 1] from e >= t
-    const uint64_t* const s1 = s0 + 1;
-    int e0 = 0;
-    if constexpr (!kAligned) {   // a unit's first batch may start inside a sector
-        const int mis = (int)(((uintptr_t)dst & 31) >> 3);
-        e0 = umin64(mis ? 4 - mis : 0, total);
-        for (int k = 0; k < e0; ++k) __stcs((unsigned long long*)dst + k, (k >= t ? s1 : s0)[k]);
-        dst += e0;
-    }
-    const int nsec = (total - e0) >> 2;
-    constexpr int kMaxSec = (B + 3) / 4;
-#pragma unroll
-    for (int q = 0; q < kMaxSec; ++q) {
-        if (q < nsec) {
-            uint64_t v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int e = e0 + 4 * q + k;
-                v[k] = (e >= t ? s1 : s0)[e];
-            }
-            z128_store_sector<double, uint64_t, 4>(dst + 4 * q, v);
-        }
-    }
-    const int rest = total - e0 - 4 * nsec;
-    const int eb = e0 + 4 * nsec;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if (k < rest) {
-            const int e = eb + k;
-            const uint64_t z = (e >= t ? s1 : s0)[e];
-            if (unit_end) __stcs((unsigned long long*)dst + 4 * nsec + k, z);
-            else row[4 - rest + k] = z;
-        }
-    }
-    dst += 4 * nsec + (unit_end ? rest : 0);
-    nc = unit_end ? 0 : rest;
-}
-
-template <int B>
-__device__ __forceinline__ void z128_flush_f64(uint64_t* row, uint32_t rj, int produced, int acc,
-                                               bool unit_end, double*& dst, int& nc) {
-    if (__any_sync(kFull, (rj & (rj - 1)) != 0)) {
-        if (rj & (rj - 1)) {   // two or more rejected slots: close them up in place
-            int d = __ffs(rj) - 1;
-            for (int c = d + 1; c < produced; ++c)
-                if (!((rj >> c) & 1u)) row[4 + d++] = row[4 + c];
-            rj = 0;
-        }
-    }
-    const int t = rj ? nc + __ffs(rj) - 1 : 1 << 30;   // the one rejected slot's sequence index
-    const int total = nc + acc;
-    if (__any_sync(kFull, ((uintptr_t)dst & 31) != 0))
-        z128_flush_f64_body<B, false>(row, t, total, unit_end, dst, nc);
-    else
-        z128_flush_f64_body<B, true>(row, t, total, unit_end, dst, nc);
-}
-
-// Resolve a slow draw w (j >= k[i]) of slot v.  A wedge is deferred to phase B
-// (its slot keeps w and the generator's record of
-// the test's uniform goes to rec) unless the lane already holds kZRec records
-// in this batch; a tail, or a wedge that is not deferred, is decided here, and
-// a rejected one draws again for the same slot.  Returns the slot's word.
-template <class G, int DT, class W>
-__device__ __forceinline__ typename ZStage<DT>::T z128_slow(G& g, const Z128Tab<DT>& t, W& ws,
-                                                             int lane, int v, uint32_t w,
-                                                             uint32_t& drel, uint32_t& smask) {
-    using S = typename ZStage<DT>::T;
-    for (;;) {
-        const uint32_t i = w & 0x7Fu;
-        if (i < 127) {
-            const int nw = __popc(smask);
-            if (nw < kZRec) {
-                ws.rec[lane][nw] = g.template snap<kRecOut<G, DT>>();   // record the uniform, move past it
-                drel += G::kStepsPerDouble;
-                smask |= 1u << v;
-                return (S)w;
-            }
-            const uint64_t mu = g.next_m53();
-            drel += G::kStepsPerDouble;
-            if (z128_wedge_accept(t, i, w >> 8, mu)) return z128_value<DT>(t, w, lane);
-        } else {
-            const uint64_t m1 = g.next_m53();
-            const uint64_t m2 = g.next_m53();
-            drel += 2 * G::kStepsPerDouble;
-            const double x = z128_tail(m1, m2);
-            if (x >= 0.0) return z128_from64<DT>(x, w);
-        }
-        // rejected: the next draw is for the same slot
-        w = g.next_u32();
-        ++drel;
-        bool slow;
-        const S val = z128_fast<DT>(t, w, lane, slow);
-        if (!slow) return val;
-    }
-}
-
-// MODE 0: generation into a.out; MODE 1: mutation x += sigma * z (binary32);
-// MODE 2: a batch of mutation requests (a.reqs), each row with its own sigma.
-// BW is the batch width; the block may have any whole number of warps up to
-// kZWarps, each with its own z128_warp_bytes of dynamic shared memory.
-template <int PRNG, int DT, int MODE, int BW = ZBatch<DT>::B>
-__global__ void __launch_bounds__(kZBlock, 1) z128_kernel(GenArgs a) {
-    using G = typename GenOf<PRNG>::T;
-    using S = typename ZStage<DT>::T;
-    using OutT = typename OutOf<DT>::T;
-    using W = ZWarp<G, DT, BW>;
-    constexpr int B = W::B;
-    __shared__ Z128Tab<DT> t;
-    extern __shared__ __align__(16) unsigned char z128_dsm[];
-    z128tab_load(t);
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt_mask = (1u << lane) - 1u;   // the lanes below this one
-    const int wib = threadIdx.x >> 5;
-    const int n_warps = blockDim.x >> 5;
-    W& ws = *(W*)(z128_dsm + (size_t)wib * z128_warp_bytes<G, DT, BW>());
-    if (MODE == 0 && a.out == nullptr) {   // only legal when every length is zero
-        if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0)
-            atomicOr(a.err, kErrNullOutput);
-        return;
-    }
-    const uint64_t n_units = units_total(a);
-    const uint64_t n_groups = (n_units + 31) >> 5;
-    const uint64_t warp_id = (uint64_t)blockIdx.x * n_warps + wib;
-    const uint64_t warp_stride = (uint64_t)gridDim.x * n_warps;
-    OutT* out = (OutT*)a.out;
-
-    for (uint64_t grp = warp_id; grp < n_groups; grp += warp_stride) {
-        const uint64_t u = grp * 32 + lane;
-        uint64_t rem = 0;
-        OutT* dst = out;
-        G g;
-        g.seed(0);
-        float sigma = a.sigma;
-        uint32_t kind = ZIG_REQ_MUTATE;
-        zig_stream_state* srec = nullptr;   // the record to advance at the unit's end
-        if (u < n_units) {
-            bool ok = true;
-            if constexpr (MODE == 2) {
-                // batched mutation: the request holding unit u (the last with ustart <= u)
-                uint32_t lo = 0, hi = a.n_req;
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (a.reqs[mid].ustart <= u) lo = mid; else hi = mid;
-                }
-                const MutDesc& r = a.reqs[lo];
-                const uint64_t ur = u - r.ustart, p = ur / r.upr, qd = ur - p * r.upr;
-                if (r.state) {   // one unit per row, continuing its record
-                    if (state_load<PRNG>(r.state + p, g, a.err, ok)) srec = r.state + p;
-                } else {
-                    g.seed(r.seed + p);
-                    if (qd) g.jump(qd * kChunkDraws, &d_jump);
-                }
-                const uint64_t t0 = qd << 10;
-                if (ok) {
-                    rem = r.state ? r.L : umin64(r.L - t0, 1024);
-                    dst = (OutT*)(r.x + p * r.L + t0);
-                }
-                sigma = r.sigma;
-                kind = r.kind;
-            } else {
-                uint64_t s, qd, off, n;
-                unit_info(a, u, s, qd, off, n);
-                if (a.state) {
-                    srec = unit_gen<PRNG>(a, s, 0, g, ok);
-                } else {
-                    g.seed(MODE == 0 ? a.seeds[s] : a.mut_seed + s);   // mutation: seed + row
-                    if (qd) g.jump(qd * kChunkDraws, &d_jump);
-                }
-                if (ok) {
-                    rem = n;
-                    dst = out + off;
-                }
-            }
-        }
-        uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
-        int nc = 0;           // values carried to the next batch (lane-per-row flush)
-        const bool check_chunk = srec == nullptr && (MODE == 2 || a.chunk_log2 != 0) && rem != 0;
-        const bool any_out = rem != 0;
-
-        while (__any_sync(kFull, rem > 0)) {
-            ws.rej[lane] = 0;
-            uint32_t drel = 0, smask = 0;
-            int produced;
-            // ---- A: draw the batch's candidates ----
-            if ((PRNG == ZIG_L64X128MIX || PRNG == ZIG_XOROSHIRO128PP) &&
-                __all_sync(kFull, rem >= (uint64_t)B)) {
-                // L64X128Mix and Xoroshiro128PlusPlus: nextInt and nextDouble are both
-                // cut from nextLong, so a deferred wedge's uniform is simply the next
-                // output.  Every iteration takes one output: a candidate, or the record
-                // of the wedge deferred just before.  No lane ever steps its generator
-                // in a divergent branch for a wedge; a lane ends the batch with B minus
-                // its deferred wedges candidates.  The iteration after a deferral runs
-                // the candidate code too, with its results discarded, so that the loop
-                // has no divergent branch but the rare slow draws'.
-                int slot = 0, nw = 0;
-                bool pend = false;
-#pragma unroll 2
-                for (int it = 0; it < B; ++it) {
-                    const uint64_t r = g.next_u64();   // this output is its own record
-                    if (pend) ws.rec[lane][nw - 1] = r;   // the uniform of the wedge just deferred
-                    const uint32_t w = (uint32_t)(r >> 32);   // nextInt
-                    bool slow;
-                    S val = z128_fast<DT>(t, w, lane, slow);
-                    slow = slow && !pend;
-                    const bool wedge = slow && (w & 0x7Fu) != 0x7Fu && nw < kZRec;
-                    if (wedge) {
-                        smask |= 1u << slot;
-                        val = (S)w;
-                    }
-                    const bool other = slow && !wedge;   // a tail, or no record left
-                    if (__any_sync(kFull, other)) {
-                        if (other) {
-                            val = z128_slow<G, DT>(g, t, ws, lane, slot, w, drel, smask);
-                            nw = __popc(smask);
-                        }
-                    }
-                    // a discarded iteration's word goes to the next free slot (in
-                    // range: slot <= it) and is overwritten or never read
-                    ws.stage[zslot<B, S>(lane, slot)] = val;
-                    slot += pend ? 0 : 1;
-                    nw += wedge ? 1 : 0;
-                    pend = wedge;
-                }
-                drel += B;
-                if (pend) {   // the last candidate was a deferred wedge: its uniform is next
-                    ws.rec[lane][nw - 1] = g.next_u64();
-                    ++drel;
-                }
-                produced = slot;
-            } else if (__all_sync(kFull, rem >= (uint64_t)B)) {
-                // full batch: B candidates per lane, one warp vote per candidate guarding
-                // the rare slow draws (unrolled by two: deeper unrolling copies the slow
-                // handler into the instruction stream and costs more than it saves)
-                int nw = 0;
-#pragma unroll 2
-                for (int v = 0; v < B; ++v) {
-                    const uint32_t w = g.next_u32();
-                    bool slow;
-                    S val = z128_fast<DT>(t, w, lane, slow);
-                    bool other = slow;   // what needs the divergent slow handler
-                    if constexpr (PRNG == ZIG_LCG48 || PRNG == ZIG_SPLITMIX64) {
-                        // a wedge is deferred without a branch: recording its uniform
-                        // and stepping past it cost a few predicated instructions
-                        // (the 64-bit generators' steps are too long to run predicated
-                        // on every candidate)
-                        const bool wedge = slow && (w & 0x7Fu) != 0x7Fu && nw < kZRec;
-                        if (wedge) {
-                            ws.rec[lane][nw] = g.template snap<kRecOut<G, DT>>();
-                            drel += G::kStepsPerDouble;
-                            smask |= 1u << v;
-                            val = (S)w;
-                        }
-                        nw += wedge ? 1 : 0;
-                        other = slow && !wedge;
-                    }
-                    if (__any_sync(kFull, other)) {
-                        if (other) {
-                            val = z128_slow<G, DT>(g, t, ws, lane, v, w, drel, smask);
-                            nw = __popc(smask);
-                        }
-                    }
-                    ws.stage[zslot<B, S>(lane, v)] = val;
-                }
-                drel += B;
-                produced = B;
-            } else {
-                // the end of some streams: up to min(rem, B) candidates per lane
-                const int cnt = (int)umin64(rem, (uint64_t)B);
-                produced = 0;
-#pragma unroll 1
-                for (int v = 0; v < B; ++v) {
-                    if (v < cnt) {
-                        const uint32_t w = g.next_u32();
-                        ++drel;
-                        bool slow;
-                        S val = z128_fast<DT>(t, w, lane, slow);
-                        if (slow) val = z128_slow<G, DT>(g, t, ws, lane, v, w, drel, smask);
-                        ws.stage[zslot<B, S>(lane, v)] = val;
-                        produced = v + 1;
-                    }
-                }
-            }
-            draws += drel;
-            // ---- B: decide the deferred wedges, 32 at a time ----
-            // List them (row, slot, the row's record index), the k-th of every
-            // row in round k, one warp vote per round; then lane r decides entry r.
-            int total = 0;
-            {
-                uint32_t m = smask;
-                int k = 0;
-                for (;;) {
-                    const uint32_t bal = __ballot_sync(kFull, m != 0);
-                    if (bal == 0) break;
-                    if (m) {
-                        ws.list[total + __popc(bal & lt_mask)] = (uint32_t)lane | (uint32_t)(__ffs(m) - 1) << 5 |
-                                                                 (uint32_t)k << 10;
-                        m &= m - 1;
-                    }
-                    total += __popc(bal);
-                    ++k;
-                }
-            }
-            if (total) {
-                __syncwarp();
-                for (int base = 0; base < total; base += 32) {
-                    const int r = base + lane;
-                    if (r < total) {
-                        const uint32_t en = ws.list[r];
-                        const int o = (int)(en & 31u), slot = (int)((en >> 5) & 31u), kr = (int)(en >> 10);
-                        const uint32_t w = (uint32_t)ws.stage[zslot<B, S>(o, slot)];   // the deferred draw
-                        if (z128_wedge_accept(t, w & 0x7Fu, w >> 8, G::template m53_of<kRecOut<G, DT>>(ws.rec[o][kr])))
-                            ws.stage[zslot<B, S>(o, slot)] = z128_value<DT>(t, w, lane);
-                        else
-                            atomicOr(&ws.rej[o], 1u << slot);
-                    }
-                }
-            }
-            __syncwarp();
-            // ---- C: write the rows, skipping rejected slots ----
-            const uint32_t rj = ws.rej[lane];
-            const int acc = produced - __popc(rj);
-            rem -= (uint64_t)acc;
-            if (MODE == 0 && a.lane_sectors) {
-                if constexpr (sizeof(S) == 8)
-                    z128_flush_f64<B>(ws.stage + lane * W::RS, rj, produced, acc, rem == 0, dst, nc);
-                else
-                    z128_flush_lane<B, W::EPS, W::CW, S, OutT>(ws.stage, ws.carry, lane, rj, acc, rem == 0, dst, nc);
-            } else {
-                // warp-cooperative: B lanes per row, one element each; the row's
-                // pointer, count, rejections (and sigma, kind) come from its lane.
-                // kRowsPerStep rows per step; when B does not divide 32 the lanes
-                // past kRowsPerStep * B idle, and so do the rows past 31 in the last step.
-                constexpr int kRowsPerStep = 32 / B;
-                constexpr int kSteps = (32 + kRowsPerStep - 1) / kRowsPerStep;
-                const int sub = lane / B, c = lane % B;
-                if constexpr (MODE != 0) {
-                    static_assert(32 % B == 0, "mutation batches are 32 or 16 wide");
-                    // read-modify-write of x, four row-steps at a time: their loads of x
-                    // are issued before any of their stores, so the loads overlap.  Each
-                    // element of x is read once, before this thread writes it, and never
-                    // read again, so the read-only load path is safe.
-                    constexpr int kG = 8;
-#pragma unroll 1
-                    for (int k0 = 0; k0 < 32 / kRowsPerStep; k0 += kG) {
-                        float* rdp[kG];
-                        float zf[kG], xv[kG], sg[kG];
-                        bool ok[kG], gen[kG];
-#pragma unroll
-                        for (int u = 0; u < kG; ++u) {
-                            const int row = kRowsPerStep * (k0 + u) + sub;
-                            rdp[u] = (float*)__shfl_sync(kFull, (unsigned long long)dst, row);
-                            const int rcnt = __shfl_sync(kFull, acc, row);
-                            const uint32_t rrej = __shfl_sync(kFull, rj, row);
-                            sg[u] = __shfl_sync(kFull, sigma, row);
-                            const uint32_t rkind = __shfl_sync(kFull, kind, row);
-                            gen[u] = MODE == 2 && rkind == ZIG_REQ_GENERATE;
-                            ok[u] = c < rcnt;
-                            int src = c;   // slot of the row's c-th accepted candidate
-                            for (uint32_t m = rrej; m; m &= m - 1) {
-                                if (__ffs(m) - 1 <= src) ++src;
-                                else break;
-                            }
-                            if (!ok[u]) src = 0;   // keep the stage read in range
-                            zf[u] = __uint_as_float((uint32_t)ws.stage[zslot<B, S>(row, src)]);
-                            xv[u] = 0.0f;
-                            if (ok[u] && !gen[u]) xv[u] = __ldg(rdp[u] + c);
-                        }
-#pragma unroll
-                        for (int u = 0; u < kG; ++u)
-                            if (ok[u]) rdp[u][c] = gen[u] ? zf[u] : fmaf(sg[u], zf[u], xv[u]);
-                    }
-                } else {
-#pragma unroll 4
-                    for (int k = 0; k < kSteps; ++k) {
-                        const int rw = kRowsPerStep * k + sub;
-                        const bool in = sub < kRowsPerStep && rw < 32;
-                        const int row = in ? rw : 0;   // every lane takes part in the shuffles
-                        OutT* const rd = (OutT*)__shfl_sync(kFull, (unsigned long long)dst, row);
-                        const int rcnt = __shfl_sync(kFull, acc, row);
-                        const uint32_t rrej = __shfl_sync(kFull, rj, row);
-                        if (in && c < rcnt) {
-                            int src = c;   // slot of the row's c-th accepted candidate
-                            for (uint32_t m = rrej; m; m &= m - 1) {
-                                if (__ffs(m) - 1 <= src) ++src;
-                                else break;
-                            }
-                            // write-once output: streaming store
-                            z128_store1<OutT, S>(rd + c, ws.stage[zslot<B, S>(row, src)]);
-                        }
-                    }
-                }
-                dst += acc;
-            }
-            __syncwarp();
-        }
-        if (check_chunk && draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
-        // every draw of a lane is one of its candidates or their uniforms, so g
-        // stands at the stream's next draw
-        if (srec && any_out) state_store(srec, g, false, 0.0);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// modified ziggurat (McFarland), binary64, batched
-// ---------------------------------------------------------------------------
-// The batch layout of z128_kernel: each lane owns a unit and writes its row of
-// B values (the carry in front) with the binary64 lane flush.  In phase A a lane
-// takes one nextLong U per iteration.  A fast draw (j = U & 255 < 253) gives
-// XS[j] m with m = U >> 11 < 2^53 (XS[j] = X[j] 2^-53), in one fused multiply-add:
-// with X' = XS[j] 2^52, m = h 2^52 + l and a = 1 + l 2^-52 (built from bits),
-// fma(a, X', h ? 0 : -X') = X' (l 2^-52 + h) = XS[j] m exactly before its one
-// rounding.  The table holds -X', so that both the addend and the multiplicand
-// come without a separate negation (a binary64 add on the narrow FP64 pipe).
-// A slow draw (an overhang or the tail, 1.2 % of draws) stops the lane for the
-// rest of the batch, its generator standing just after the draw; after the loop
-// each stopped lane finishes that draw's slow path, one divergent pass per batch
-// (inline, a warp would run it in about every third iteration).  No slot is
-// rejected afterwards, so the rows have no holes.
-struct Z256Fast {
-    double XN[256][16];   // -XS[j] 2^52, 16 copies (a half warp reads without conflicts)
-};
-constexpr int kZ256Row = ZBatch<ZIG_F64>::B + 5;   // row stride in 8-byte words: carry in 1..3, slots from 4
-
-__host__ __device__ constexpr size_t z256_warp_bytes() { return (size_t)32 * kZ256Row * sizeof(uint64_t); }
-
-template <int PRNG>
-__global__ void __launch_bounds__(kZBlock, 1) z256_kernel(GenArgs a) {
-    using G = typename GenOf<PRNG>::T;
-    constexpr int B = ZBatch<ZIG_F64>::B;
-    constexpr uint32_t kSteps64 = PRNG == ZIG_LCG48 ? 2u : 1u;   // raw steps of one nextLong
-    __shared__ Z256Smem t;
-    __shared__ Z256Fast f;
-    extern __shared__ __align__(16) unsigned char z256_dsm[];
-    z256_load(t);
-    for (int k = threadIdx.x; k < 256 * 16; k += blockDim.x) f.XN[k >> 4][k & 15] = __dmul_rn(d_z256_XS[k >> 4], -0x1p52);
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int n_warps = blockDim.x >> 5;
-    uint64_t* const row = (uint64_t*)(z256_dsm + (size_t)wib * z256_warp_bytes()) + lane * kZ256Row;
-    if (a.out == nullptr) {   // only legal when every length is zero
-        if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0)
-            atomicOr(a.err, kErrNullOutput);
-        return;
-    }
-    const uint64_t n_units = units_total(a);
-    const uint64_t n_groups = (n_units + 31) >> 5;
-    const uint64_t warp_id = (uint64_t)blockIdx.x * n_warps + wib;
-    const uint64_t warp_stride = (uint64_t)gridDim.x * n_warps;
-    double* const out = (double*)a.out;
-
-    for (uint64_t grp = warp_id; grp < n_groups; grp += warp_stride) {
-        const uint64_t u = grp * 32 + lane;
-        uint64_t rem = 0;
-        double* dst = out;
-        G g;
-        g.seed(0);
-        zig_stream_state* srec = nullptr;
-        if (u < n_units) {
-            uint64_t s, q, off, n;
-            unit_info(a, u, s, q, off, n);
-            bool ok;
-            srec = unit_gen<PRNG>(a, s, q, g, ok);
-            if (ok) {
-                rem = n;
-                dst = out + off;
-            }
-        }
-        const bool check_chunk = a.chunk_log2 != 0 && rem != 0;
-        const bool any_out = rem != 0;
-        uint64_t draws = 0;   // raw steps used by this unit (chunk-overflow check)
-        int nc = 0;           // values carried to the next batch
-        while (__any_sync(kFull, rem > 0)) {
-            const int cnt = (int)umin64(rem, (uint64_t)B);
-            int slot = 0;
-            bool stopped = false;
-            uint64_t pend = 0;   // a stopped lane's slow draw
-#pragma unroll 2
-            for (int it = 0; it < B; ++it) {
-                // a lane draws while it has not stopped and still needs values
-                const bool act = !stopped && slot < cnt;
-                G gn = g;
-                const uint64_t U = gn.next_u64();
-                if (act) g = gn;
-                const uint32_t j = (uint32_t)U & 0xFFu;
-                const uint64_t m = U >> 11;
-                const uint32_t mh = (uint32_t)(m >> 32);
-                const double xn = f.XN[j][lane & 15];
-                const double av = __hiloint2double((int)(0x3FF00000u | (mh & 0xFFFFFu)), (int)(uint32_t)m);
-                const double x = __fma_rn(av, -xn, (mh >> 20) ? 0.0 : xn);
-                const bool fast = j < (uint32_t)zigtab::ZIG256_NR;
-                if (act && fast) row[4 + slot] = (uint64_t)__double_as_longlong(x) | ((U >> 8) & 1u) << 63;
-                slot += (act && fast) ? 1 : 0;
-                if (act && !fast) {
-                    stopped = true;
-                    pend = U;
-                }
-            }
-            draws += (uint64_t)kSteps64 * (uint64_t)(slot + (stopped ? 1 : 0));   // one nextLong per active iteration
-            if (__any_sync(kFull, stopped)) {
-                if (stopped) {
-                    uint32_t extra = 0;
-                    const double x = z256_slow(g, t, extra);   // x >= 0
-                    draws += extra;
-                    row[4 + slot] = (uint64_t)__double_as_longlong(x) | ((pend >> 8) & 1u) << 63;
-                    ++slot;
-                }
-            }
-            rem -= (uint64_t)slot;
-            z128_flush_f64<B>(row, 0u, slot, slot, rem == 0, dst, nc);
-        }
-        if (check_chunk && draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
-        // a lane draws only while it needs values, so g stands at the stream's next draw
-        if (srec && any_out) state_store(srec, g, false, 0.0);
-    }
-}
-
 #include "z128_f64.cuh"
+#include "z256_batch.cuh"
 
 // Exhaustive check of the fast path's arithmetic against CUDA's IEEE operations:
 // RN(j * w[i]) by the fused multiply-add construction against __dmul_rn for all
@@ -1345,6 +476,13 @@ __global__ void __launch_bounds__(256) selfcheck_kernel(unsigned long long* coun
         }
         n_p += 5;
         const double u = m53_to_double(((k * 0x9E3779B97F4A7C15ull) >> 11) | 1u);   // in (0, 1)
+        // the binary64 -> binary32 rounding of the narrow outputs, on u scaled into [2^-60, 8)
+        {
+            const double v = __dmul_rn(u, __longlong_as_double((long long)(0x3C3ull + (k % 64)) << 52));
+            bad_b += f64_to_f32_bits(v) != __float_as_uint(__double2float_rn(v));
+            bad_b += f64_to_f32_bits(-v) != __float_as_uint(__double2float_rn(-v));
+            n_b += 2;
+        }
         const long long dl = __double_as_longlong(zlog(u)) - __double_as_longlong(log(u));
         far_l += dl > 1 || dl < -1;
         ne_l += dl != 0;
@@ -1588,68 +726,45 @@ static GenFn pick_zf(int fma) {
 }
 
 template <int ALG, int PRNG>
-static GenFn pick_dt(int dt, bool half_batch, int fma) {
+static GenFn pick_dt(int dt, int fma) {
     if constexpr (ALG == ZIG_ZIG128) {
         switch (dt) {
         case ZIG_F64: return pick_zf<PRNG>(fma);
         case ZIG_F32: return zf::z128f_kernel<PRNG, ZIG_F32, 4>;
         default: return zf::z128f_kernel<PRNG, ZIG_BF16, 4>;
         }
+    } else if constexpr (ALG == ZIG_ZIG256) {
+        switch (dt) {
+        case ZIG_F64: return zb::z256b_kernel<PRNG, ZIG_F64>;
+        case ZIG_F32: return zb::z256b_kernel<PRNG, ZIG_F32>;
+        default: return zb::z256b_kernel<PRNG, ZIG_BF16>;
+        }
     } else {
         switch (dt) {
-        case ZIG_F64: return ALG == ZIG_ZIG256 ? z256_kernel<PRNG> : gen_kernel<ALG, PRNG, ZIG_F64>;
+        case ZIG_F64: return gen_kernel<ALG, PRNG, ZIG_F64>;
         case ZIG_F32: return gen_kernel<ALG, PRNG, ZIG_F32>;
         default: return gen_kernel<ALG, PRNG, ZIG_BF16>;
         }
     }
 }
 template <int ALG>
-static GenFn pick_prng(int prng, int dt, bool half_batch, int fma) {
+static GenFn pick_prng(int prng, int dt, int fma) {
     switch (prng) {
-    case ZIG_LCG48: return pick_dt<ALG, 0>(dt, half_batch, fma);
-    case ZIG_SPLITMIX64: return pick_dt<ALG, 1>(dt, half_batch, fma);
-    case ZIG_L64X128MIX: return pick_dt<ALG, 2>(dt, half_batch, fma);
-    default: return pick_dt<ALG, 3>(dt, half_batch, fma);
+    case ZIG_LCG48: return pick_dt<ALG, 0>(dt, fma);
+    case ZIG_SPLITMIX64: return pick_dt<ALG, 1>(dt, fma);
+    case ZIG_L64X128MIX: return pick_dt<ALG, 2>(dt, fma);
+    default: return pick_dt<ALG, 3>(dt, fma);
     }
 }
-static GenFn pick(int alg, int prng, int dt, bool half_batch = false, int fma = 4) {
+static GenFn pick(int alg, int prng, int dt, int fma) {
     switch (alg) {
-    case ZIG_ZIG128: return pick_prng<ZIG_ZIG128>(prng, dt, half_batch, fma);
-    case ZIG_POLAR: return pick_prng<ZIG_POLAR>(prng, dt, false, fma);
-    default: return pick_prng<ZIG_ZIG256>(prng, dt, false, fma);
+    case ZIG_ZIG128: return pick_prng<ZIG_ZIG128>(prng, dt, fma);
+    case ZIG_POLAR: return pick_prng<ZIG_POLAR>(prng, dt, fma);
+    default: return pick_prng<ZIG_ZIG256>(prng, dt, fma);
     }
 }
 
-// Dynamic shared memory a kernel needs (0 for the kernels that use static only).
-// Every instantiation must fit one SM's shared memory (227 KB per block).
-template <class G, int DT>
-constexpr bool z128_fits() {   // the default batch width is the larger one
-    return z128_warp_bytes<G, DT>() * kZWarps + sizeof(Z128Tab<DT>) <= 227 * 1024;
-}
-static_assert(z128_fits<GenLcg48, ZIG_F64>() && z128_fits<GenLcg48, ZIG_F32>() &&
-                  z128_fits<GenLcg48, ZIG_BF16>() && z128_fits<GenSplitMix64, ZIG_F64>() &&
-                  z128_fits<GenSplitMix64, ZIG_F32>() && z128_fits<GenSplitMix64, ZIG_BF16>() &&
-                  z128_fits<GenL64X128Mix, ZIG_F64>() && z128_fits<GenL64X128Mix, ZIG_F32>() &&
-                  z128_fits<GenL64X128Mix, ZIG_BF16>() && z128_fits<GenXoroshiro128PP, ZIG_F64>() &&
-                  z128_fits<GenXoroshiro128PP, ZIG_F32>() && z128_fits<GenXoroshiro128PP, ZIG_BF16>(),
-              "z128_kernel shared memory exceeds 227 KB per block");
-static_assert(sizeof(Z256Smem) + sizeof(Z256Fast) + z256_warp_bytes() * kZWarps <= 227 * 1024,
-              "z256_kernel shared memory exceeds 227 KB per block");
-
-// Exactly the per-warp bytes the kernel instantiation for (G, dt, batch width)
-// indexes (its carry rows depend on the output type, not only the staging word).
-template <class G>
-static size_t z128_dyn_for(int dt, bool half_batch, int warps) {
-    size_t per;
-    switch (dt) {
-    case ZIG_F64: per = half_batch ? z128_warp_bytes<G, ZIG_F64, 10>() : z128_warp_bytes<G, ZIG_F64>(); break;
-    case ZIG_F32: per = half_batch ? z128_warp_bytes<G, ZIG_F32, 16>() : z128_warp_bytes<G, ZIG_F32>(); break;
-    default: per = half_batch ? z128_warp_bytes<G, ZIG_BF16, 16>() : z128_warp_bytes<G, ZIG_BF16>(); break;
-    }
-    return per * (size_t)warps;
-}
-
-// Shared memory of the binary64 128-level kernel: tables plus one warp area per warp.
+// Shared memory of the 128-level batch kernel: tables plus one warp area per warp.
 template <int DT>
 static size_t zf_smem_dt(int prng, int warps) {
     switch (prng) {
@@ -1671,18 +786,11 @@ static int zf_max_block(int prng, int dt) {
     return 32 * w;
 }
 
-static size_t dyn_smem_of(int alg, int dt, int prng, bool half_batch = false, int block = kZBlock,
-                          bool mutation = false) {
-    if (alg == ZIG_ZIG256 && dt == ZIG_F64) return z256_warp_bytes() * (size_t)(block / 32);
+// Dynamic shared memory of a generation launch (the polar kernel uses static only).
+static size_t dyn_smem_of(int alg, int dt, int prng, int block) {
+    if (alg == ZIG_ZIG256) return zb::smem_bytes(block / 32);
     if (alg != ZIG_ZIG128) return 0;
-    if (mutation) {   // the mutation kernel (binary32 into the population)
-        const int warps = block / 32;
-        return prng == ZIG_LCG48 ? z128_dyn_for<GenLcg48>(dt, half_batch, warps)
-             : prng == ZIG_SPLITMIX64 ? z128_dyn_for<GenSplitMix64>(dt, half_batch, warps)
-             : prng == ZIG_L64X128MIX ? z128_dyn_for<GenL64X128Mix>(dt, half_batch, warps)
-                                      : z128_dyn_for<GenXoroshiro128PP>(dt, half_batch, warps);
-    }
-    return zf_smem(prng, dt, block / 32);   // the batch kernel
+    return zf_smem(prng, dt, block / 32);
 }
 
 // ---- launch configuration of the 128-level generation kernel ----
@@ -1784,16 +892,38 @@ static int grid_for(const void* fn, int dev, uint64_t n_groups, size_t dyn = 0, 
 
 // Launch the generation kernel of (alg, prng, dt) for the arguments in a, with
 // the configuration `force` or else the one recorded for this device.
+// The batch kernel's mutation forms (MUT 1: one population, 2: a batch of requests)
+// on binary32 rows, with as many warps as shared memory holds.
+template <int MUT, int PRNG>
+static zig_status launch_mut_p(int dev, uint64_t n_groups, GenArgs& a, cudaStream_t s) {
+    const GenFn fn = zf::z128f_kernel<PRNG, ZIG_F32, 4, MUT>;
+    int w = zf::max_threads(PRNG) / 32;
+    while (w > 1 && zf::smem_bytes<PRNG, ZIG_F32, MUT>(w) > 227 * 1024) --w;
+    const size_t dyn = zf::smem_bytes<PRNG, ZIG_F32, MUT>(w);
+    if (!allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
+    const int grid = grid_for((const void*)fn, dev, n_groups, dyn, 32 * w);
+    fn<<<grid, 32 * w, dyn, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
+}
+template <int MUT>
+static zig_status launch_mut(int prng, int dev, uint64_t n_groups, GenArgs& a, cudaStream_t s) {
+    switch (prng) {
+    case ZIG_LCG48: return launch_mut_p<MUT, 0>(dev, n_groups, a, s);
+    case ZIG_SPLITMIX64: return launch_mut_p<MUT, 1>(dev, n_groups, a, s);
+    case ZIG_L64X128MIX: return launch_mut_p<MUT, 2>(dev, n_groups, a, s);
+    default: return launch_mut_p<MUT, 3>(dev, n_groups, a, s);
+    }
+}
+
 static zig_status launch_gen(int alg, int prng, int dt, int dev, bool variable, uint64_t n_groups_hint,
                              GenArgs& a, cudaStream_t s, const LaunchCfg* force) {
     const bool z128 = alg == ZIG_ZIG128;
     const LaunchCfg c = force ? *force : z128 ? cfg_of(dev, prng, dt, variable) : default_cfg(dt);
-    int block = z128 ? (int)c.block : (alg == ZIG_ZIG256 && dt == ZIG_F64) ? kZBlock : kBlock;
+    int block = z128 ? (int)c.block : alg == ZIG_ZIG256 ? zb::kThreads : kBlock;
     if (z128) block = std::min(block, zf_max_block(prng, dt));
-    a.lane_sectors = 0u;
     const int fma = c.fma ? (int)c.fma : (int)default_fma(prng);
-    GenFn fn = pick(alg, prng, dt, false, fma);
-    const size_t dyn = dyn_smem_of(alg, dt, prng, false, block);
+    GenFn fn = pick(alg, prng, dt, fma);
+    const size_t dyn = dyn_smem_of(alg, dt, prng, block);
     if (!allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
     const int grid = grid_for((const void*)fn, dev, n_groups_hint, dyn, block);
     fn<<<grid, block, dyn, s>>>(a);
@@ -2138,16 +1268,8 @@ static zig_status mutate_impl(float* x_dev, float sigma, uint64_t P, uint64_t L,
     // without records the kernel seeds row p with a.mut_seed + p in mutation mode
     a.err = host::g_err_ptr[dev];
     GenArgs am = a;
-    host::GenFn fn = prng == ZIG_LCG48 ? z128_kernel<0, ZIG_F32, 1>
-                   : prng == ZIG_SPLITMIX64 ? z128_kernel<1, ZIG_F32, 1>
-                   : prng == ZIG_L64X128MIX ? z128_kernel<2, ZIG_F32, 1>
-                                            : z128_kernel<3, ZIG_F32, 1>;
     am.mut_seed = seed;
-    const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32, prng, false, kZBlock, true);
-    if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
-    int grid = host::grid_for((const void*)fn, dev, groups, dyn, kZBlock);
-    fn<<<grid, kZBlock, dyn, s>>>(am);
-    return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
+    return launch_mut<1>(prng, dev, groups, am, s);
 }
 }  // namespace host
 }  // namespace zig
@@ -2214,15 +1336,7 @@ zig_status zig_mutate_batch(const zig_mutation* reqs_host, uint32_t n_req, zig_p
     a.n_req = n_req;
     a.n_units = units;
     a.chunk_log2 = 10;
-    host::GenFn fn = prng == ZIG_LCG48 ? z128_kernel<0, ZIG_F32, 2>
-                   : prng == ZIG_SPLITMIX64 ? z128_kernel<1, ZIG_F32, 2>
-                   : prng == ZIG_L64X128MIX ? z128_kernel<2, ZIG_F32, 2>
-                                            : z128_kernel<3, ZIG_F32, 2>;
-    const size_t dyn = host::dyn_smem_of(ZIG_ZIG128, ZIG_F32, prng, false, kZBlock, true);
-    if (!host::allow_dyn_smem((const void*)fn, dyn)) return ZIG_ERR_CUDA;
-    int grid = host::grid_for((const void*)fn, dev, (units + 31) / 32, dyn, kZBlock);
-    fn<<<grid, kZBlock, dyn, s>>>(a);
-    return cudaGetLastError() == cudaSuccess ? ZIG_OK : ZIG_ERR_CUDA;
+    return host::launch_mut<2>(prng, dev, (units + 31) / 32, a, s);
 }
 
 zig_status zig_prng_fill(zig_prng prng, const uint64_t* seeds_dev, uint64_t n_streams, uint64_t n,
