@@ -194,7 +194,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
-KERNEL_SOURCES = ("zig_lib.cu", "z128_f64.cuh", "zig_device.cuh", "zig_tables.inc")
+KERNEL_SOURCES = ("zig_lib.cu", "z128_batch.cuh", "zig_device.cuh", "zig_tables.inc")
 
 
 def kernel_sources_sha256():
@@ -218,6 +218,33 @@ def load_kernel_record(name):
     if d.get("source_sha256") != kernel_sources_sha256():
         return None
     return d
+
+
+def write_kernel_record(spec):
+    """profiles/<name>.json from one ncu --csv metrics capture: spec is
+    name:csv_path:scale:command, where scale = the bench launch's variates over the
+    captured launch's and command is the capture's full command line."""
+    import csv
+    name, path, scale, command = spec.split(":", 3)
+    vals = {}
+    with open(path) as fh:
+        for row in csv.reader(fh):
+            if len(row) > 14 and row[0].isdigit():
+                vals[row[12]] = float(row[14].replace(",", ""))
+    scale = float(scale)
+    rec = {"kernel": name, "command": command,
+           "dram_bytes_read_captured": vals["dram__bytes_read.sum"],
+           "dram_bytes_write_captured": vals["dram__bytes_write.sum"],
+           "warp_instructions_captured": vals["smsp__inst_executed.sum"],
+           "scale_to_bench_launch": scale,
+           "dram_bytes_per_launch": (vals["dram__bytes_read.sum"] + vals["dram__bytes_write.sum"]) * scale,
+           "warp_instructions_per_launch": vals["smsp__inst_executed.sum"] * scale,
+           "source_sha256": kernel_sources_sha256()}
+    with open(os.path.join(ROOT, "profiles", name + ".json"), "w") as fh:
+        json.dump(rec, fh, indent=1)
+        fh.write("\n")
+    print(json.dumps(rec))
+    return 0
 
 
 def issue_roofline(rec, launch_ms, sm_mhz, n_sms):
@@ -328,9 +355,9 @@ def run_gpu(args):
     f32 = line_extra["comparisons"]["zig128/splitmix64/f32"]
     f32_bytes = N_STREAMS * PER_STREAM * 4 + N_STREAMS * 8
     f32_hbm = f32_bytes / (f32["ms_mean"] / 1e3) / 1e9
-    rec32 = load_kernel_record("z128_f32_splitmix64_record")
+    rec32 = load_kernel_record("z128f_f32_splitmix64_record")
     line_extra["roofline_f32"] = {
-        "kernel": "z128_kernel<splitmix64, f32>", "bound": "alu",
+        "kernel": "z128f_kernel<splitmix64, f32>", "bound": "alu",
         "hbm": {"achieved": f32_hbm, "peak": peak, "unit": "GB/s", "frac": f32_hbm / peak,
                 "algorithmic_bytes_per_launch": f32_bytes,
                 "traffic": rec32["dram_bytes_per_launch"] if rec32 else None},
@@ -659,7 +686,11 @@ def main(argv=None):
     ap.add_argument("--ncu-case", default=None,
                     help="run only alg:prng:dtype:n_streams:len[:chunk_log2] (for ncu)")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--kernel-record", default=None,
+                    help="write profiles/<name>.json from an ncu --csv capture: name:csv:scale:command")
     args = ap.parse_args(argv)
+    if args.kernel_record:
+        return write_kernel_record(args.kernel_record)
     if args.ncu_case:
         return run_case(args.ncu_case, args.reps)
     ws, _, _ = dist_env()

@@ -23,7 +23,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB_DIR = os.path.join(HERE, "_lib")
 SOURCES = ["zig_lib.cu", "zig_server.cpp"]
-DEPS = ["zig_lib.cu", "zig_server.cpp", "zig_device.cuh", "z128_f64.cuh", "z256_batch.cuh", "zig_tables.inc"]
+DEPS = ["zig_lib.cu", "zig_server.cpp", "zig_device.cuh", "z128_batch.cuh", "z256_batch.cuh", "zig_tables.inc"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

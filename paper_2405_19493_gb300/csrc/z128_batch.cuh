@@ -1,4 +1,5 @@
-// 128-level ziggurat with binary64 output: the speculative batch kernel.
+// 128-level ziggurat (GSL form): the speculative batch kernel, for binary64,
+// binary32 and bfloat16 output and for Gaussian mutation of binary32 rows.
 // Included by zig_lib.cu after the samplers and the unit helpers.
 //
 // Each lane owns one unit (a stream, or a 2^c chunk of one) with its generator
@@ -24,9 +25,10 @@
 //     it, so one store instruction writes the row's batch as one contiguous
 //     run (about 240 bytes) at any alignment, with no close-up of the row and
 //     no carry between batches.  Each lane rebuilds its value x = sign RN(j w[i])
-//     from the draw: one binary64 fma, or for some rows the same correctly
+//     from the draw: binary64, one fma, or for some rows the same correctly
 //     rounded product in 32-bit integer arithmetic (the narrow binary64 pipe
-//     and the integer pipes share the work).
+//     and the integer pipes share the work); binary32 and bfloat16, one binary32
+//     multiplication j w32[i].  Mutation rows read x and store x + sigma z.
 // A unit's outputs are its accepted candidates in draw order: the sequence a
 // one-variate-at-a-time loop produces (Sec. 2, Listing 2, repeated).
 #pragma once

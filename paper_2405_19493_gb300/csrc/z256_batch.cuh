@@ -1,6 +1,6 @@
 // Modified ziggurat (McFarland's 256 slots, Sec. 2 "Java 17"), every output type:
 // the batch layout of the 128-level kernel.  Included by zig_lib.cu after
-// z128_f64.cuh.
+// z128_batch.cuh.
 //
 // Each lane owns one unit with its generator in registers; a warp works on its
 // 32 units in batches of 32 draws per lane.  A draw is one nextLong U (two raw

@@ -1,6 +1,7 @@
 // Device-side building blocks of libzig_gb300: uniform generators with state in
-// registers, the exact binary64 product j * w[i] in integer arithmetic, and the
-// warp-cooperative staging that turns per-thread streams into coalesced stores.
+// registers (seeding, stepping, jumps, one step back, stream records), integer
+// roundings to binary32 and bfloat16, and the warp staging of the polar kernel
+// that turns per-thread streams into coalesced stores.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -1,7 +1,9 @@
 // libzig_gb300: bulk N(0,1) generation on GB300 (sm_103a) behind the C ABI in
 // include/zig.h.  One thread owns one (stream, chunk) unit with its generator
 // state in registers; the 32 units of a warp are staged in shared memory and
-// written out as coalesced rows.
+// written out as coalesced rows.  The two ziggurats run in batch kernels
+// (z128_batch.cuh, z256_batch.cuh); this file holds the shared device code,
+// the polar kernel, the checks and the host side.
 //
 // Transforms (Sec. 2, second list; Table 3):
 //   zig128  original ziggurat in the GSL form: a 32-bit draw gives layer i
@@ -165,7 +167,6 @@ __device__ __forceinline__ double neg_half_sq(double x) {
     return __dmul_rn(__dmul_rn(-0.5, x), x);
 }
 
-// Polar method with the cached second variate.
 // Natural logarithm of a positive normal binary64 x, by P. T. P. Tang's
 // table-driven method (ACM TOMS 16(4), 1990), all inline (no call):
 // x = 2^e m with m in [1, 2); F = 1 + k/128 is the table point nearest m;
@@ -218,6 +219,7 @@ __device__ __forceinline__ double polar_v(uint64_t m) {
     return d < 0 ? __longlong_as_double(__double_as_longlong(r) ^ (long long)(1ull << 63)) : r;
 }
 
+// Polar method with the cached second variate (`extra` counts the raw steps).
 template <class G>
 __device__ __forceinline__ double polar_f64(G& g, bool& have, double& cached, uint32_t& extra) {
     if (have) {
@@ -287,7 +289,7 @@ template <> __device__ __forceinline__ uint16_t from_f64<ZIG_BF16>(double z) { r
 // ---------------------------------------------------------------------------
 // The polar method (Marsaglia), one stream per lane, outputs staged per warp.
 template <int ALG, int PRNG, int DT>
-__global__ void __launch_bounds__(kBlock) gen_kernel(GenArgs a) {
+__global__ void __launch_bounds__(kBlock) polar_kernel(GenArgs a) {
     using G = typename GenOf<PRNG>::T;
     using OutT = typename OutOf<DT>::T;
     static_assert(ALG == ZIG_POLAR, "the ziggurats run in their batch kernels");
@@ -441,7 +443,7 @@ __device__ __forceinline__ double z128_tail_value(uint64_t m1) {
     return __dsub_rn(zigtab::ZIG128_R, div_by_R(zlog(U1)));
 }
 
-#include "z128_f64.cuh"
+#include "z128_batch.cuh"
 #include "z256_batch.cuh"
 
 // Exhaustive check of the fast path's arithmetic against CUDA's IEEE operations:
@@ -741,9 +743,9 @@ static GenFn pick_dt(int dt, int fma) {
         }
     } else {
         switch (dt) {
-        case ZIG_F64: return gen_kernel<ALG, PRNG, ZIG_F64>;
-        case ZIG_F32: return gen_kernel<ALG, PRNG, ZIG_F32>;
-        default: return gen_kernel<ALG, PRNG, ZIG_BF16>;
+        case ZIG_F64: return polar_kernel<ALG, PRNG, ZIG_F64>;
+        case ZIG_F32: return polar_kernel<ALG, PRNG, ZIG_F32>;
+        default: return polar_kernel<ALG, PRNG, ZIG_BF16>;
         }
     }
 }
