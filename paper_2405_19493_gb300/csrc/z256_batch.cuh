@@ -136,7 +136,6 @@ __device__ __forceinline__ double slow_path(S& src, const Z256Smem& t) {
 // rounding (XN = -XS 2^52 in the table, so no separate negation is needed).
 template <int PRNG>
 __device__ __forceinline__ uint64_t value_of(const Tabs& tb, uint64_t v, bool slow, int lane) {
-    if (slow) return v;
     const uint64_t U = slot_u64<PRNG>(v);
     const uint32_t j = (uint32_t)U & 0xFFu;
     const uint64_t m = U >> 11;
@@ -144,7 +143,8 @@ __device__ __forceinline__ uint64_t value_of(const Tabs& tb, uint64_t v, bool sl
     const double xn = tb.XN[j][lane & 15];
     const double av = __hiloint2double((int)(0x3FF00000u | (mh & 0xFFFFFu)), (int)(uint32_t)m);
     const double x = __fma_rn(av, -xn, (mh >> 20) ? 0.0 : xn);
-    return (uint64_t)__double_as_longlong(x) | ((U >> 8) & 1u) << 63;
+    const uint64_t fast = (uint64_t)__double_as_longlong(x) | ((U >> 8) & 1u) << 63;
+    return slow ? v : fast;   // a select, not a branch: the rows' loads and fmas overlap
 }
 
 template <int PRNG, int DT>
