@@ -525,6 +525,24 @@ const char *zig_status_string(zig_status status);
  */
 zig_status zig_selfcheck(uint64_t counts_host[6]);
 
+/*
+ * zig_filtercheck -- the slow tests' binary32 filters against their binary64
+ * definitions on the current device (test support).  The kernels decide each
+ * slow test first in binary32 and leave it to binary64 only inside a margin
+ * that must cover every binary32 error: the 128-level wedge test (Sec. 1, the
+ * GSL form's wedge comparison) and tail test, and the modified ziggurat's
+ * overhang and tail tests (Sec. 2, "Java 17").  For each test f (0 wedge,
+ * 1 tail, 2 overhang, 3 the 256-slot tail) 2^27 inputs: half uniform, with the
+ * tails' uniforms spread over every binary scale down to 2^-53, half within
+ * 2^-8 of the test's boundary.  Writes counts_host[3 f] = inputs checked,
+ * [3 f + 1] = inputs the filter left undecided, [3 f + 2] = inputs the filter
+ * decided unlike the binary64 definition (0 when its margin holds).
+ * Synchronous; allocates 96 bytes of device memory for the call.
+ * ZIG_ERR_INVALID_ARG for a NULL counts_host; ZIG_ERR_NOT_INITIALIZED without
+ * zig_tables_init.
+ */
+zig_status zig_filtercheck(uint64_t counts_host[12]);
+
 /* Library version as major * 10000 + minor * 100 + patch. */
 int zig_version(void);
 

@@ -36,7 +36,7 @@ EXPORTS = (
     "zig_server_create", "zig_server_submit", "zig_server_wait", "zig_server_query",
     "zig_server_drain", "zig_server_stats", "zig_server_destroy", "zig_server_submit_generate",
     "zig_launch_config_get", "zig_launch_config_set", "zig_autotune_candidates", "zig_autotune",
-    "zig_selfcheck", "zig_generate_checked", "zig_status_decode", "zig_tables_get",
+    "zig_selfcheck", "zig_filtercheck", "zig_generate_checked", "zig_status_decode", "zig_tables_get",
     "zig_state_init", "zig_generate_state", "zig_mutate_state", "zig_server_population",
     "zig_server_submit_population", "zig_server_population_release",
 )
@@ -149,6 +149,8 @@ def load(build_if_missing: bool = True):
             getattr(lib, name).restype = i32
         lib.zig_selfcheck.argtypes = [C.POINTER(u64)]
         lib.zig_selfcheck.restype = i32
+        lib.zig_filtercheck.argtypes = [C.POINTER(u64)]
+        lib.zig_filtercheck.restype = i32
         lib.zig_device_status.argtypes = [i32, i32]
         lib.zig_generate_checked.argtypes = [i32, i32, vp, vp, u64, u64, C.c_uint32, i32, vp, vp,
                                              C.c_size_t, vp, vp]
@@ -412,6 +414,16 @@ def zig_selfcheck() -> dict:
     return {"product_mismatches": int(c[0]), "rounding_mismatches": int(c[1]),
             "products_checked": int(c[2]), "roundings_checked": int(c[3]),
             "logs_beyond_one_ulp": int(c[4]), "logs_not_equal": int(c[5])}
+
+
+def zig_filtercheck() -> dict:
+    """The slow tests' binary32 filters against their binary64 definitions (see zig.h):
+    per test, inputs checked, left undecided, and decided unlike the definition."""
+    c = (C.c_uint64 * 12)()
+    _check(load().zig_filtercheck(c), "zig_filtercheck")
+    names = ("wedge128", "tail128", "overhang256", "tail256")
+    return {nm: {"checked": int(c[3 * f]), "undecided": int(c[3 * f + 1]), "wrong": int(c[3 * f + 2])}
+            for f, nm in enumerate(names)}
 
 
 def zig_device_status(device: int = 0, clear: bool = False) -> int:

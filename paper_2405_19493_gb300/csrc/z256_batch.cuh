@@ -10,9 +10,12 @@
 //  B. Each lane walks its nf bits in draw order and runs the slow path of each
 //     slow draw it meets (an overhang or the tail), taking that path's uniforms
 //     from the slots after it (they are consumed, not candidates) and from its
-//     generator once the row is used up.  The slow path always ends with a value,
-//     which replaces the raw draw in its slot.  A lane stops once its unit has all
-//     its outputs.  No lane waits for another's slow path, and none stops early.
+//     generator once the row is used up.  The tests run in binary32 where proven
+//     margins decide them, in binary64 otherwise (binary64 arithmetic runs on
+//     the narrow FP64 pipe).  An overhang's value replaces the raw draw in its slot; an accepted
+//     tail's value, x0 - ln(U1)/x0 in binary64, is left to a per-warp queue that
+//     evaluates 32 at a time.  A lane stops once its unit has all its outputs.
+//     No lane waits for another's slow path, and none stops early.
 //  C. The warp writes its rows as the 128-level kernel does, lane c on slot c of
 //     one row at a time: the output index of a kept slot is the number of kept
 //     slots below it.  A fast slot's value XS[j] m (m = U >> 11) is rebuilt from
@@ -55,6 +58,7 @@ __device__ __forceinline__ uint32_t lt_mask_of(int p) { return p >= 32 ? ~0u : (
 
 constexpr int kThreads = 640;   // 20 warps: shared memory holds no more
 constexpr int kRS = 33;         // row stride in 8-byte words
+constexpr int kTQ = 32;         // tail queue entries per warp
 
 struct Tabs {
     double XN[256][16];   // -XS[j] 2^52, 16 copies (a half warp reads without conflicts)
@@ -63,6 +67,9 @@ struct Tabs {
 struct Warp {
     uint64_t stage[32 * kRS];   // row r, slot d at r kRS + d
     uint4 info[32];             // per row: output address (low, high), dropped slots, slow values
+    uint64_t tq_addr[kTQ];      // accepted tails waiting for their value: output address | negative
+    uint64_t tq_m1[kTQ];        // and their uniform m1 (U1 = 1 - m1 2^-53)
+    uint32_t tq_n;
 };
 __host__ __device__ constexpr size_t smem_bytes(int warps) {
     return ((sizeof(Tabs) + 15) & ~(size_t)15) + sizeof(Warp) * (size_t)warps;
@@ -89,45 +96,105 @@ struct Src {
     }
 };
 
+// The tail step (Marsaglia's, beyond x0) on U = 1 - m 2^-53 in (0, 1]: x = -ln(U1)/x0,
+// y = -ln(U2), accepted when 2y > x^2, which is ln U2 < -s^2/2 with s = x in exact
+// arithmetic.  tail_filter decides it in binary32 when that clears a margin of
+// 2^-14 (1 + s^2/2 + |ln U2|), far above the binary32 errors (correctly rounded
+// conversions; the hardware log2 within 2^-22.6 absolute on [0.5, 2] and 2 ulp
+// elsewhere: below 1e-5 relative here): 1 accept, 0 reject, -1 undecided.
+// tail_exact is the binary64 definition; tail_value the accepted value x0 + x.
+__device__ __forceinline__ int tail_filter(uint64_t m1, uint64_t m2) {
+    const uint64_t n1 = (1ull << 53) - m1, n2 = (1ull << 53) - m2;   // U = n 2^-53
+    constexpr float kLn2 = 0.693147180559945309f;
+    constexpr float kLn2OverX0 = (float)(0.693147180559945309 / zigtab::ZIG256_X0);
+    const float s32 = -__log2f(m53_to_float(n1)) * kLn2OverX0;
+    const float h32 = 0.5f * s32 * s32;
+    const float l32 = __log2f(m53_to_float(n2)) * kLn2;
+    const float marg = 0x1p-14f * (1.0f + h32 - l32);
+    if (l32 < -h32 - marg) return 1;
+    if (l32 > -h32 + marg) return 0;
+    return -1;
+}
+__device__ __forceinline__ bool tail_exact(uint64_t m1, uint64_t m2) {
+    const double U1 = __dsub_rn(1.0, m53_to_double(m1));
+    const double U2 = __dsub_rn(1.0, m53_to_double(m2));
+    const double x = __ddiv_rn(-zlog(U1), zigtab::ZIG256_X0);
+    const double y = -zlog(U2);
+    return __dadd_rn(y, y) > __dmul_rn(x, x);
+}
+__device__ __forceinline__ double tail_value(uint64_t m1) {
+    const double U1 = __dsub_rn(1.0, m53_to_double(m1));
+    return __dadd_rn(zigtab::ZIG256_X0, __ddiv_rn(-zlog(U1), zigtab::ZIG256_X0));
+}
+
+// slow_path's result for an accepted tail: this flag | m1 (its value comes later)
+constexpr uint64_t kTailFlag = 1ull << 63;
+
 // McFarland's slow path after a slow first draw: a slot r chosen by the alias
 // table from a fresh nextLong, then the tail (r = 0) or that overhang's
-// rejection loop, each on fresh uniforms.  Returns x >= 0.
+// rejection loop, each on fresh uniforms.  Returns an overhang's x >= 0 as
+// binary64 bits (computed once, for the accepted uniform), or kTailFlag | m1 for
+// an accepted tail.
 template <int PRNG, class S>
-__device__ __forceinline__ double slow_path(S& src, const Z256Smem& t) {
+__device__ __forceinline__ uint64_t slow_path(S& src, const Z256Smem& t) {
     const uint64_t two53 = 1ull << 53;
     const uint64_t V = slot_u64<PRNG>(src.next());
     const uint32_t b = (uint32_t)(V & 0xFF);
     const int r = ((V >> 8) < t.THR[b]) ? (int)b : t.ALIAS[b];
     if (r == 0) {
-        const double x0 = zigtab::ZIG256_X0;
         for (;;) {
-            const double U1 = __dsub_rn(1.0, m53_to_double(slot_m53<PRNG>(src.next())));
-            const double U2 = __dsub_rn(1.0, m53_to_double(slot_m53<PRNG>(src.next())));
-            const double x = __ddiv_rn(-zlog(U1), x0);
-            const double y = -zlog(U2);
-            if (__dadd_rn(y, y) > __dmul_rn(x, x)) return __dadd_rn(x0, x);
+            const uint64_t m1 = slot_m53<PRNG>(src.next());
+            const uint64_t m2 = slot_m53<PRNG>(src.next());
+            int f = tail_filter(m1, m2);
+            if (f < 0) f = tail_exact(m1, m2) ? 1 : 0;
+            if (f) return kTailFlag | m1;
         }
     }
     const int kd = d_z256_KIND[r - 1];
-    const double ox = d_z256_OX[r - 1], odx = d_z256_ODX[r - 1];
-    const double oy = d_z256_OY[r - 1], ody = d_z256_ODY[r - 1];
     const uint64_t qa = d_z256_QA[r - 1];
+    const float ox32 = d_z256_F32[0][r - 1], odx32 = d_z256_F32[1][r - 1];
+    const float oy32 = d_z256_F32[2][r - 1], ody32 = d_z256_F32[3][r - 1];
+    uint64_t m1;
     for (;;) {
-        uint64_t m1 = slot_m53<PRNG>(src.next());
+        m1 = slot_m53<PRNG>(src.next());
         uint64_t m2 = slot_m53<PRNG>(src.next());
         if (kd > 0 && m1 + m2 > two53) {
             m1 = two53 - m1;
             m2 = two53 - m2;
         }
-        const double x = __dadd_rn(ox, __dmul_rn(odx, u53_to_double(m1, 53)));
-        if (kd > 0 && m1 + m2 <= two53 - qa) return x;
-        if (kd < 0 && m1 + m2 < two53) return x;
-        const int f = z256_overhang_filter((float)ox, (float)odx, (float)oy, (float)ody, m1, m2);
-        if (f == 1) return x;
+        if (kd > 0 && m1 + m2 <= two53 - qa) break;
+        if (kd < 0 && m1 + m2 < two53) break;
+        const int f = z256_overhang_filter(ox32, odx32, oy32, ody32, m1, m2);
+        if (f == 1) break;
         if (f == 0) continue;
-        const double y = __dadd_rn(oy, __dmul_rn(ody, u53_to_double(m2, 53)));
-        if (y < exp(neg_half_sq(x))) return x;
+        const double x = __dadd_rn(d_z256_OX[r - 1], __dmul_rn(d_z256_ODX[r - 1], u53_to_double(m1, 53)));
+        const double y = __dadd_rn(d_z256_OY[r - 1], __dmul_rn(d_z256_ODY[r - 1], u53_to_double(m2, 53)));
+        if (y < exp(neg_half_sq(x))) break;
     }
+    const double x = __dadd_rn(d_z256_OX[r - 1], __dmul_rn(d_z256_ODX[r - 1], u53_to_double(m1, 53)));
+    return (uint64_t)__double_as_longlong(x);
+}
+
+// The values of queued accepted tails, up to 32 at once (all 32 lanes call this):
+// binary64 x, or the binary32 / bfloat16 rounding of it, with the sign from bit 0
+// of the entry's address.
+template <int DT>
+__device__ __forceinline__ void drain_tails(Warp& ws, int lane) {
+    if ((uint32_t)lane < ws.tq_n) {
+        const uint64_t ad = ws.tq_addr[lane];
+        const double x = tail_value(ws.tq_m1[lane]);
+        const uint32_t neg = (uint32_t)(ad & 1u);
+        if constexpr (DT == ZIG_F64) {
+            __stcs((unsigned long long*)(ad & ~1ull), (unsigned long long)__double_as_longlong(x) | (unsigned long long)neg << 63);
+        } else if constexpr (DT == ZIG_F32) {
+            __stcs((unsigned int*)(ad & ~1ull), f64_to_f32_bits(x) | neg << 31);
+        } else {
+            __stcs((unsigned short*)(ad & ~1ull), (unsigned short)(f64_to_bf16_bits(x) | neg << 15));
+        }
+    }
+    __syncwarp();
+    if (lane == 0) ws.tq_n = 0;
+    __syncwarp();
 }
 
 // The value of slot c of a row: the slow path's value (bit c of Sv), or the fast
@@ -165,6 +232,8 @@ __global__ void __launch_bounds__(kThreads, 1) z256b_kernel(GenArgs a) {
     const int n_warps = blockDim.x >> 5;
     Warp& ws = *(Warp*)(zb_dsm + ((sizeof(Tabs) + 15) & ~(size_t)15) + (size_t)wib * sizeof(Warp));
     uint64_t* const row = ws.stage + lane * kRS;
+    if (lane == 0) ws.tq_n = 0;
+    __syncwarp();
     if (a.out == nullptr) {   // only legal when every length is zero
         if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.err, kErrNullOutput);
         return;
@@ -214,22 +283,27 @@ __global__ void __launch_bounds__(kThreads, 1) z256b_kernel(GenArgs a) {
             if constexpr (PRNG == ZIG_LCG48) GT::template skip<2 * B>(g);
             // ---- B: each lane's slow paths, in draw order ----
             int drawn = B;
-            uint32_t du = 0, Sv = 0;   // consumed draws, slots holding a slow path's value
+            uint32_t du = 0, Sv = 0, Tq = 0;   // consumed draws, slots with a slow value, accepted tails
             int last_end = 0;          // the draw after the last slow path run
             for (uint32_t m = rem > 0 ? nf : 0u; m;) {
                 const int p = __ffs(m) - 1;
                 m &= m - 1u;
                 if ((du >> p) & 1u) continue;   // a uniform of an earlier slow path
                 if ((uint64_t)__popc(~du & lt_mask_of(p)) >= rem) break;   // the unit ends before p
-                const uint64_t U = slot_u64<PRNG>(row[p]);
+                const uint64_t neg = (slot_u64<PRNG>(row[p]) >> 8) & 1u;
                 Src<PRNG, G> src{row, p + 1, drawn, g};
-                const double x = slow_path<PRNG>(src, tb.s);
+                const uint64_t xv = slow_path<PRNG>(src, tb.s);
                 g = src.g;
                 drawn = src.drawn;
                 const int hi = src.pos < 32 ? src.pos : 32;
                 du |= lt_mask_of(hi) & ~lt_mask_of(p + 1);
-                row[p] = (uint64_t)__double_as_longlong(x) | ((U >> 8) & 1u) << 63;
-                Sv |= 1u << p;
+                if (xv & kTailFlag) {   // m1 and the sign wait in the slot for the queue
+                    row[p] = xv | neg << 62;
+                    Tq |= 1u << p;
+                } else {
+                    row[p] = xv | neg << 63;
+                    Sv |= 1u << p;
+                }
                 last_end = src.pos;
             }
             // ---- C: drops, the unit's end, then the rows ----
@@ -243,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) z256b_kernel(GenArgs a) {
                 D |= keepm;
                 if ((check_chunk || srec) && k_out > 0) {
                     const int c = 31 - __clz(~D);   // slot of the last output
-                    const int used = ((Sv >> c) & 1u) ? last_end : c + 1;   // draws up to it and its slow path
+                    const int used = (((Sv | Tq) >> c) & 1u) ? last_end : c + 1;   // draws up to it and its slow path
                     draws += (uint64_t)used * kStepsPerSlot<PRNG>;
                     if (srec) {   // the generator after those draws (the batch took `drawn` from sb)
                         G t = g;
@@ -274,12 +348,32 @@ __global__ void __launch_bounds__(kThreads, 1) z256b_kernel(GenArgs a) {
                     else __stcs((unsigned short*)p, f64_to_bf16_bits(x));
                 }
             }
+            // accepted tails join the queue (one per lane per round; their rows
+            // stored a placeholder, which the queue's value overwrites)
+            uint32_t Tk = Tq & ~D;
+            for (;;) {
+                const uint32_t bal = __ballot_sync(kFull, Tk != 0);
+                if (bal == 0) break;
+                if (ws.tq_n + __popc(bal) > (uint32_t)kTQ) drain_tails<DT>(ws, lane);
+                if (Tk) {
+                    const int p = __ffs(Tk) - 1;
+                    Tk &= Tk - 1u;
+                    const uint32_t idx = ws.tq_n + __popc(bal & lt_mask);
+                    const uint64_t v = row[p];
+                    ws.tq_addr[idx] = (uint64_t)(uintptr_t)(dst + __popc(~D & ((1u << p) - 1u))) | ((v >> 62) & 1u);
+                    ws.tq_m1[idx] = v & ((1ull << 53) - 1u);
+                }
+                __syncwarp();
+                if (lane == 0) ws.tq_n += __popc(bal);
+                __syncwarp();
+            }
             dst += k_out;
             rem -= (uint64_t)k_out;
             __syncwarp();
         }
         if (check_chunk && draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
     }
+    drain_tails<DT>(ws, lane);
 }
 
 }  // namespace zb

@@ -39,6 +39,7 @@ __device__ double d_z128_Y[128];
 __device__ float d_z128_W32[128];
 __device__ double d_z256_XS[256];
 __device__ double d_z256_OX[256], d_z256_ODX[256], d_z256_OY[256], d_z256_ODY[256];
+__device__ float d_z256_F32[4][256];   // RN32 of OX, ODX, OY, ODY (the overhang filter's operands)
 __device__ int d_z256_KIND[256];
 __device__ uint64_t d_z256_QA[256];
 __device__ uint64_t d_z256_THR[256];
@@ -367,10 +368,11 @@ __device__ __forceinline__ double mul_j_w(uint32_t j, double b) {
     return __fma_rn(__hiloint2double(0x3FF00000, (int)j), b, -b);
 }
 
-// binary32 value of m * 2^-53 for m < 2^53 (relative error < 2^-23).
+// binary32 value of m * 2^-53 for m < 2^53, correctly rounded (relative error
+// at most 2^-24 at every scale: the slow tests take logarithms of uniforms far
+// below 2^-8, where keeping only the top 24 of 53 bits would not do).
 __device__ __forceinline__ float m53_to_float(uint64_t m) {
-    const uint32_t hi = (uint32_t)(m >> 29);
-    return hi ? (float)hi * 0x1p-24f : (float)(uint32_t)m * 0x1p-53f;
+    return __fmul_rn(__ull2float_rn(m), 0x1p-53f);   // the scaling is exact
 }
 
 // The wedge test for layer i, abscissa j and uniform U = m1 2^-53:
@@ -503,6 +505,96 @@ __global__ void __launch_bounds__(256) selfcheck_kernel(unsigned long long* coun
     atomicAdd(&counts[3], n_b);
     atomicAdd(&counts[4], far_l);
     atomicAdd(&counts[5], ne_l);
+}
+
+// The slow tests' binary32 filters against their binary64 definitions: the
+// 128-level wedge and tail tests, the 256-slot overhang and tail tests.  Half the
+// inputs are uniform (the tails' uniforms spread over every binary scale), half
+// sit at +-2^s units of 2^-53 (s < 45) from the test's boundary, where a filter
+// error would show.  counts[3 f]: inputs checked for filter f, [3 f + 1]: left
+// undecided (binary64 decides them), [3 f + 2]: decided unlike the definition.
+__device__ __forceinline__ uint64_t near53(double v, int64_t off) {   // clamp(v 2^53 + off) to [0, 2^53)
+    const double s = __dmul_rn(v, 0x1p53);
+    const int64_t b = s >= 0x1p53 ? (int64_t)(1ll << 53) : s > 0.0 ? (int64_t)s : 0;
+    const int64_t m = b + off;
+    return m < 0 ? 0 : m >= (1ll << 53) ? (1ull << 53) - 1 : (uint64_t)m;
+}
+__global__ void __launch_bounds__(256) filtercheck_kernel(unsigned long long* counts, uint64_t n) {
+    __shared__ zf::SlowTab st;
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+        st.W32[i] = d_z128_W32[i];
+        st.Y32[i] = d_z128_Y32[i];
+        st.DY32[i] = d_z128_DY32[i];
+        st.Wd[i] = d_z128_W[i];
+        st.Y[i] = d_z128_Y[i];
+    }
+    __syncthreads();
+    unsigned long long c[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) c[q] = 0;
+    auto tally = [&](int f, int filt, bool exact) {
+        c[3 * f] += 1;
+        c[3 * f + 1] += filt < 0;
+        c[3 * f + 2] += filt >= 0 && (filt == 1) != exact;
+    };
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r0 = mix64(4 * k + 1), r1 = mix64(4 * k + 2), r2 = mix64(4 * k + 3), r3 = mix64(4 * k + 4);
+        const bool near = r0 & 1u;
+        const int s = (int)((r0 >> 1) % 45);
+        const int64_t mag = (int64_t)((1ull << s) + (r3 & ((1ull << s) - 1u)));
+        const int64_t off = ((r0 >> 8) & 1u) ? -mag : mag;
+        // a uniform's integer at every scale: (53 random bits) >> (0 .. 52)
+        const uint64_t spread1 = (r2 >> 11) >> ((r1 >> 58) % 53);
+        const uint64_t spread2 = (r3 >> 11) >> ((r2 & 63) % 53);
+        {   // 128-level wedge, layer i < 127, a slow abscissa j >= k[i]
+            const uint32_t i = (uint32_t)(r1 % 127u);
+            const uint32_t K = d_z128_kE[i] & 0xFFFFFFu;
+            if (K < (1u << 24)) {
+                const uint32_t j = K + (uint32_t)((r1 >> 8) % ((1u << 24) - K));
+                uint64_t m1 = r2 >> 11;
+                if (near) {
+                    const double x = __dmul_rn((double)j, st.Wd[i]);
+                    m1 = near53(__ddiv_rn(__dsub_rn(exp(neg_half_sq(x)), st.Y[i + 1]), __dsub_rn(st.Y[i], st.Y[i + 1])), off);
+                }
+                tally(0, z128_wedge_filter(st, i, j, m1), z128_wedge_exact(st, i, j, m1));
+            }
+        }
+        {   // 128-level tail: U1 = 1 - m1 2^-53, U2 = m2 2^-53
+            const uint64_t n1 = spread1 | 1u;
+            const uint64_t m1 = (1ull << 53) - n1;
+            uint64_t m2 = spread2;
+            if (near) {
+                const double sv = __ddiv_rn(-zlog(m53_to_double(n1)), zigtab::ZIG128_R);
+                m2 = near53(exp(__dmul_rn(__dmul_rn(-0.5, sv), sv)), off);
+            }
+            tally(1, z128_tail_filter(m1, m2), z128_tail_exact(m1, m2));
+        }
+        {   // 256-slot overhang of table entry r
+            const int r = (int)(r1 % (uint64_t)zigtab::ZIG256_NR);
+            const uint64_t m1 = r2 >> 11;
+            uint64_t m2 = r3 >> 11;
+            const double x = __dadd_rn(d_z256_OX[r], __dmul_rn(d_z256_ODX[r], u53_to_double(m1, 53)));
+            if (near && d_z256_ODY[r] != 0.0)
+                m2 = near53(__ddiv_rn(__dsub_rn(exp(neg_half_sq(x)), d_z256_OY[r]), d_z256_ODY[r]), off);
+            const double y = __dadd_rn(d_z256_OY[r], __dmul_rn(d_z256_ODY[r], u53_to_double(m2, 53)));
+            tally(2, z256_overhang_filter(d_z256_F32[0][r], d_z256_F32[1][r], d_z256_F32[2][r], d_z256_F32[3][r], m1, m2),
+                  y < exp(neg_half_sq(x)));
+        }
+        {   // 256-slot tail: U = 1 - m 2^-53 for both uniforms
+            const uint64_t n1 = spread1 | 1u;
+            const uint64_t m1 = (1ull << 53) - n1;
+            uint64_t n2 = spread2 | 1u;
+            if (near) {
+                const double sv = __ddiv_rn(-zlog(m53_to_double(n1)), zigtab::ZIG256_X0);
+                n2 = near53(exp(__dmul_rn(__dmul_rn(-0.5, sv), sv)), off);
+                n2 = n2 ? n2 : 1u;
+            }
+            const uint64_t m2 = (1ull << 53) - n2;
+            tally(3, zb::tail_filter(m1, m2), zb::tail_exact(m1, m2));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 12; ++q) atomicAdd(&counts[q], c[q]);
 }
 
 // Exclusive prefix sums of lengths and unit counts (one block).  Sums saturate
@@ -690,6 +782,14 @@ static zig_status init_device(int device) {
     ZIG_CUDA(cudaMemcpyToSymbol(d_z256_OY, zigtab::ZIG256_OY, sizeof(double) * nr));
     ZIG_CUDA(cudaMemcpyToSymbol(d_z256_ODY, zigtab::ZIG256_ODY, sizeof(double) * nr));
     ZIG_CUDA(cudaMemcpyToSymbol(d_z256_KIND, zigtab::ZIG256_KIND, sizeof(int) * nr));
+    float f32[4][256] = {};
+    for (int r = 0; r < nr; ++r) {
+        f32[0][r] = (float)zigtab::ZIG256_OX[r];
+        f32[1][r] = (float)zigtab::ZIG256_ODX[r];
+        f32[2][r] = (float)zigtab::ZIG256_OY[r];
+        f32[3][r] = (float)zigtab::ZIG256_ODY[r];
+    }
+    ZIG_CUDA(cudaMemcpyToSymbol(d_z256_F32, f32, sizeof(f32)));
     ZIG_CUDA(cudaMemcpyToSymbol(d_z256_QA, zigtab::ZIG256_QA, sizeof(uint64_t) * nr));
     ZIG_CUDA(cudaMemcpyToSymbol(d_z256_THR, zigtab::ZIG256_THR, sizeof(zigtab::ZIG256_THR)));
     ZIG_CUDA(cudaMemcpyToSymbol(d_z256_ALIAS, zigtab::ZIG256_ALIAS, sizeof(zigtab::ZIG256_ALIAS)));
@@ -1411,6 +1511,25 @@ zig_status zig_selfcheck(uint64_t counts_host[6]) {
         selfcheck_kernel<<<host::g_sms[dev] * 8, 256>>>(d);
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpy(counts_host, d, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = ZIG_ERR_CUDA;
+    }
+    cudaFree(d);
+    return st;
+}
+
+zig_status zig_filtercheck(uint64_t counts_host[12]) {
+    if (!counts_host) return ZIG_ERR_INVALID_ARG;
+    int dev;
+    zig_status st = host::current_device(dev);
+    if (st != ZIG_OK) return st;
+    unsigned long long* d = nullptr;
+    ZIG_CUDA(cudaMalloc(&d, 12 * sizeof(unsigned long long)));
+    st = ZIG_OK;
+    if (cudaMemset(d, 0, 12 * sizeof(unsigned long long)) != cudaSuccess) st = ZIG_ERR_CUDA;
+    if (st == ZIG_OK) {
+        filtercheck_kernel<<<host::g_sms[dev] * 8, 256>>>(d, 1ull << 27);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(counts_host, d, 12 * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
             st = ZIG_ERR_CUDA;
     }
     cudaFree(d);

@@ -147,6 +147,7 @@ def test_more_host_side_argument_errors():
     assert lib.zig_autotune(0, P, None, 16, 4, 0, 0, P, None, 0, 0, None, None, None) == INVALID
     assert lib.zig_autotune(0, P, None, 16, 4, 0, 0, P, None, 0, 1001, None, None, None) == INVALID
     assert lib.zig_selfcheck(None) == INVALID
+    assert lib.zig_filtercheck(None) == INVALID
 
 
 def test_status_decode_and_table_sizes():
