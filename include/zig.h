@@ -514,8 +514,9 @@ const char *zig_status_string(zig_status status);
  * (+-2^52 w[i]) -- and compares each with IEEE multiplication (__dmul_rn, negated
  * for the negative entries); rounds every finite binary32 bit pattern to
  * bfloat16 by the kernel's routine and compares it with __float2bfloat16_rn,
- * and 2^32 binary64 values in [2^-113, 8) of both signs to binary32 and compares
- * that with __double2float_rn; and compares the tail step's own binary64 log
+ * 2^32 binary64 values in [2^-112, 16) of both signs to binary32 and to bfloat16
+ * and compares them with __double2float_rn and __double2bfloat16, and the same
+ * for 2^31 exact ties and tie neighbours each; and compares the tail step's own binary64 log
  * with CUDA's log on 2^31 uniforms in (0, 1).  Writes counts_host[0] = product
  * mismatches, [1] = rounding mismatches, [2] = products checked (5 * 2^31),
  * [3] = roundings checked, [4] = logs more than one ulp from CUDA's, [5] = logs

@@ -12,15 +12,17 @@
 //     from the slots after it (they are consumed, not candidates) and from its
 //     generator once the row is used up.  The tests run in binary32 where proven
 //     margins decide them, in binary64 otherwise (binary64 arithmetic runs on
-//     the narrow FP64 pipe).  An overhang's value replaces the raw draw in its slot; an accepted
-//     tail's value, x0 - ln(U1)/x0 in binary64, is left to a per-warp queue that
-//     evaluates 32 at a time.  A lane stops once its unit has all its outputs.
-//     No lane waits for another's slow path, and none stops early.
+//     the narrow FP64 pipe).  An accepted slow path leaves its slot r and
+//     uniform in its slot; its binary64 value (an overhang's ox + odx U1, the
+//     tail's x0 - ln(U1)/x0) is left to a per-warp queue that evaluates 32 at a
+//     time.  A lane stops once its unit has all its outputs.  No lane waits for
+//     another's slow path, and none stops early.
 //  C. The warp writes its rows as the 128-level kernel does, lane c on slot c of
 //     one row at a time: the output index of a kept slot is the number of kept
 //     slots below it.  A fast slot's value XS[j] m (m = U >> 11) is rebuilt from
 //     the raw draw with one binary64 fma; binary32 and bfloat16 outputs round
-//     the binary64 value once, in integer arithmetic.
+//     the binary64 value once, in integer arithmetic.  A slow slot's entry
+//     joins the queue with its output address.
 // A unit's outputs are its candidates' values in draw order: the sequence a
 // one-variate-at-a-time loop produces (Sec. 2, Listing 2, repeated).
 #pragma once
@@ -58,7 +60,7 @@ __device__ __forceinline__ uint32_t lt_mask_of(int p) { return p >= 32 ? ~0u : (
 
 constexpr int kThreads = 640;   // 20 warps: shared memory holds no more
 constexpr int kRS = 33;         // row stride in 8-byte words
-constexpr int kTQ = 32;         // tail queue entries per warp
+constexpr int kSQ = 32;         // slow-value queue entries per warp
 
 struct Tabs {
     double XN[256][16];   // -XS[j] 2^52, 16 copies (a half warp reads without conflicts)
@@ -66,10 +68,10 @@ struct Tabs {
 };
 struct Warp {
     uint64_t stage[32 * kRS];   // row r, slot d at r kRS + d
-    uint4 info[32];             // per row: output address (low, high), dropped slots, slow values
-    uint64_t tq_addr[kTQ];      // accepted tails waiting for their value: output address | negative
-    uint64_t tq_m1[kTQ];        // and their uniform m1 (U1 = 1 - m1 2^-53)
-    uint32_t tq_n;
+    uint4 info[32];             // per row: output address (low, high), dropped slots
+    uint64_t sq_addr[kSQ];      // accepted slow paths waiting for their value: output address | negative
+    uint64_t sq_val[kSQ];       // and their slot and uniform, r << 53 | m1
+    uint32_t sq_n;
 };
 __host__ __device__ constexpr size_t smem_bytes(int warps) {
     return ((sizeof(Tabs) + 15) & ~(size_t)15) + sizeof(Warp) * (size_t)warps;
@@ -102,7 +104,7 @@ struct Src {
 // 2^-14 (1 + s^2/2 + |ln U2|), far above the binary32 errors (correctly rounded
 // conversions; the hardware log2 within 2^-22.6 absolute on [0.5, 2] and 2 ulp
 // elsewhere: below 1e-5 relative here): 1 accept, 0 reject, -1 undecided.
-// tail_exact is the binary64 definition; tail_value the accepted value x0 + x.
+// tail_exact is the binary64 definition.
 __device__ __forceinline__ int tail_filter(uint64_t m1, uint64_t m2) {
     const uint64_t n1 = (1ull << 53) - m1, n2 = (1ull << 53) - m2;   // U = n 2^-53
     constexpr float kLn2 = 0.693147180559945309f;
@@ -122,19 +124,24 @@ __device__ __forceinline__ bool tail_exact(uint64_t m1, uint64_t m2) {
     const double y = -zlog(U2);
     return __dadd_rn(y, y) > __dmul_rn(x, x);
 }
-__device__ __forceinline__ double tail_value(uint64_t m1) {
-    const double U1 = __dsub_rn(1.0, m53_to_double(m1));
-    return __dadd_rn(zigtab::ZIG256_X0, __ddiv_rn(-zlog(U1), zigtab::ZIG256_X0));
-}
 
-// slow_path's result for an accepted tail: this flag | m1 (its value comes later)
-constexpr uint64_t kTailFlag = 1ull << 63;
+// The value x >= 0 of an accepted slow path q = r << 53 | m1: the tail's
+// x0 + RN(-ln(U1) / x0) with U1 = 1 - m1 2^-53 (r = 0), or overhang r's
+// RN(ox + RN(odx U1)) with U1 = m1 2^-53.
+__device__ __forceinline__ double slow_value(uint64_t q) {
+    const uint64_t m1 = q & ((1ull << 53) - 1u);
+    const int r = (int)(q >> 53);
+    if (r == 0) {
+        const double U1 = __dsub_rn(1.0, m53_to_double(m1));
+        return __dadd_rn(zigtab::ZIG256_X0, __ddiv_rn(-zlog(U1), zigtab::ZIG256_X0));
+    }
+    return __dadd_rn(d_z256_OX[r - 1], __dmul_rn(d_z256_ODX[r - 1], u53_to_double(m1, 53)));
+}
 
 // McFarland's slow path after a slow first draw: a slot r chosen by the alias
 // table from a fresh nextLong, then the tail (r = 0) or that overhang's
-// rejection loop, each on fresh uniforms.  Returns an overhang's x >= 0 as
-// binary64 bits (computed once, for the accepted uniform), or kTailFlag | m1 for
-// an accepted tail.
+// rejection loop, each on fresh uniforms.  Returns the accepted slot and
+// uniform, r << 53 | m1 (slow_value gives its value).
 template <int PRNG, class S>
 __device__ __forceinline__ uint64_t slow_path(S& src, const Z256Smem& t) {
     const uint64_t two53 = 1ull << 53;
@@ -147,7 +154,7 @@ __device__ __forceinline__ uint64_t slow_path(S& src, const Z256Smem& t) {
             const uint64_t m2 = slot_m53<PRNG>(src.next());
             int f = tail_filter(m1, m2);
             if (f < 0) f = tail_exact(m1, m2) ? 1 : 0;
-            if (f) return kTailFlag | m1;
+            if (f) return m1;
         }
     }
     const int kd = d_z256_KIND[r - 1];
@@ -171,18 +178,17 @@ __device__ __forceinline__ uint64_t slow_path(S& src, const Z256Smem& t) {
         const double y = __dadd_rn(d_z256_OY[r - 1], __dmul_rn(d_z256_ODY[r - 1], u53_to_double(m2, 53)));
         if (y < exp(neg_half_sq(x))) break;
     }
-    const double x = __dadd_rn(d_z256_OX[r - 1], __dmul_rn(d_z256_ODX[r - 1], u53_to_double(m1, 53)));
-    return (uint64_t)__double_as_longlong(x);
+    return (uint64_t)r << 53 | m1;
 }
 
-// The values of queued accepted tails, up to 32 at once (all 32 lanes call this):
+// The values of queued slow paths, up to 32 at once (all 32 lanes call this):
 // binary64 x, or the binary32 / bfloat16 rounding of it, with the sign from bit 0
 // of the entry's address.
 template <int DT>
-__device__ __forceinline__ void drain_tails(Warp& ws, int lane) {
-    if ((uint32_t)lane < ws.tq_n) {
-        const uint64_t ad = ws.tq_addr[lane];
-        const double x = tail_value(ws.tq_m1[lane]);
+__device__ __forceinline__ void drain_slow(Warp& ws, int lane) {
+    if ((uint32_t)lane < ws.sq_n) {
+        const uint64_t ad = ws.sq_addr[lane];
+        const double x = slow_value(ws.sq_val[lane]);
         const uint32_t neg = (uint32_t)(ad & 1u);
         if constexpr (DT == ZIG_F64) {
             __stcs((unsigned long long*)(ad & ~1ull), (unsigned long long)__double_as_longlong(x) | (unsigned long long)neg << 63);
@@ -193,16 +199,16 @@ __device__ __forceinline__ void drain_tails(Warp& ws, int lane) {
         }
     }
     __syncwarp();
-    if (lane == 0) ws.tq_n = 0;
+    if (lane == 0) ws.sq_n = 0;
     __syncwarp();
 }
 
-// The value of slot c of a row: the slow path's value (bit c of Sv), or the fast
-// draw's sign XS[j] m with m = U >> 11 = h 2^52 + l: a = 1 + l 2^-52 from bits
+// The value of a fast slot of a row: the draw's sign XS[j] m with
+// m = U >> 11 = h 2^52 + l: a = 1 + l 2^-52 from bits
 // and fma(a, -XN[j], h ? 0 : XN[j]) = XS[j] 2^52 (l 2^-52 + h) before its one
 // rounding (XN = -XS 2^52 in the table, so no separate negation is needed).
 template <int PRNG>
-__device__ __forceinline__ uint64_t value_of(const Tabs& tb, uint64_t v, bool slow, int lane) {
+__device__ __forceinline__ uint64_t value_of(const Tabs& tb, uint64_t v, int lane) {
     const uint64_t U = slot_u64<PRNG>(v);
     const uint32_t j = (uint32_t)U & 0xFFu;
     const uint64_t m = U >> 11;
@@ -210,8 +216,7 @@ __device__ __forceinline__ uint64_t value_of(const Tabs& tb, uint64_t v, bool sl
     const double xn = tb.XN[j][lane & 15];
     const double av = __hiloint2double((int)(0x3FF00000u | (mh & 0xFFFFFu)), (int)(uint32_t)m);
     const double x = __fma_rn(av, -xn, (mh >> 20) ? 0.0 : xn);
-    const uint64_t fast = (uint64_t)__double_as_longlong(x) | ((U >> 8) & 1u) << 63;
-    return slow ? v : fast;   // a select, not a branch: the rows' loads and fmas overlap
+    return (uint64_t)__double_as_longlong(x) | ((U >> 8) & 1u) << 63;
 }
 
 template <int PRNG, int DT>
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1) z256b_kernel(GenArgs a) {
     const int n_warps = blockDim.x >> 5;
     Warp& ws = *(Warp*)(zb_dsm + ((sizeof(Tabs) + 15) & ~(size_t)15) + (size_t)wib * sizeof(Warp));
     uint64_t* const row = ws.stage + lane * kRS;
-    if (lane == 0) ws.tq_n = 0;
+    if (lane == 0) ws.sq_n = 0;
     __syncwarp();
     if (a.out == nullptr) {   // only legal when every length is zero
         if (a.lengths && a.totals[1] != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.err, kErrNullOutput);
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1) z256b_kernel(GenArgs a) {
             if constexpr (PRNG == ZIG_LCG48) GT::template skip<2 * B>(g);
             // ---- B: each lane's slow paths, in draw order ----
             int drawn = B;
-            uint32_t du = 0, Sv = 0, Tq = 0;   // consumed draws, slots with a slow value, accepted tails
+            uint32_t du = 0, Q = 0;    // consumed draws, slots of accepted slow paths
             int last_end = 0;          // the draw after the last slow path run
             for (uint32_t m = rem > 0 ? nf : 0u; m;) {
                 const int p = __ffs(m) - 1;
@@ -292,18 +297,13 @@ __global__ void __launch_bounds__(kThreads, 1) z256b_kernel(GenArgs a) {
                 if ((uint64_t)__popc(~du & lt_mask_of(p)) >= rem) break;   // the unit ends before p
                 const uint64_t neg = (slot_u64<PRNG>(row[p]) >> 8) & 1u;
                 Src<PRNG, G> src{row, p + 1, drawn, g};
-                const uint64_t xv = slow_path<PRNG>(src, tb.s);
+                const uint64_t q = slow_path<PRNG>(src, tb.s);
                 g = src.g;
                 drawn = src.drawn;
                 const int hi = src.pos < 32 ? src.pos : 32;
                 du |= lt_mask_of(hi) & ~lt_mask_of(p + 1);
-                if (xv & kTailFlag) {   // m1 and the sign wait in the slot for the queue
-                    row[p] = xv | neg << 62;
-                    Tq |= 1u << p;
-                } else {
-                    row[p] = xv | neg << 63;
-                    Sv |= 1u << p;
-                }
+                row[p] = q | neg << 62;   // waits in the slot for the queue
+                Q |= 1u << p;
                 last_end = src.pos;
             }
             // ---- C: drops, the unit's end, then the rows ----
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) z256b_kernel(GenArgs a) {
                 D |= keepm;
                 if ((check_chunk || srec) && k_out > 0) {
                     const int c = 31 - __clz(~D);   // slot of the last output
-                    const int used = (((Sv | Tq) >> c) & 1u) ? last_end : c + 1;   // draws up to it and its slow path
+                    const int used = ((Q >> c) & 1u) ? last_end : c + 1;   // draws up to it and its slow path
                     draws += (uint64_t)used * kStepsPerSlot<PRNG>;
                     if (srec) {   // the generator after those draws (the batch took `drawn` from sb)
                         G t = g;
@@ -333,38 +333,48 @@ __global__ void __launch_bounds__(kThreads, 1) z256b_kernel(GenArgs a) {
             } else if (check_chunk) {
                 draws += (uint64_t)drawn * kStepsPerSlot<PRNG>;
             }
-            ws.info[lane] = make_uint4((uint32_t)(uintptr_t)dst, (uint32_t)((uintptr_t)dst >> 32), D, Sv);
+            ws.info[lane] = make_uint4((uint32_t)(uintptr_t)dst, (uint32_t)((uintptr_t)dst >> 32), D, 0u);
             __syncwarp();
 #pragma unroll 4
             for (int r = 0; r < 32; ++r) {
                 const uint4 inf = ws.info[r];
-                const uint64_t v = value_of<PRNG>(tb, ws.stage[r * kRS + lane], (inf.w >> lane) & 1u, lane);
+                const uint64_t v = value_of<PRNG>(tb, ws.stage[r * kRS + lane], lane);
                 const uint32_t e = __popc(~inf.z & lt_mask);
                 OutT* const p = (OutT*)((uint64_t)inf.x | (uint64_t)inf.y << 32) + e;
-                if (!(inf.z & lane_bit)) {
-                    const double x = __longlong_as_double((long long)v);
-                    if constexpr (DT == ZIG_F64) __stcs((unsigned long long*)p, (unsigned long long)v);
-                    else if constexpr (DT == ZIG_F32) __stcs((unsigned int*)p, f64_to_f32_bits(x));
-                    else __stcs((unsigned short*)p, f64_to_bf16_bits(x));
+                // a predicated store of a value computed on every lane, so that the
+                // unrolled rows' loads and arithmetic overlap.  A queued slow slot
+                // stores a placeholder, which its queue entry overwrites: the row's
+                // run leaves no hole in a sector (a hole filled after the sector
+                // left L2 would cost a read-modify-write of it).
+                const uint32_t skip = inf.z & lane_bit;
+                const double x = __longlong_as_double((long long)v);
+                if constexpr (DT == ZIG_F64) {
+                    asm volatile("{\n\t.reg .pred q;\n\tsetp.eq.u32 q, %2, 0;\n\t@q st.global.cs.b64 [%0], %1;\n\t}" ::"l"(p),
+                                 "l"(v), "r"(skip));
+                } else if constexpr (DT == ZIG_F32) {
+                    asm volatile("{\n\t.reg .pred q;\n\tsetp.eq.u32 q, %2, 0;\n\t@q st.global.cs.b32 [%0], %1;\n\t}" ::"l"(p),
+                                 "r"(f64_to_f32_bits(x)), "r"(skip));
+                } else {
+                    asm volatile("{\n\t.reg .pred q;\n\tsetp.eq.u32 q, %2, 0;\n\t@q st.global.cs.b16 [%0], %1;\n\t}" ::"l"(p),
+                                 "h"(f64_to_bf16_bits(x)), "r"(skip));
                 }
             }
-            // accepted tails join the queue (one per lane per round; their rows
-            // stored a placeholder, which the queue's value overwrites)
-            uint32_t Tk = Tq & ~D;
+            // accepted slow paths join the queue (one per lane per round)
+            uint32_t Qk = Q & ~D;
             for (;;) {
-                const uint32_t bal = __ballot_sync(kFull, Tk != 0);
+                const uint32_t bal = __ballot_sync(kFull, Qk != 0);
                 if (bal == 0) break;
-                if (ws.tq_n + __popc(bal) > (uint32_t)kTQ) drain_tails<DT>(ws, lane);
-                if (Tk) {
-                    const int p = __ffs(Tk) - 1;
-                    Tk &= Tk - 1u;
-                    const uint32_t idx = ws.tq_n + __popc(bal & lt_mask);
+                if (ws.sq_n + __popc(bal) > (uint32_t)kSQ) drain_slow<DT>(ws, lane);
+                if (Qk) {
+                    const int p = __ffs(Qk) - 1;
+                    Qk &= Qk - 1u;
+                    const uint32_t idx = ws.sq_n + __popc(bal & lt_mask);
                     const uint64_t v = row[p];
-                    ws.tq_addr[idx] = (uint64_t)(uintptr_t)(dst + __popc(~D & ((1u << p) - 1u))) | ((v >> 62) & 1u);
-                    ws.tq_m1[idx] = v & ((1ull << 53) - 1u);
+                    ws.sq_addr[idx] = (uint64_t)(uintptr_t)(dst + __popc(~D & ((1u << p) - 1u))) | ((v >> 62) & 1u);
+                    ws.sq_val[idx] = v & ((1ull << 61) - 1u);
                 }
                 __syncwarp();
-                if (lane == 0) ws.tq_n += __popc(bal);
+                if (lane == 0) ws.sq_n += __popc(bal);
                 __syncwarp();
             }
             dst += k_out;
@@ -373,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1) z256b_kernel(GenArgs a) {
         }
         if (check_chunk && draws > kChunkDraws) atomicOr(a.err, kErrChunkOverflow);
     }
-    drain_tails<DT>(ws, lane);
+    drain_slow<DT>(ws, lane);
 }
 
 }  // namespace zb

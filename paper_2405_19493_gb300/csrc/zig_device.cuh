@@ -311,32 +311,33 @@ __device__ __forceinline__ double m53_to_double(uint64_t m) {
     return (double)m * 0x1p-53;   // exact: m < 2^53
 }
 
-// RN-even binary64 -> bfloat16 bits (finite, normal-range inputs).
+// RN-even binary64 -> bfloat16 bits, for zero and for results in bfloat16's
+// normal range, in 32-bit integer operations on the two words: the exponent and
+// top 7 fraction bits, rounded on the 45 bits below them, then rebiased by
+// 1023 - 127 (a rounding carry moves into the exponent first).
 __device__ __forceinline__ uint16_t f64_to_bf16_bits(double x) {
-    uint64_t b = (uint64_t)__double_as_longlong(x);
-    uint64_t sign = b >> 63;
-    uint64_t mag = b & 0x7FFFFFFFFFFFFFFFull;
-    if (mag == 0) return (uint16_t)(sign << 15);
-    uint64_t q = mag >> 45;
-    uint64_t rem = mag & ((1ull << 45) - 1);
-    const uint64_t half = 1ull << 44;
-    q += (rem > half) | ((rem == half) & (q & 1));
-    uint64_t e = (q >> 7) - 1023 + 127;
-    return (uint16_t)((sign << 15) | (e << 7) | (q & 0x7F));
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t mag_hi = hi & 0x7FFFFFFFu;
+    uint32_t q = mag_hi >> 13;
+    const uint32_t r = hi & 0x1FFFu;   // with lo, the 45 bits below q
+    const bool above = r > 0x1000u || (r == 0x1000u && lo != 0u);
+    const bool tie = r == 0x1000u && lo == 0u;
+    q += (above || (tie && (q & 1u))) ? 1u : 0u;
+    const uint32_t sign = (hi >> 16) & 0x8000u;
+    return (uint16_t)((mag_hi | lo) == 0u ? sign : (sign | (q - (896u << 7))));
 }
 
-// RN-even binary64 -> binary32 bits for zero and for magnitudes in [2^-126, 2^128)
-// (the exponent is rebiased by 1023 - 127 after the rounding carry).
+// RN-even binary64 -> binary32 bits, for zero and for magnitudes in [2^-126, 2^128),
+// in 32-bit integer operations: the exponent and top 23 fraction bits (a funnel
+// shift of the two words, exact modulo 2^32 once rebiased by 1023 - 127), rounded
+// on the 29 bits below them (a carry moves into the exponent).
 __device__ __forceinline__ uint32_t f64_to_f32_bits(double x) {
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-    const uint64_t mag = b & 0x7FFFFFFFFFFFFFFFull;
-    if (mag == 0) return sign;
-    uint64_t q = mag >> 29;
-    const uint64_t rem = mag & ((1ull << 29) - 1);
-    const uint64_t half = 1ull << 28;
-    q += (rem > half) | ((rem == half) & (q & 1));
-    return sign | (uint32_t)(q - (896ull << 23));
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t sign = hi & 0x80000000u;
+    uint32_t q = __funnelshift_l(lo, hi, 3) - (896u << 23);
+    const uint32_t rem = lo & 0x1FFFFFFFu;
+    q += (rem > 0x10000000u || (rem == 0x10000000u && (q & 1u))) ? 1u : 0u;
+    return ((hi & 0x7FFFFFFFu) | lo) == 0u ? sign : (sign | q);
 }
 
 // RN-even binary32 -> bfloat16 bits (finite inputs).

@@ -480,12 +480,23 @@ __global__ void __launch_bounds__(256) selfcheck_kernel(unsigned long long* coun
         }
         n_p += 5;
         const double u = m53_to_double(((k * 0x9E3779B97F4A7C15ull) >> 11) | 1u);   // in (0, 1)
-        // the binary64 -> binary32 rounding of the narrow outputs, on u scaled into [2^-60, 8)
+        // the binary64 -> binary32 and -> bfloat16 roundings of the narrow outputs, on u
+        // scaled into [2^-112, 16) (every output's magnitude is below 15), of both
+        // signs; then on exact ties and their neighbours (a fraction whose dropped
+        // bits are half an ulp, +-1), which random fractions almost never give
         {
-            const double v = __dmul_rn(u, __longlong_as_double((long long)(0x3C3ull + (k % 64)) << 52));
+            const uint64_t e64 = (uint64_t)(0x3C4ull + (k % 64)) << 52;
+            const double v = __dmul_rn(u, __longlong_as_double((long long)e64));
             bad_b += f64_to_f32_bits(v) != __float_as_uint(__double2float_rn(v));
             bad_b += f64_to_f32_bits(-v) != __float_as_uint(__double2float_rn(-v));
-            n_b += 2;
+            bad_b += f64_to_bf16_bits(v) != __bfloat16_as_ushort(__double2bfloat16(v));
+            bad_b += f64_to_bf16_bits(-v) != __bfloat16_as_ushort(__double2bfloat16(-v));
+            const int64_t d = (int64_t)((k >> 6) % 3) - 1;
+            const double t32 = __longlong_as_double((long long)(e64 | ((k >> 8) & 0x7FFFFFu) << 29 | (uint64_t)((1ll << 28) + d)));
+            const double t16 = __longlong_as_double((long long)(e64 | ((k >> 8) & 0x7Fu) << 45 | (uint64_t)((1ll << 44) + d)));
+            bad_b += f64_to_f32_bits(t32) != __float_as_uint(__double2float_rn(t32));
+            bad_b += f64_to_bf16_bits(t16) != __bfloat16_as_ushort(__double2bfloat16(t16));
+            n_b += 6;
         }
         const long long dl = __double_as_longlong(zlog(u)) - __double_as_longlong(log(u));
         far_l += dl > 1 || dl < -1;

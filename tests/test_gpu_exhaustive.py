@@ -7,8 +7,9 @@ signed entries +-b it keeps; each must equal IEEE multiplication (negated for
 the negative entries) for every abscissa j < 2^24 of every layer (5 x 2^31
 products).  The bfloat16 outputs round binary32
 values with an integer routine that must equal CUDA's RN-even conversion for
-every finite binary32 pattern; the modified ziggurat's binary32 outputs round
-binary64 values with another, checked the same way on 2^32 values.  The tail step's table-driven binary64 log must
+every finite binary32 pattern; the modified ziggurat's binary32 and bfloat16
+outputs round binary64 values with two more, checked against CUDA's conversions
+on 2^32 values each and on 2^31 exact ties or tie neighbours each.  The tail step's table-driven binary64 log must
 stay within one ulp of CUDA's log (both are within about an ulp of the exact
 value) on 2^31 uniforms spread over (0, 1), and equal it almost always.
 
@@ -31,8 +32,9 @@ def test_product_and_bf16_rounding_exhaustive():
     Z.zig_tables_init(0)
     r = Z._binding.zig_selfcheck()
     assert r["products_checked"] == 5 * 128 * 2 ** 24
-    # every finite binary32 pattern (to bfloat16), and 2^32 binary64 values (to binary32)
-    assert r["roundings_checked"] == 2 ** 32 - 2 * (2 ** 23) + 2 ** 32
+    # every finite binary32 pattern (to bfloat16); 2^32 binary64 values to binary32 and
+    # to bfloat16 each, and 2^31 ties or tie neighbours for each
+    assert r["roundings_checked"] == 2 ** 32 - 2 * (2 ** 23) + 6 * 2 ** 31
     assert r["product_mismatches"] == 0
     assert r["rounding_mismatches"] == 0
     assert r["logs_beyond_one_ulp"] == 0
