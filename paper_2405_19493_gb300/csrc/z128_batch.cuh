@@ -139,9 +139,23 @@ __device__ __forceinline__ uint64_t first_state_of(const G& g) {
 // for j = 0, takes b's sign by an OR), the integer product takes it from b's
 // sign bit, and the binary32 product j (-w32[i]) is -(j w32[i]), -0 for j = 0.
 // The block stride of 256 bytes makes each address one byte permute of w.
-struct Tab {
-    uint32_t blk[256][64];
+// The generators whose slots are 64-bit nextLong outputs use a compact form
+// instead: 128-byte blocks with half the copies (8 of b, or 16 of w32; 16 of K),
+// addressed by a shift and an OR.  Their stages are twice as large, and the
+// compact table is what lets 20 warps rather than 16 fit in shared memory (the
+// extra copies only avoid bank conflicts).
+template <int PRNG>
+constexpr bool kCompactTab = Gen<PRNG>::SW == 2;
+template <bool C>
+struct TabT {
+    uint32_t blk[256][C ? 32 : 64];
 };
+// byte offset of this lane's copy (copy: its byte offset in the block) in block w & 0xFF
+template <bool C>
+__device__ __forceinline__ uint32_t entry_off(uint32_t w, uint32_t copy) {
+    if constexpr (C) return ((w & 0xFFu) << 7) | copy;
+    else return __byte_perm(w, copy, 0x5504);
+}
 struct SlowTab {   // the wedge test's tables (z128_wedge_filter, z128_wedge_exact)
     float W32[128], Y32[128], DY32[128];
     double Wd[128], Y[128];
@@ -159,9 +173,9 @@ struct Warp {
     static constexpr int RS = SW == 1 ? 33 : 66;            // row stride in words
     uint32_t stage[32 * RS];   // row r, slot d: words r RS + SW d ..
     uint4 info[32];            // per row: output address (low, high), dropped slots
-    uint64_t tq_addr[64];      // accepted tails waiting for their value: output address | negative
-    uint64_t tq_m1[64];        // and their uniform m1 (U1 = 1 - m1 2^-53)
-    uint32_t tq_sig[MUT ? 64 : 1];   // mutation: and their row's sigma bits (kGenerate: x = z)
+    uint64_t tq_addr[32];      // accepted tails waiting for their value: output address | negative
+    uint64_t tq_m1[32];        // and their uniform m1 (U1 = 1 - m1 2^-53)
+    uint32_t tq_sig[MUT ? 32 : 1];   // mutation: and their row's sigma bits (kGenerate: x = z)
     uint32_t tails[MUT ? 32 : 1];    // mutation: per row, the accepted tails (their queue entry updates x)
     uint32_t tq_n;
 };
@@ -172,20 +186,22 @@ __host__ __device__ constexpr size_t warp_bytes() {
 // a mutation row's sigma word when the request generates (x = z): a NaN pattern
 // no finite sigma has
 constexpr uint32_t kGenerate = 0xFFFFFFFFu;
-__host__ __device__ constexpr size_t head_bytes() { return sizeof(Tab) + ((sizeof(SlowTab) + 15) & ~(size_t)15); }
+template <bool C>
+__host__ __device__ constexpr size_t head_bytes() { return sizeof(TabT<C>) + ((sizeof(SlowTab) + 15) & ~(size_t)15); }
 template <int PRNG, int DT, int MUT = 0>
 __host__ __device__ constexpr size_t smem_bytes(int warps) {
-    return head_bytes() + warp_bytes<PRNG, DT, MUT>() * (size_t)warps;
+    return head_bytes<kCompactTab<PRNG>>() + warp_bytes<PRNG, DT, MUT>() * (size_t)warps;
 }
 
-template <int DT>
-__device__ __forceinline__ void tab_load(Tab& t, SlowTab& s) {
-    for (int k = threadIdx.x; k < 256 * 64; k += blockDim.x) {
-        const int ix = k >> 6, wd = k & 63, i = ix & 127;
+template <int DT, bool C>
+__device__ __forceinline__ void tab_load(TabT<C>& t, SlowTab& s) {
+    constexpr int kWords = C ? 32 : 64;   // per block; the second half holds K
+    for (int k = threadIdx.x; k < 256 * kWords; k += blockDim.x) {
+        const int ix = k / kWords, wd = k % kWords, i = ix & 127;
         const double wi = d_z128_W[i];
         const uint32_t K = (d_z128_kE[i] & 0xFFFFFFu) << 8;
         uint32_t v;
-        if (wd >= 32) {
+        if (wd >= kWords / 2) {
             v = K;
         } else if (DT == ZIG_F64) {
             const double bd = __dmul_rn(ix < 128 ? -wi : wi, 0x1p52);   // exact scaling, signed
@@ -231,9 +247,9 @@ __device__ __forceinline__ uint64_t int_mul_jw(uint32_t j, uint32_t mlo, uint32_
 // fma(1 + j 2^-52, b, -b) with the signed b = +-2^52 w[i] (exact before its one
 // rounding; 1 + j 2^-52 is built from j's bits), or (kInt) int_mul_jw with the
 // significand, exponent and sign read off b (E(b) = E(w[i]) + 52).
-template <bool kInt>
+template <bool kInt, bool C>
 __device__ __forceinline__ uint64_t x_of(const unsigned char* tab, uint32_t w, uint32_t copy8) {
-    const uint2 e = *(const uint2*)(tab + __byte_perm(w, copy8, 0x5504));   // block ix, copy
+    const uint2 e = *(const uint2*)(tab + entry_off<C>(w, copy8));   // block ix, copy
     const uint32_t j = w >> 8;
     if constexpr (kInt) {
         const uint32_t mhi = __funnelshift_l(e.x, (e.y & 0xFFFFFu) | 0x100000u, 11);
@@ -248,8 +264,9 @@ __device__ __forceinline__ uint64_t x_of(const unsigned char* tab, uint32_t w, u
 
 // The binary32 value RN32(j w32[i]) with the entry's sign, for the draw w
 // (binary32 and bfloat16 output; j < 2^24 converts exactly).
+template <bool C>
 __device__ __forceinline__ uint32_t x32_of(const unsigned char* tab, uint32_t w, uint32_t copy4) {
-    const float e = *(const float*)(tab + __byte_perm(w, copy4, 0x5504));   // block ix, copy
+    const float e = *(const float*)(tab + entry_off<C>(w, copy4));   // block ix, copy
     return __float_as_uint(__fmul_rn((float)(w >> 8), e));
 }
 
@@ -264,17 +281,17 @@ __device__ __forceinline__ void write_row(const W& ws, const unsigned char* tb, 
     const uint32_t e = __popc(~inf.z & lt_mask);
     const uint64_t base = (uint64_t)inf.x | (uint64_t)inf.y << 32;
     if constexpr (DT == ZIG_F64) {
-        const uint64_t v = x_of<kInt>(tb, w, copy);
+        const uint64_t v = x_of<kInt, kCompactTab<PRNG>>(tb, w, copy);
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %2, 0;\n\t@p st.global.cs.b64 [%0], %1;\n\t}" ::"l"(base + 8ull * e),
             "l"(v), "r"(inf.z & lane_bit));
     } else if constexpr (DT == ZIG_F32) {
-        const uint32_t v = x32_of(tb, w, copy);
+        const uint32_t v = x32_of<kCompactTab<PRNG>>(tb, w, copy);
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %2, 0;\n\t@p st.global.cs.b32 [%0], %1;\n\t}" ::"l"(base + 4ull * e),
             "r"(v), "r"(inf.z & lane_bit));
     } else {
-        const uint16_t v = f32_to_bf16_bits(__uint_as_float(x32_of(tb, w, copy)));
+        const uint16_t v = f32_to_bf16_bits(__uint_as_float(x32_of<kCompactTab<PRNG>>(tb, w, copy)));
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %2, 0;\n\t@p st.global.cs.b16 [%0], %1;\n\t}" ::"l"(base + 2ull * e),
             "h"(v), "r"(inf.z & lane_bit));
@@ -304,7 +321,7 @@ __device__ __forceinline__ void mutate_rows8(const W& ws, const unsigned char* t
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const float z = __uint_as_float(x32_of(tb, ws.stage[(r0 + k) * W::RS + GT::SW * lane + GT::SW - 1], copy));
+        const float z = __uint_as_float(x32_of<kCompactTab<PRNG>>(tb, ws.stage[(r0 + k) * W::RS + GT::SW * lane + GT::SW - 1], copy));
         if (st[k]) __stcs(px[k], sg[k] == kGenerate ? z : fmaf(__uint_as_float(sg[k]), z, xv[k]));
     }
 }
@@ -352,9 +369,10 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
     static_assert(DT == ZIG_F64 || NDF == 4, "binary32 and bfloat16 rows have one product");
     static_assert(MUT == 0 || DT == ZIG_F32, "populations are binary32");
     extern __shared__ __align__(16) unsigned char zf_dsm[];
-    Tab& tab = *(Tab*)zf_dsm;
-    SlowTab& slow = *(SlowTab*)(zf_dsm + sizeof(Tab));
-    tab_load<DT>(tab, slow);
+    constexpr bool C = kCompactTab<PRNG>;
+    TabT<C>& tab = *(TabT<C>*)zf_dsm;
+    SlowTab& slow = *(SlowTab*)(zf_dsm + sizeof(TabT<C>));
+    tab_load<DT, C>(tab, slow);
     __syncthreads();
     const unsigned char* const tb = zf_dsm;
 
@@ -362,11 +380,12 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
     const uint32_t lane_bit = 1u << lane, lt_mask = lane_bit - 1u;
     const int wib = threadIdx.x >> 5;
     const int n_warps = blockDim.x >> 5;
-    W& ws = *(W*)(zf_dsm + head_bytes() + (size_t)wib * warp_bytes<PRNG, DT, MUT>());
+    W& ws = *(W*)(zf_dsm + head_bytes<C>() + (size_t)wib * warp_bytes<PRNG, DT, MUT>());
     uint32_t* const row = ws.stage + lane * W::RS;
-    // this lane's copy of the fast entry: b (binary64) or w32
-    const uint32_t copy = DT == ZIG_F64 ? (uint32_t)(lane & 15) << 3 : (uint32_t)lane << 2;
-    const uint32_t kcopy = 0x80u + ((uint32_t)lane << 2);  // this lane's copy of K
+    // this lane's copy of the fast entry, b (binary64) or w32, and of K
+    const uint32_t copy = C ? (DT == ZIG_F64 ? (uint32_t)(lane & 7) << 3 : (uint32_t)(lane & 15) << 2)
+                            : (DT == ZIG_F64 ? (uint32_t)(lane & 15) << 3 : (uint32_t)lane << 2);
+    const uint32_t kcopy = C ? 0x40u + ((uint32_t)(lane & 15) << 2) : 0x80u + ((uint32_t)lane << 2);
 
     if (lane == 0) ws.tq_n = 0;
     __syncwarp();
@@ -445,7 +464,7 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
                 } else {
                     GT::draw(g, row + SW * d, w);
                 }
-                const uint32_t K = *(const uint32_t*)(tb + __byte_perm(w, kcopy, 0x5504));
+                const uint32_t K = *(const uint32_t*)(tb + entry_off<C>(w, kcopy));
                 nf |= (w >= K ? 1u : 0u) << d;
             };
             unroll<B>(step);
@@ -538,11 +557,13 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
                     write_row<PRNG, DT, (3 >= NDF)>(ws, tb, r + 3, lane, lane_bit, lt_mask, copy);
                 }
             }
-            // accepted tails join the queue (one per lane per round), evaluated 32 at a time
+            // accepted tails join the queue (one per lane per round), evaluated 32 at a
+            // time (drained first when a round would overfill it)
             uint32_t Lk = L & ~D;
             for (;;) {
                 const uint32_t bal = __ballot_sync(kFull, Lk != 0);
                 if (bal == 0) break;
+                if (ws.tq_n + __popc(bal) > 32u) drain_tails<DT, MUT>(ws, lane);
                 if (Lk) {
                     const int p = __ffs(Lk) - 1;
                     Lk &= Lk - 1u;
@@ -555,7 +576,6 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
                 __syncwarp();
                 if (lane == 0) ws.tq_n += __popc(bal);
                 __syncwarp();
-                if (ws.tq_n >= 32) drain_tails<DT, MUT>(ws, lane);
             }
             dst += k_out;
             rem -= (uint64_t)k_out;
