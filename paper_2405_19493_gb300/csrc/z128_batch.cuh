@@ -4,8 +4,9 @@
 //
 // Each lane owns one unit (a stream, or a 2^c chunk of one) with its generator
 // in registers; a warp works on its 32 units in batches of B draws per lane,
-// B = 32 - 2 kU (kU = raw steps per nextDouble), so that a batch with the
-// draws a tail may need past it fills exactly 32 slots of the lane's row.
+// B = 33 - 2 kU (kU = raw steps per nextDouble), so that a batch with the
+// draws a tail may need past it fills the 33 slots of the lane's row (the
+// last one, past the 32 a row store writes, only ever holds a uniform).
 //  A. Every lane takes B draws in lockstep and keeps each in its row, with no
 //     branch and no vote: the fast test j < k[i] (Sec. 1; the GSL form's first
 //     comparison) only sets a bit of the lane's mask nf.  A slot holds the
@@ -169,8 +170,8 @@ constexpr int kMaxThreads = 640;
 template <int PRNG, int DT, int MUT = 0>
 struct Warp {
     static constexpr int kU = Gen<PRNG>::kU, SW = Gen<PRNG>::SW;
-    static constexpr int B = 32 - 2 * kU;                  // draws per batch
-    static constexpr int RS = SW == 1 ? 33 : 66;            // row stride in words
+    static constexpr int B = 33 - 2 * kU;                  // draws per batch
+    static constexpr int RS = SW == 1 ? 33 : 66;            // row stride in words: 33 slots
     uint32_t stage[32 * RS];   // row r, slot d: words r RS + SW d ..
     uint4 info[32];            // per row: output address (low, high), dropped slots
     uint64_t tq_addr[32];      // accepted tails waiting for their value: output address | negative
@@ -485,7 +486,7 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
                 const uint32_t w = row[SW * p + SW - 1];
                 const bool tail = (w & 0x7Fu) == 0x7Fu;
                 const int need = tail ? 2 * kU : kU;
-                du |= ((1u << need) - 1u) << (p + 1);   // p + need <= 31 + 4: bits past 31 drop out
+                du |= ((1u << need) - 1u) << (p + 1);   // bits past 31 drop out: slot 32 holds only uniforms
                 while (B + ne <= p + need) {   // uniforms past the batch (rare)
                     uint32_t wx;
                     GT::draw(g, row + SW * (B + ne), wx);
@@ -523,7 +524,10 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
                     // the draws up to the last output and its uniforms
                     const int c = 31 - __clz(~D);   // slot of the last output
                     int used = c + 1;
-                    while (used < n && ((du >> used) & 1u)) ++used;
+                    if ((nf >> c) & 1u) {   // a slow candidate: its uniforms follow it
+                        const uint32_t wc = row[SW * c + SW - 1];
+                        used += (wc & 0x7Fu) == 0x7Fu ? 2 * kU : kU;
+                    }
                     draws += (uint64_t)used;
                     // the stream's record: the generator after those draws (the
                     // batch drew n from the state sb)
