@@ -302,8 +302,9 @@ zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uint64_t *seed
  *               lowered at launch to what one SM's shared memory holds for the
  *               generator.
  *  batch        slots of a lane's row per batch that a row store writes: 32, the
- *               only value (33 - 2 kU draws per batch, kU the raw steps of one
- *               nextDouble; a 33rd slot holds uniforms drawn past the batch).
+ *               only value (min(32, S - 2 kU) draws per batch, kU the raw steps
+ *               of one nextDouble, S = 35 slots per row for 32-bit draws and 33
+ *               for nextLong ones; slots past 32 hold uniforms drawn past the batch).
  *  store_bytes  0, the only value: the warp writes each row with one store per
  *               lane, the row's batch as one contiguous run, for every dtype.
  *  fma_of_4     ZIG_F64: of every 4 rows, how many rebuild their values with one

@@ -4,9 +4,10 @@
 //
 // Each lane owns one unit (a stream, or a 2^c chunk of one) with its generator
 // in registers; a warp works on its 32 units in batches of B draws per lane,
-// B = 33 - 2 kU (kU = raw steps per nextDouble), so that a batch with the
-// draws a tail may need past it fills the 33 slots of the lane's row (the
-// last one, past the 32 a row store writes, only ever holds a uniform).
+// B = min(32, S - 2 kU) (kU = raw steps per nextDouble), so that a batch with
+// the draws a tail may need past it fits the S slots of the lane's row (35 for
+// 32-bit slots, 33 for 64-bit ones; slots past the 32 a row store writes only
+// ever hold uniforms).
 //  A. Every lane takes B draws in lockstep and keeps each in its row, with no
 //     branch and no vote: the fast test j < k[i] (Sec. 1; the GSL form's first
 //     comparison) only sets a bit of the lane's mask nf.  A slot holds the
@@ -170,8 +171,9 @@ constexpr int kMaxThreads = 640;
 template <int PRNG, int DT, int MUT = 0>
 struct Warp {
     static constexpr int kU = Gen<PRNG>::kU, SW = Gen<PRNG>::SW;
-    static constexpr int B = 33 - 2 * kU;                  // draws per batch
-    static constexpr int RS = SW == 1 ? 33 : 66;            // row stride in words: 33 slots
+    static constexpr int S = SW == 1 ? 35 : 33;             // slots per row (an odd stride in words)
+    static constexpr int RS = SW * S;                       // row stride in words
+    static constexpr int B = S - 2 * kU < 32 ? S - 2 * kU : 32;   // draws per batch
     uint32_t stage[32 * RS];   // row r, slot d: words r RS + SW d ..
     uint4 info[32];            // per row: output address (low, high), dropped slots
     uint64_t tq_addr[32];      // accepted tails waiting for their value: output address | negative
@@ -486,7 +488,7 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
                 const uint32_t w = row[SW * p + SW - 1];
                 const bool tail = (w & 0x7Fu) == 0x7Fu;
                 const int need = tail ? 2 * kU : kU;
-                du |= ((1u << need) - 1u) << (p + 1);   // bits past 31 drop out: slot 32 holds only uniforms
+                if (p < 31) du |= ((1u << need) - 1u) << (p + 1);   // bits past 31 drop out: slots 32.. hold only uniforms
                 while (B + ne <= p + need) {   // uniforms past the batch (rare)
                     uint32_t wx;
                     GT::draw(g, row + SW * (B + ne), wx);
