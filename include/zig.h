@@ -303,7 +303,7 @@ zig_status zig_generate_noalloc(zig_prng prng, zig_alg alg, const uint64_t *seed
  *               generator.
  *  batch        slots of a lane's row per batch that a row store writes: 32, the
  *               only value (min(32, S - 2 kU) draws per batch, kU the raw steps
- *               of one nextDouble, S = 35 slots per row for 32-bit draws and 33
+ *               of one nextDouble, S = 35 slots per row for 32-bit draws and 34
  *               for nextLong ones; slots past 32 hold uniforms drawn past the batch).
  *  store_bytes  0, the only value: the warp writes each row with one store per
  *               lane, the row's batch as one contiguous run, for every dtype.

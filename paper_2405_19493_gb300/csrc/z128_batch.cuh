@@ -6,8 +6,8 @@
 // in registers; a warp works on its 32 units in batches of B draws per lane,
 // B = min(32, S - 2 kU) (kU = raw steps per nextDouble), so that a batch with
 // the draws a tail may need past it fits the S slots of the lane's row (35 for
-// 32-bit slots, 33 for 64-bit ones; slots past the 32 a row store writes only
-// ever hold uniforms).
+// 32-bit slots, 34 for 64-bit ones, what shared memory holds for 20 warps;
+// slots past the 32 a row store writes only ever hold uniforms).
 //  A. Every lane takes B draws in lockstep and keeps each in its row, with no
 //     branch and no vote: the fast test j < k[i] (Sec. 1; the GSL form's first
 //     comparison) only sets a bit of the lane's mask nf.  A slot holds the
@@ -171,7 +171,7 @@ constexpr int kMaxThreads = 640;
 template <int PRNG, int DT, int MUT = 0>
 struct Warp {
     static constexpr int kU = Gen<PRNG>::kU, SW = Gen<PRNG>::SW;
-    static constexpr int S = SW == 1 ? 35 : 33;             // slots per row (an odd stride in words)
+    static constexpr int S = SW == 1 ? 35 : 34;             // slots per row
     static constexpr int RS = SW * S;                       // row stride in words
     static constexpr int B = S - 2 * kU < 32 ? S - 2 * kU : 32;   // draws per batch
     uint32_t stage[32 * RS];   // row r, slot d: words r RS + SW d ..
