@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
                 for (int r = 0; r < 32; r += 8) mutate_rows8<PRNG>(ws, tb, r, lane, lane_bit, lt_mask, copy);
             } else {
                 // products q = 0..3 of every two steps: the binary64 fma for q < NDF
-#pragma unroll 2
+#pragma unroll 4
                 for (int r = 0; r < 32; r += 4) {
                     write_row<PRNG, DT, (0 >= NDF)>(ws, tb, r + 0, lane, lane_bit, lt_mask, copy);
                     write_row<PRNG, DT, (1 >= NDF)>(ws, tb, r + 1, lane, lane_bit, lt_mask, copy);

@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1) z256b_kernel(GenArgs a) {
             }
             ws.info[lane] = make_uint4((uint32_t)(uintptr_t)dst, (uint32_t)((uintptr_t)dst >> 32), D, 0u);
             __syncwarp();
-#pragma unroll 4
+#pragma unroll(DT == ZIG_F64 ? 8 : 4)   // binary64 rows: more fmas in flight; narrow rows: fewer registers
             for (int r = 0; r < 32; ++r) {
                 const uint4 inf = ws.info[r];
                 const uint64_t v = value_of<PRNG>(tb, ws.stage[r * kRS + lane], lane);
