@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
 
         while (__any_sync(kFull, rem > 0)) {
             // ---- A: B draws per lane, lockstep; nf marks the slow candidates ----
-            uint32_t nf = 0;
+            uint32_t nfr = 0;   // draw d's fast-test bit at B - 1 - d (built by doubling)
             const uint64_t sb = first_state_of(g);
             auto step = [&](auto dc) {
                 constexpr int d = decltype(dc)::value;
@@ -468,9 +468,12 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
                     GT::draw(g, row + SW * d, w);
                 }
                 const uint32_t K = *(const uint32_t*)(tb + entry_off<C>(w, kcopy));
-                nf |= (w >= K ? 1u : 0u) << d;
+                // nfr = 2 nfr + (w >= K): the carry of w - K is 1 when nothing is borrowed
+                asm("{\n\t.reg .u32 t;\n\tsub.cc.u32 t, %1, %2;\n\taddc.u32 %0, %3, %3;\n\t}"
+                    : "=r"(nfr) : "r"(w), "r"(K), "r"(nfr));
             };
             unroll<B>(step);
+            const uint32_t nf = __brev(nfr) >> (32 - B);
             if constexpr (PRNG == ZIG_LCG48) GT::template skip<B>(g);
             // ---- B: each lane decides its own slow candidates, in draw order ----
             // Walking its nf bits, a lane meets each slow draw that an earlier one
