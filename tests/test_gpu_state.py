@@ -222,3 +222,20 @@ def test_server_population_continues_its_streams(Z):
     ref = fmaf_ref(fmaf_ref(x0.cpu().numpy(), sigma, zc[:, :L]), sigma, zc[:, L:2 * L])
     assert np.array_equal(x.cpu().numpy().view(np.int32), ref.view(np.int32))
     assert torch.equal(g, z[:, 2 * L:])
+
+
+@pytest.mark.parametrize("prng", PRNGS)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_records_at_a_batch_end(Z, prng, dtype):
+    # A batch takes 32 draws (31 for LCG48) and the draws a slow candidate needs past
+    # them go to the row's spare slots.  With a first call as long as one batch, about
+    # one stream in a hundred ends it on a slow candidate in the batch's last slot,
+    # whose uniforms lie past the 32 stored slots; the record must account for them.
+    n = 1 << 16
+    L1 = 31 if prng == "lcg48" else 32
+    seeds = W.seeds(n, base=0x3A7 + 11 * PRNGS.index(prng))
+    a = np.full(n, L1, dtype=np.uint64)
+    b = np.full(n, 50, dtype=np.uint64)
+    got, _ = split_then_join(Z, prng, "zig128", seeds, [a, b], dtype)
+    ref = stateless(Z, prng, "zig128", seeds, a + b, dtype).view(INT_VIEW[dtype]).cpu().numpy()
+    assert np.array_equal(got, ref)
