@@ -10,12 +10,13 @@
 // slots past the 32 a row store writes only ever hold uniforms).
 //  A. Every lane takes B draws in lockstep and keeps each in its row, with no
 //     branch and no vote: the fast test j < k[i] (Sec. 1; the GSL form's first
-//     comparison) only sets a bit of the lane's mask nf.  A slot holds the
+//     comparison) only sets a bit of the lane's mask nf (a carry chain: two
+//     instructions a draw).  A slot holds the
 //     32-bit draw w, or for the generators whose draws are nextLong outputs the
 //     whole output (a wedge or tail test may read it as its uniform).
 //  B. Each lane walks its nf bits in draw order and decides its own slow
-//     candidates (about 0.36 per lane and batch, so the warp's loop runs about
-//     twice).  A slow candidate at draw p (j >= k[i]) consumes the next kU
+//     candidates (2.8 % of draws: about 0.9 per lane and batch, so the warp's
+//     loop runs about three times).  A slow candidate at draw p (j >= k[i]) consumes the next kU
 //     (wedge, i < 127) or 2 kU (tail) draws as its uniforms; a consumed draw is
 //     not a candidate, whatever its bit says.  Uniforms past the batch are drawn
 //     at once.  The wedge and tail tests run first in binary32 with proven
