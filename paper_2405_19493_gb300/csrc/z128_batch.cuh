@@ -483,37 +483,43 @@ __global__ void __launch_bounds__(max_threads(PRNG), 1) z128f_kernel(GenArgs a) 
             // and tail tests run first in binary32 with proven margins (binary64 only
             // inside them).  A rejected candidate goes to the drops; an accepted
             // tail's m1 goes to the words of its first uniform for the value pass.
-            uint32_t du = 0, Dr = 0, L = 0;   // consumed uniforms, rejected, accepted tails
+            uint32_t du = 0, Dr = 0, L = 0, T = 0;   // consumed uniforms, rejected, accepted tails, tails
             int ne = 0;
             for (uint32_t m = rem > 0 ? nf : 0u; m;) {
                 const int p = __ffs(m) - 1;
-                m &= m - 1u;
-                if ((du >> p) & 1u) continue;   // a uniform of an earlier candidate
                 const uint32_t w = row[SW * p + SW - 1];
                 const bool tail = (w & 0x7Fu) == 0x7Fu;
                 const int need = tail ? 2 * kU : kU;
-                if (p < 31) du |= ((1u << need) - 1u) << (p + 1);   // bits past 31 drop out: slots 32.. hold only uniforms
+                // bits past 31 drop out: slots 32.. hold only uniforms
+                const uint32_t cons = p < 31 ? ((1u << need) - 1u) << (p + 1) : 0u;
+                du |= cons;
+                m &= ~(cons | (1u << p));   // this candidate and the draws it consumes
                 while (B + ne <= p + need) {   // uniforms past the batch (rare)
                     uint32_t wx;
                     GT::draw(g, row + SW * (B + ne), wx);
                     ++ne;
                 }
+                if (tail) {   // tested after the wedges (a tail is 5 % of candidates)
+                    T |= 1u << p;
+                    continue;
+                }
                 const uint64_t m1 = GT::m53(row, p + 1, sb);
-                if (!tail) {
-                    int f = z128_wedge_filter(slow, w & 0x7Fu, w >> 8, m1);
-                    if (f < 0) f = z128_wedge_exact(slow, w & 0x7Fu, w >> 8, m1) ? 1 : 0;
-                    Dr |= (f == 0 ? 1u : 0u) << p;
-                } else {
-                    const uint64_t m2 = GT::m53(row, p + 1 + kU, sb);
-                    int ft = z128_tail_filter(m1, m2);
-                    if (ft < 0) ft = z128_tail_exact(m1, m2) ? 1 : 0;
-                    if (ft == 0) {
-                        Dr |= 1u << p;
-                    } else {   // m1 goes to the first uniform's words (a dropped slot)
-                        row[SW * (p + 1)] = (uint32_t)m1;
-                        row[SW * (p + 1) + 1] = (uint32_t)(m1 >> 32);
-                        L |= 1u << p;
-                    }
+                int f = z128_wedge_filter(slow, w & 0x7Fu, w >> 8, m1);
+                if (f < 0) f = z128_wedge_exact(slow, w & 0x7Fu, w >> 8, m1) ? 1 : 0;
+                Dr |= (f == 0 ? 1u : 0u) << p;
+            }
+            for (uint32_t m = T; m; m &= m - 1u) {
+                const int p = __ffs(m) - 1;
+                const uint64_t m1 = GT::m53(row, p + 1, sb);
+                const uint64_t m2 = GT::m53(row, p + 1 + kU, sb);
+                int ft = z128_tail_filter(m1, m2);
+                if (ft < 0) ft = z128_tail_exact(m1, m2) ? 1 : 0;
+                if (ft == 0) {
+                    Dr |= 1u << p;
+                } else {   // m1 goes to the first uniform's words (a dropped slot)
+                    row[SW * (p + 1)] = (uint32_t)m1;
+                    row[SW * (p + 1) + 1] = (uint32_t)(m1 >> 32);
+                    L |= 1u << p;
                 }
             }
             // ---- C: drops, the unit's end, then the rows ----
